@@ -1,0 +1,134 @@
+"""Whole-step pins of the oracle's grid update (no GPU).
+
+The paper states no numerical experiment; these pins come from the mathematics
+of the update and from textbook lattice Boltzmann results (stated here as such):
+  * a sinusoidal shear wave decays at nu k^2 with nu = T0 (tau - 1/2)
+    (textbook LB viscosity; T0 = 1/3 for D2Q9/D3Q19/D3Q27, 2/3 for D3Q39);
+  * the 2-D Taylor-Green vortex, an exact Navier-Stokes solution, decays at 2 nu k^2;
+  * the Galilean-invariance claim of Sec. 4: on a uniform background flow U the
+    decay rate departs from its U = 0 value, and the departure shrinks as the
+    truncation order K rises within the lattice's support;
+  * periodic translation and lattice rotation commute with the step;
+  * total mass and momentum are conserved (Eq. inv summed over the lattice).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_02503_gb300 import fields
+
+
+def _amp(name, dims, f, comp, axis):
+    rho, u = oracle.moments(name, dims, f)
+    nx, ny, nz = (list(dims) + [1, 1])[:3]
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    pos = [x, y, z][axis].reshape(-1)
+    return abs(np.sum(u[comp] * np.exp(-2j * np.pi * pos / dims[axis])))
+
+
+def shear_decay_ratio(name, K, tau, dims, flow, grad, U=0.0, t0=100, t1=1000, amp=0.01):
+    lat = oracle.lattice(name)
+    bg = [0.0] * lat["D"]
+    bg[grad] = U
+    rho, u = fields.shear_wave(dims, amp, lat["D"], flow, grad, background=bg)
+    f = oracle.init_eq(name, K, dims, rho, u)
+    f = oracle.run(name, K, tau, dims, f, t0)
+    a0 = _amp(name, dims, f, flow, grad)
+    f = oracle.run(name, K, tau, dims, f, t1 - t0)
+    a1 = _amp(name, dims, f, flow, grad)
+    gamma = -np.log(a1 / a0) / (t1 - t0)
+    k = 2 * np.pi / dims[grad]
+    return gamma / (lat["T0"] * (tau - 0.5) * k * k)
+
+
+@pytest.mark.parametrize("K", [2, 3])
+def test_d2q9_shear_wave_decays_at_lb_viscosity(K):
+    # 64 x 64, tau = 0.8, u_x = 0.01 sin(2 pi y / 64), fit over t in [100, 1000]
+    r = shear_decay_ratio("D2Q9", K, 0.8, (64, 64), 0, 1)
+    assert abs(r - 1) < 0.01, r
+
+
+def test_d3q39_viscosity_uses_its_own_t0():
+    r = shear_decay_ratio("D3Q39", 4, 0.6, (32, 6, 6), 1, 0, t0=50, t1=400)
+    assert abs(r - 1) < 0.01, r
+
+
+@pytest.mark.parametrize("name,dims", [("D2Q9", (32, 32)), ("D3Q19", (32, 32, 2))])
+def test_taylor_green_2d_decays_at_twice_nu_k2(name, dims):
+    lat = oracle.lattice(name)
+    tau, u0 = 0.8, 0.01
+    rho, u = fields.taylor_green_2d(dims, u0, lat["T0"], D=lat["D"])
+    shape = u[0].copy()
+    f = oracle.init_eq(name, 3, dims, rho, u)
+    amps = []
+    for steps in (20, 180):
+        f = oracle.run(name, 3, tau, dims, f, steps)
+        _, uu = oracle.moments(name, dims, f)
+        amps.append(np.dot(uu[0], shape) / np.dot(shape, shape))
+    gamma = -np.log(amps[1] / amps[0]) / 180
+    k = 2 * np.pi / 32
+    nu = lat["T0"] * (tau - 0.5)
+    assert abs(gamma / (2 * nu * k * k) - 1) < 0.01
+
+
+@pytest.mark.parametrize("name,Ks,dims", [("D3Q27", [2, 3], (32, 2, 2)), ("D3Q39", [2, 3, 4], (32, 6, 6))])
+def test_galilean_error_shrinks_with_truncation_order(name, Ks, dims):
+    """|gamma(U)/gamma(0) - 1| on a background flow U_x falls as K rises (Sec. 4)."""
+    errs = {}
+    for K in Ks:
+        base = shear_decay_ratio(name, K, 0.6, dims, 1, 0, U=0.0, t0=50, t1=400)
+        errs[K] = [abs(shear_decay_ratio(name, K, 0.6, dims, 1, 0, U=U, t0=50, t1=400) / base - 1) for U in (0.1, 0.2)]
+    for lo, hi in zip(Ks[:-1], Ks[1:]):
+        assert errs[hi][0] < errs[lo][0] and errs[hi][1] < errs[lo][1], errs
+    assert errs[Ks[0]][1] > 0.05  # prior filtered form (K = 2) is visibly not Galilean invariant at U = 0.2
+    assert errs[Ks[-1]][1] < 1e-3
+
+
+def test_translation_commutes_with_step():
+    name, dims = "D3Q19", (5, 7, 9)
+    lat = oracle.lattice(name)
+    f = fields.random_distributions(lat["Q"], 5 * 7 * 9, salt=3)
+    out = oracle.run(name, 3, 0.6, dims, f, 3)
+    shift = (1, 2, 3)
+
+    def roll(a):
+        a = a.reshape(lat["Q"], dims[2], dims[1], dims[0])
+        return np.roll(a, (shift[2], shift[1], shift[0]), axis=(1, 2, 3)).reshape(lat["Q"], -1)
+
+    out2 = oracle.run(name, 3, 0.6, dims, roll(f), 3)
+    np.testing.assert_array_equal(out2, roll(out))
+
+
+@pytest.mark.parametrize("name,K", [("D3Q19", 3), ("D3Q39", 4)])
+def test_quarter_turn_commutes_with_step(name, K):
+    """Rotate fields by 90 degrees about z: (x, y) -> (-y, x); velocities map the same way."""
+    lat = oracle.lattice(name)
+    n = 8
+    dims = (n, n, 3)
+    C = n * n * 3
+    f = fields.random_distributions(lat["Q"], C, salt=4)
+    c = [tuple(v) for v in lat["c"]]
+    perm = [c.index((-v[1], v[0], v[2])) for v in c]  # velocity i -> index of its rotated image
+
+    def rotate(a):
+        a = a.reshape(lat["Q"], 3, n, n)  # [i, z, y, x]
+        out = np.empty_like(a)
+        for i in range(lat["Q"]):
+            # new(x', y') = old(x, y) with x' = -y, y' = x (periodic)
+            out[perm[i]] = np.transpose(a[i], (0, 2, 1))[:, :, ::-1]
+            out[perm[i]] = np.roll(out[perm[i]], 1, axis=2)
+        return out.reshape(lat["Q"], C)
+
+    out = oracle.run(name, K, 0.7, dims, f, 2)
+    out_rot = oracle.run(name, K, 0.7, dims, rotate(f), 2)
+    np.testing.assert_allclose(out_rot, rotate(out), rtol=0, atol=1e-15)
+
+
+def test_grid_conserves_mass_and_momentum():
+    name, dims = "D3Q39", (8, 7, 6)
+    lat = oracle.lattice(name)
+    f = fields.random_distributions(lat["Q"], 8 * 7 * 6, salt=5)
+    out = oracle.run(name, 4, 0.55, dims, f, 10)
+    c = lat["c"].astype(np.float64)
+    assert abs(out.sum() - f.sum()) < 1e-12 * f.sum()
+    np.testing.assert_allclose(c.T @ out.sum(1), c.T @ f.sum(1), atol=1e-13)
