@@ -1,0 +1,343 @@
+"""Benchmark of the fused GI-filtered lattice Boltzmann step on one or more GB300s.
+
+Default workload: D3Q19 periodic 256^3, FP32 storage and arithmetic, Taylor-Green
+vortex u0 = 0.05, tau = 0.55, truncation order K = 2.  A "step" is one fused
+pull-stream + collision pass over the whole lattice.  The metric is MLUPS
+(million lattice-cell updates per second, whole job); the roofline is the HBM
+bandwidth (2 Q sizeof(storage) algorithmic bytes per cell update).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on the host cores, on a bounded sample of the same workload.
+Multi-GPU runs are independent replicas (one lattice per rank; the method has no
+exchange between independent solves), launched with torchrun.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+LATTICE_Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27, "D3Q39": 39}
+LATTICE_T0 = {"D2Q9": 1.0 / 3.0, "D3Q19": 1.0 / 3.0, "D3Q27": 1.0 / 3.0, "D3Q39": 2.0 / 3.0}
+STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}
+DTYPE_NAME = {"f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)", "f64": "f64"}
+KERNEL_SOURCES = ["lbm_core.cuh", "lbm_kernels.cuh", "lbm_lattice.cuh", "lbm_staged.cuh"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--lattice", default="D3Q19", choices=list(LATTICE_Q))
+    p.add_argument("--dims", type=int, nargs=3, default=[256, 256, 256])
+    p.add_argument("--K", type=int, default=2)
+    p.add_argument("--tau", type=float, default=0.55)
+    p.add_argument("--u0", type=float, default=0.05)
+    p.add_argument("--storage", default="f32", choices=list(STORE_BYTES))
+    p.add_argument("--variant", type=int, default=None, help="force a kernel variant (default: autotune)")
+    p.add_argument("--cpt", type=int, default=None, help="force cells per thread (with --variant 0)")
+    p.add_argument("--block", type=int, default=None)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    return p.parse_args()
+
+
+def workload_name(a):
+    return "%s periodic %dx%dx%d %s Taylor-Green u0=%g tau=%g K=%d" % (
+        a.lattice, a.dims[0], a.dims[1], a.dims[2], a.storage.upper(), a.u0, a.tau, a.K)
+
+
+def config_of(a, extra=None):
+    c = {"workload": workload_name(a), "lattice": a.lattice, "dims": list(a.dims), "K": a.K, "tau": a.tau,
+         "u0": a.u0, "storage": a.storage, "parallelism": "replicas",
+         "l2": "inputs larger than L2: %.2f GB of distributions per step" % (
+             2 * LATTICE_Q[a.lattice] * STORE_BYTES[a.storage] * int(np.prod(a.dims)) / 1e9)}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def initial_fields(a):
+    from paper_2002_02503_gb300 import fields
+
+    D = 2 if a.lattice == "D2Q9" else 3
+    dims = tuple(a.dims)
+    if D == 3:
+        return fields.taylor_green_3d(dims, a.u0, LATTICE_T0[a.lattice])
+    return fields.taylor_green_2d(dims, a.u0, LATTICE_T0[a.lattice], D=2)
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_sample(a, seconds):
+    """Time the FP64 oracle on a sub-lattice of the workload (same lattice, K, tau)."""
+    import oracle
+    from paper_2002_02503_gb300 import fields
+
+    nthreads = oracle.default_threads()
+    side = 64 if a.lattice != "D3Q39" else 48
+    dims = (side, side, side) if a.lattice != "D2Q9" else (256, 256, 1)
+    D = 2 if a.lattice == "D2Q9" else 3
+    if D == 3:
+        rho, u = fields.taylor_green_3d(dims, a.u0, LATTICE_T0[a.lattice])
+    else:
+        rho, u = fields.taylor_green_2d(dims, a.u0, LATTICE_T0[a.lattice], D=2)
+    f = oracle.init_eq(a.lattice, a.K, dims, rho, u)
+    C = int(np.prod(dims))
+    t0 = time.perf_counter()
+    f = oracle.run(a.lattice, a.K, a.tau, dims, f, 1, nthreads)
+    one = time.perf_counter() - t0
+    steps = int(max(1, min(200, seconds / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(a.lattice, a.K, a.tau, dims, f, steps, nthreads)
+    dt = time.perf_counter() - t0
+    return {"value": C * steps / dt / 1e6, "unit": "MLUPS", "cores": nthreads, "kind": "oracle",
+            "sample": "%s K=%d tau=%g Taylor-Green sub-lattice %dx%dx%d, %d steps, %.1f s" % (
+                a.lattice, a.K, a.tau, dims[0], dims[1], dims[2], steps, dt)}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.active = False
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if self.active:
+                self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline helpers
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        p = os.path.join(ROOT, "paper_2002_02503_gb300", "csrc", f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(a, variant):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    key = "%s_%dx%dx%d_%s_K%d_v%d" % (a.lattice, a.dims[0], a.dims[1], a.dims[2], a.storage, a.K, variant)
+    r = rec.get(key)
+    if not r or r.get("kernel_hash") != kernel_hash():
+        return None
+    return r.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------ main arms
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    cpu = oracle_sample(a, a.cpu_seconds)
+    out = {"metric": "MLUPS", "value": cpu["value"], "unit": "MLUPS", "n_gpus": a.gpus, "steps": a.steps,
+           "warmup": a.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic (Taylor-Green initial field)", "impl": "reference",
+           "config": config_of(a), "cpu_baseline": cpu,
+           "e2e": {"value": cpu["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(a):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2002_02503_gb300 import lbm
+
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream(dev)
+    dims = tuple(a.dims)
+    C = int(np.prod(dims))
+    Q = LATTICE_Q[a.lattice]
+    rho, u = initial_fields(a)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        s = lbm.Solver(a.lattice, dims, a.tau, a.K, a.storage, stream=stream)
+        s.set_fields(rho, u)
+        tuned_us = None
+        if a.variant is None:
+            tuned_us = lbm.lbm_autotune(s.handle, 20)
+        else:
+            lbm.lbm_set_kernel(s.handle, a.variant, a.cpt or 0, a.block or 0)
+        variant, cpt, block = lbm.lbm_get_kernel(s.handle)
+        s.set_fields(rho, u)
+        s.step(a.warmup)
+        barrier()
+
+        clocks = ClockSampler(dev)
+        clocks.start()
+        time.sleep(0.3)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        clocks.active = True
+        ev0.record(stream)
+        s.step(a.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        clocks.active = False
+        ms = ev0.elapsed_time(ev1)
+        barrier()
+        cons = s.conservation()
+
+        # end to end through the C-ABI with host buffers: fields in, K steps, moments out
+        e2e = None
+        if not a.no_e2e:
+            D = 2 if a.lattice == "D2Q9" else 3
+            rho_h = torch.from_numpy(rho).pin_memory()
+            u_h = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
+            rho_o = torch.empty(C, dtype=torch.float64).pin_memory()
+            u_o = torch.empty((D, C), dtype=torch.float64).pin_memory()
+            barrier()
+            t0 = time.perf_counter()
+            lbm.lbm_set_fields(s.handle, rho_h, u_h)
+            lbm.lbm_step(s.handle, a.steps)
+            lbm.lbm_get_moments(s.handle, rho_o, u_o)
+            t_e2e = time.perf_counter() - t0
+            barrier()
+            h2d = (rho_h.numel() + u_h.numel()) * 8
+            d2h = (rho_o.numel() + u_o.numel()) * 8
+            e2e = {"value": C * a.steps / t_e2e / 1e6, "unit": "MLUPS",
+                   "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
+                   "note": "one solve: set_fields from pinned host, %d steps, get_moments to pinned host; "
+                           "copies amortised over the steps" % a.steps}
+        s.close()
+    clocks.stop()
+
+    t_max = ms
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        if e2e is not None:
+            ee = torch.tensor([e2e["value"]], device="cuda", dtype=torch.float64)
+            dist.all_reduce(ee, op=dist.ReduceOp.MIN)
+            e2e["value"] = float(ee.item()) * world
+    value = world * C * a.steps / (t_max / 1e3) / 1e6
+    if rank == 0:
+        bpu = 2 * Q * STORE_BYTES[a.storage]
+        per_launch_s = (ms / 1e3) / a.steps
+        achieved = bpu * C / per_launch_s / 1e9
+        peak, peak_kind = measured_peak()
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(a, variant), "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": bpu * C,
+                "kernel": "step_%s" % ("direct" if variant == 0 else "staged")}
+        cpu = None
+        if not a.no_cpu_baseline:
+            cpu = oracle_sample(a, a.cpu_seconds)
+        out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": DTYPE_NAME[a.storage], "data": "synthetic (Taylor-Green initial field)",
+               "config": config_of(a, {"kernel": {"variant": variant, "cells_per_thread": cpt, "block": block,
+                                                  "autotuned_us": tuned_us}}),
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps,
+               "clocks": clocks.summary(),
+               "conservation": {"mass": cons[0], "momentum": list(cons[1:])}}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

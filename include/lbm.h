@@ -1,0 +1,153 @@
+/*
+ * lbm.h -- C-ABI of the GB300 lattice Boltzmann library implementing the
+ * Galilean-invariant filtered collision of Chen, Zhang & Gopalakrishnan,
+ * "Filtered lattice Boltzmann collision formulation enforcing isotropy and
+ * Galilean invariance" (arXiv 2002.02503).
+ *
+ * The state is a set of particle distributions f_i(x, t) on a periodic
+ * Cartesian lattice (Sec. 1, Eq. lbe).  One step applies the filtered collision
+ * of Eq. lbe-reg with the truncated Galilean-invariant non-equilibrium part of
+ * Eq. hermite-coll (closed forms Eq. filter-Pi, filter-1st, filter-2nd) and the
+ * truncated equilibrium of Eq. hermite, then streams every f_i one link along
+ * c_i (Eq. lbe).  The observables are rho and u of Eq. mme.
+ *
+ * Conventions shared by every call
+ *   - dims = {nx, ny, nz}; D2Q9 requires nz == 1.  Cell index = x + nx*(y + ny*z).
+ *   - Density fields are double[C]; velocity fields are double[D][C] (SoA).
+ *   - Distributions exchanged as double are [Q][C] in the library's velocity
+ *     order (lbm_lattice_info): index 0 is the rest velocity, then pairs
+ *     (2p+1, 2p+2) with c_{2p+2} = -c_{2p+1}.
+ *   - lbm_mem says whether a pointer is host memory (pageable or pinned) or
+ *     device memory of the solver's device.
+ *   - Every call returns an lbm_status; none throws, aborts or exits.  On an
+ *     error, lbm_last_error() holds a message for the calling thread.
+ *   - Nothing is allocated on the device by the library except a few bytes of
+ *     kernel-argument tables: the caller owns the workspace and every buffer.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1,   /* a NULL pointer, a size out of range, tau <= 1/2 ... */
+    LBM_ERR_UNSUPPORTED = 2,   /* truncation order outside [2, 2N-1] for the lattice, unknown storage */
+    LBM_ERR_OUT_OF_MEMORY = 3, /* workspace or pool too small for the request */
+    LBM_ERR_CUDA = 4,          /* a CUDA runtime call failed (message in lbm_last_error) */
+    LBM_ERR_NONFINITE = 5,     /* a reduction met NaN or Inf: the run has gone unstable */
+    LBM_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    LBM_ERR_BUSY = 7,          /* no free slot or memory in a pool right now */
+    LBM_ERR_NOT_FOUND = 8      /* unknown request id */
+} lbm_status;
+
+/* Velocity sets.  D2Q9, D3Q19: isotropy class 2N = 4, T0 = 1/3 (Sec. 2 after
+ * Eq. iso); D3Q39: 2N = 6, T0 = 2/3; D3Q27 (not in the paper): 2N = 4, T0 = 1/3. */
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2, LBM_D3Q39 = 3 } lbm_lattice;
+
+/* How distributions are stored in HBM.  The collision always computes in FP32
+ * (FP64 for LBM_STORE_F64).  Every form stores the shifted value
+ * g~_i = g_i - w_i rho0; the 16-bit forms store round_to_nearest(g~_i / w_i). */
+typedef enum {
+    LBM_STORE_F32 = 0,
+    LBM_STORE_F16 = 1,
+    LBM_STORE_BF16 = 2,
+    LBM_STORE_F64 = 3
+} lbm_storage;
+
+typedef enum { LBM_MEM_HOST = 0, LBM_MEM_DEVICE = 1 } lbm_mem;
+
+typedef struct lbm_solver lbm_solver; /* opaque; owned by the library */
+
+/* Velocity table of a lattice.  Any output pointer may be NULL.  c: int[Q*3]
+ * (z component 0 for D2Q9), w: double[Q].  kmax = 2N - 1, the highest
+ * truncation order the lattice supports (Sec. 2 truncation rule, Sec. 3). */
+lbm_status lbm_lattice_info(lbm_lattice lattice, int *D, int *Q, int *c, double *w, double *T0, int *kmax);
+
+/* Bytes of device workspace lbm_create needs: two distribution buffers of
+ * Q*C values of the storage type (pull streaming ping-pongs between them) plus
+ * a small reduction area.  Returns 0 for invalid arguments. */
+size_t lbm_workspace_bytes(lbm_lattice lattice, const int64_t dims[3], lbm_storage storage);
+
+/* Create a solver for a periodic lattice (Eq. lbe, Eq. lbe-reg).
+ *   tau               relaxation time, > 1/2 (Eq. post-1); viscosity T0 (tau - 1/2)
+ *   truncation_order  K, the highest Hermite order kept in BOTH Eq. hermite and
+ *                     Eq. hermite-coll; 2 <= K <= 2N-1 of the lattice.  K = 2 is the
+ *                     prior filtered form (Eq. filter-Pi), K = 3 Eq. filter-1st,
+ *                     K = 4 Eq. filter-2nd, K = 5 the next term of Eq. hermite-coll.
+ *   rho0              reference density of the storage shift (> 0)
+ *   device_workspace  caller-owned device memory of at least lbm_workspace_bytes,
+ *                     256-byte aligned; it must outlive the solver.
+ *   cuda_stream       cudaStream_t for all device work (NULL = legacy default stream)
+ * Validation happens before any device work.  The distributions are undefined
+ * until lbm_set_fields or lbm_set_distributions. */
+lbm_status lbm_create(lbm_lattice lattice, const int64_t dims[3], double tau, int truncation_order,
+                      lbm_storage storage, double rho0, void *device_workspace, size_t workspace_bytes,
+                      void *cuda_stream, lbm_solver **out);
+
+/* Set f_i(x, 0) = f^eq_i(rho(x), u(x)) truncated at K (Eq. hermite) and t = 0.
+ * rho: double[C], u: double[D][C].  Host inputs are staged through the idle
+ * distribution buffer; the call returns once the data has been consumed. */
+lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm_mem mem);
+
+/* Advance n >= 0 steps of pull-streaming + collision (Eq. lbe-reg).  Asynchronous
+ * on the solver's stream; no host synchronisation. */
+lbm_status lbm_step(lbm_solver *s, int64_t n);
+
+/* rho(x, t) and u(x, t) of the pre-collision distributions at the current t
+ * (Eq. mme).  Either pointer may be NULL.  Synchronises the stream. */
+lbm_status lbm_get_moments(lbm_solver *s, double *rho, double *u, lbm_mem mem);
+
+/* The pre-collision distributions f_i(x, t) as double[Q][C] (library velocity
+ * order).  Synchronises the stream. */
+lbm_status lbm_get_f(lbm_solver *s, double *f, lbm_mem mem);
+
+/* Global FP64 sums over the lattice: out = {sum rho, sum rho u_x, sum rho u_y,
+ * sum rho u_z} (Eq. inv summed over x: constant in time up to rounding).
+ * Host output; synchronises.  LBM_ERR_NONFINITE if any sum is NaN/Inf. */
+lbm_status lbm_conservation(lbm_solver *s, double out[4]);
+
+/* Fourier amplitude of one velocity component at integer wave vector k:
+ * out = {Re, Im} of sum_x u_comp(x) exp(-2 pi i (kx x/nx + ky y/ny + kz z/nz)),
+ * accumulated in FP64.  Host output; synchronises. */
+lbm_status lbm_mode_amplitude(lbm_solver *s, const int64_t k[3], int component, double out[2]);
+
+/* Checkpoint: the raw stored distributions (bytes = Q*C*sizeof(storage)) and
+ * the step counter.  get synchronises; set replaces the state. */
+lbm_status lbm_get_distributions(lbm_solver *s, void *dst, size_t bytes, lbm_mem mem, int64_t *t);
+lbm_status lbm_set_distributions(lbm_solver *s, const void *src, size_t bytes, lbm_mem mem, int64_t t);
+
+/* Current step counter t. */
+lbm_status lbm_time(const lbm_solver *s, int64_t *t);
+
+/* Kernel configuration of the step.  variant: 0 = register pull (vector loads
+ * plus warp shuffles for the x shift), 1 = persistent shared-memory row
+ * staging through bulk asynchronous copies.  cells_per_thread: 1, 2, 4 or 8 (must
+ * divide nx).  block_threads: 32..1024, a multiple of 32.  A negative variant
+ * and a zero cells_per_thread or block_threads keep the current setting.
+ * LBM_ERR_UNSUPPORTED if the combination is not built. */
+lbm_status lbm_set_kernel(lbm_solver *s, int variant, int cells_per_thread, int block_threads);
+lbm_status lbm_get_kernel(const lbm_solver *s, int *variant, int *cells_per_thread, int *block_threads);
+
+/* Autotuner: times every built kernel configuration for this solver on its own
+ * buffers (reads the current state, writes only the idle buffer, so the state is
+ * unchanged) over `iters` launches each and keeps the fastest.  best_us, if not
+ * NULL, receives the average step time of the chosen configuration. */
+lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us);
+
+/* Release the solver (not the workspace).  Synchronises its stream. */
+lbm_status lbm_destroy(lbm_solver *s);
+
+const char *lbm_status_string(lbm_status status);
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

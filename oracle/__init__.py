@@ -36,7 +36,7 @@ def _load():
         lib.orc_feq.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
         lib.orc_fneq_hat.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
         lib.orc_collide.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, dp, dp, dp]
-        lib.orc_init_eq.argtypes = [ctypes.c_int, ctypes.c_int, i64p, dp, dp, dp]
+        lib.orc_init_eq.argtypes = [ctypes.c_int, ctypes.c_int, i64p, dp, dp, dp, ctypes.c_int]
         lib.orc_moments.argtypes = [ctypes.c_int, i64p, dp, dp, dp]
         lib.orc_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, i64p, dp, ctypes.c_int64, ctypes.c_int]
         _lib = lib
@@ -130,7 +130,7 @@ def _dims(dims):
     return d
 
 
-def init_eq(name, K, dims, rho, u):
+def init_eq(name, K, dims, rho, u, nthreads=None):
     """f := f^eq_K(rho, u) everywhere.  rho [C], u [D, C] -> f [Q, C]."""
     lat = lattice(name)
     d = _dims(dims)
@@ -138,8 +138,9 @@ def init_eq(name, K, dims, rho, u):
     rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(C)
     u = np.ascontiguousarray(u, dtype=np.float64).reshape(lat["D"], C)
     f = np.zeros((lat["Q"], C))
+    nt = default_threads() if nthreads is None else int(nthreads)
     rc = _load().orc_init_eq(_lat(name), int(K), d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                             _dp(rho), _dp(u), _dp(f))
+                             _dp(rho), _dp(u), _dp(f), nt)
     _check(rc, "init_eq")
     return f
 

@@ -348,7 +348,7 @@ typedef struct {
     long nx, ny, nz;
     const double *f;
     double *fnew;
-    long z0, z1;
+    long r0, r1; /* rows (y + ny z) handled by this thread */
     int err;
 } step_job_t;
 
@@ -363,9 +363,9 @@ static void *step_worker(void *arg) {
         return NULL;
     }
     double fc[ORC_MAXQ], fp[ORC_MAXQ];
-    for (long z = job->z0; z < job->z1; ++z)
-        for (long y = 0; y < job->ny; ++y)
-            for (long x = 0; x < job->nx; ++x) {
+    for (long r = job->r0; r < job->r1; ++r) {
+        const long y = r % job->ny, z = r / job->ny;
+        for (long x = 0; x < job->nx; ++x) {
                 long cell = x + job->nx * (y + job->ny * z);
                 for (int i = 0; i < L->Q; ++i) fc[i] = job->f[i * C + cell];
                 collide_cell(job->ctx, &wk, job->tau, fc, fp, NULL, NULL, NULL, NULL, NULL);
@@ -376,15 +376,16 @@ static void *step_worker(void *arg) {
                     job->fnew[i * C + xd + job->nx * (yd + job->ny * zd)] = fp[i];
                 }
             }
+    }
     work_free(&wk);
     return NULL;
 }
 
 static int run_parallel(const orc_ctx_t *ctx, double tau, const int64_t *dims, const double *f, double *fnew,
                         int nthreads) {
-    long nz = dims[2];
+    long rows = dims[1] * dims[2];
     if (nthreads < 1) nthreads = 1;
-    if (nthreads > nz) nthreads = (int)nz;
+    if (nthreads > rows) nthreads = (int)rows;
     step_job_t jobs[256];
     pthread_t th[256];
     if (nthreads > 256) nthreads = 256;
@@ -393,11 +394,11 @@ static int run_parallel(const orc_ctx_t *ctx, double tau, const int64_t *dims, c
         jobs[t].tau = tau;
         jobs[t].nx = dims[0];
         jobs[t].ny = dims[1];
-        jobs[t].nz = nz;
+        jobs[t].nz = dims[2];
         jobs[t].f = f;
         jobs[t].fnew = fnew;
-        jobs[t].z0 = nz * t / nthreads;
-        jobs[t].z1 = nz * (t + 1) / nthreads;
+        jobs[t].r0 = rows * t / nthreads;
+        jobs[t].r1 = rows * (t + 1) / nthreads;
         jobs[t].err = 0;
     }
     for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, step_worker, &jobs[t]);
@@ -489,8 +490,36 @@ int orc_collide(int lat, int K, double tau, const double *f, double *fpost, doub
 }
 
 /* f := f^eq_K(rho, u) at every cell (no non-equilibrium part).
- * rho: [C], u: [D][C] (SoA), f: [Q][C]. */
-int orc_init_eq(int lat, int K, const int64_t *dims, const double *rho, const double *u, double *f) {
+ * rho: [C], u: [D][C] (SoA), f: [Q][C].  Cells are split over threads. */
+typedef struct {
+    const orc_ctx_t *ctx;
+    long C, c0, c1;
+    const double *rho, *u;
+    double *f;
+    int err;
+} init_job_t;
+
+static void *init_worker(void *arg) {
+    init_job_t *job = (init_job_t *)arg;
+    const orc_lattice_t *L = &job->ctx->L;
+    orc_work_t wk;
+    if (work_init(L->D, job->ctx->K, &wk)) {
+        job->err = -3;
+        work_free(&wk);
+        return NULL;
+    }
+    double feq[ORC_MAXQ];
+    for (long cell = job->c0; cell < job->c1; ++cell) {
+        double uc[3] = {0, 0, 0};
+        for (int a = 0; a < L->D; ++a) uc[a] = job->u[a * job->C + cell];
+        feq_cell(job->ctx, &wk, job->rho[cell], uc, feq);
+        for (int i = 0; i < L->Q; ++i) job->f[i * job->C + cell] = feq[i];
+    }
+    work_free(&wk);
+    return NULL;
+}
+
+int orc_init_eq(int lat, int K, const int64_t *dims, const double *rho, const double *u, double *f, int nthreads) {
     orc_ctx_t ctx;
     int rc = ctx_init(lat, K, &ctx);
     if (rc) return rc;
@@ -499,18 +528,28 @@ int orc_init_eq(int lat, int K, const int64_t *dims, const double *rho, const do
         return -5;
     }
     long C = dims[0] * dims[1] * dims[2];
-    orc_work_t wk;
-    if (work_init(ctx.L.D, K, &wk)) rc = -3;
-    else {
-        double feq[ORC_MAXQ];
-        for (long cell = 0; cell < C; ++cell) {
-            double uc[3] = {0, 0, 0};
-            for (int a = 0; a < ctx.L.D; ++a) uc[a] = u[a * C + cell];
-            feq_cell(&ctx, &wk, rho[cell], uc, feq);
-            for (int i = 0; i < ctx.L.Q; ++i) f[i * C + cell] = feq[i];
-        }
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (nthreads > C) nthreads = (int)C;
+    init_job_t jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].ctx = &ctx;
+        jobs[t].C = C;
+        jobs[t].c0 = C * t / nthreads;
+        jobs[t].c1 = C * (t + 1) / nthreads;
+        jobs[t].rho = rho;
+        jobs[t].u = u;
+        jobs[t].f = f;
+        jobs[t].err = 0;
     }
-    work_free(&wk);
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, init_worker, &jobs[t]);
+    init_worker(&jobs[0]);
+    rc = jobs[0].err;
+    for (int t = 1; t < nthreads; ++t) {
+        pthread_join(th[t], NULL);
+        if (jobs[t].err) rc = jobs[t].err;
+    }
     ctx_free(&ctx);
     return rc;
 }

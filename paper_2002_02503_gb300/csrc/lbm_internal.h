@@ -1,0 +1,88 @@
+// lbm_internal.h -- host-side interfaces between the C-ABI layer and the
+// per-lattice kernel instantiation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// Cells per thread variants of the register-pull step: V = 1, 2, 4, 8.
+constexpr int kNumV = 4;
+inline int v_index(int V) { return V == 1 ? 0 : V == 2 ? 1 : V == 4 ? 2 : V == 8 ? 3 : -1; }
+inline int v_of_index(int k) { return 1 << k; }
+
+struct StepArgs {
+    const void *src;  // stored distributions at t (post-collision of t-1, un-streamed)
+    void *dst;        // stored distributions at t+1
+    int nx, ny, nz;
+    long long P;      // cells per velocity plane (nx*ny*nz)
+    double relax;     // 1 - 1/tau
+    double rho0;
+    unsigned int *status;  // device status word (persistent variant), may be null
+    int grid_limit;        // persistent variant: CTAs to launch (0 = one per SM slot)
+};
+
+struct InitArgs {
+    void *dst;             // distributions to write
+    const double *rho;     // [count] density for cells [c0, c0+count)
+    const double *u;       // [D][ustride] velocity (component a at u + a*ustride)
+    long long ustride;
+    long long c0, count;
+    int nx, ny, nz;
+    long long P;
+    double rho0;
+};
+
+struct PullArgs {
+    const void *src;       // stored distributions
+    double *rho;           // [count] or null
+    double *u;             // [D][ustride] or null
+    double *f;             // [Q][fstride] or null (pull_f)
+    long long ustride, fstride;
+    long long c0, count;
+    int nx, ny, nz;
+    long long P;
+    double rho0;
+};
+
+struct ReduceArgs {
+    const void *src;
+    int nx, ny, nz;
+    long long P;
+    double rho0;
+    double *partials;      // [blocks][nvals]
+    double *out;           // [nvals] device
+    int blocks;
+    int k[3];              // mode wave vector
+    int component;         // mode velocity component
+};
+
+typedef cudaError_t (*step_fn)(const StepArgs &, int block_threads, cudaStream_t);
+typedef cudaError_t (*init_fn)(const InitArgs &, cudaStream_t);
+typedef cudaError_t (*pull_fn)(const PullArgs &, cudaStream_t);
+typedef cudaError_t (*reduce_fn)(const ReduceArgs &, cudaStream_t);
+
+struct KernelSet {
+    step_fn direct[kNumV];   // variant 0, per V (null where not built)
+    step_fn staged;          // variant 1 (null where not built)
+    int staged_block;        // threads per CTA the staged variant is built for
+    init_fn init;
+    pull_fn moments;
+    pull_fn pull_f;
+    reduce_fn conservation;  // nvals = 4
+    reduce_fn mode;          // nvals = 2
+};
+
+// Defined in the instantiation units, one per lattice.
+const KernelSet *kernels_d2q9(int K, lbm_storage st);
+const KernelSet *kernels_d3q19(int K, lbm_storage st);
+const KernelSet *kernels_d3q27(int K, lbm_storage st);
+const KernelSet *kernels_d3q39(int K, lbm_storage st);
+
+constexpr int kReduceBlocks = 1216;  // 8 x 152 SMs
+constexpr int kReduceThreads = 256;
+
+}  // namespace lbm

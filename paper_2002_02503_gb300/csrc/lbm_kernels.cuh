@@ -1,0 +1,455 @@
+// lbm_kernels.cuh -- kernel templates of the fused lattice Boltzmann step and
+// its helpers.  Included once per lattice by an instantiation unit.
+//
+// Storage: SoA planes g[i][z][y][x] (x fastest), one plane of P = nx*ny*nz
+// values per velocity, in the lattice's pair order.  The stored field at step t
+// is the post-collision distribution of step t-1 before streaming, so step t
+// pulls f_i(x, t) = g_i(x - c_i) (Eq. lbe read backwards along each link),
+// collides (Eq. lbe-reg) and writes g_i(x) of step t+1 to the other buffer.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_core.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------ vector IO
+template <int BYTES>
+struct RawOf;
+template <>
+struct RawOf<2> { using type = unsigned short; };
+template <>
+struct RawOf<4> { using type = unsigned int; };
+template <>
+struct RawOf<8> { using type = uint2; };
+template <>
+struct RawOf<16> { using type = uint4; };
+
+template <typename S, int V>
+__device__ __forceinline__ void load_vec(const S *__restrict__ p, S (&out)[V]) {
+    constexpr int B = int(sizeof(S)) * V;
+    if constexpr (B <= 16) {
+        using R = typename RawOf<B>::type;
+        R r = *reinterpret_cast<const R *>(p);
+        memcpy(out, &r, B);
+    } else {
+        static_assert(B % 16 == 0, "vector width");
+#pragma unroll
+        for (int k = 0; k < B / 16; ++k) {
+            uint4 r = reinterpret_cast<const uint4 *>(p)[k];
+            memcpy(reinterpret_cast<char *>(out) + 16 * k, &r, 16);
+        }
+    }
+}
+
+template <typename S, int V>
+__device__ __forceinline__ void store_vec(S *__restrict__ p, const S (&in)[V]) {
+    constexpr int B = int(sizeof(S)) * V;
+    if constexpr (B <= 16) {
+        using R = typename RawOf<B>::type;
+        R r;
+        memcpy(&r, in, B);
+        *reinterpret_cast<R *>(p) = r;
+    } else {
+#pragma unroll
+        for (int k = 0; k < B / 16; ++k) {
+            uint4 r;
+            memcpy(&r, reinterpret_cast<const char *>(in) + 16 * k, 16);
+            reinterpret_cast<uint4 *>(p)[k] = r;
+        }
+    }
+}
+
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+__device__ __forceinline__ int wrapn(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+__host__ __device__ constexpr int floordiv(int e, int V) { return e >= 0 ? e / V : -((-e + V - 1) / V); }
+
+// ------------------------------------------------------------------ fused step, variant 0
+// One thread owns V consecutive cells of one x-row.  For each velocity it loads
+// the source row's aligned V-vector (same x range), then realigns the x shift
+// with warp shuffles from the neighbouring lanes; lanes whose neighbour does not
+// hold the adjacent chunk of the same row (warp or row edge, periodic wrap) read
+// the missing values directly.
+template <class LT, int K, class ST, int V>
+__global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *__restrict__ src,
+                                                          typename ST::S *__restrict__ dst, int nx, int ny,
+                                                          int ncx, long long P, typename ST::T relax,
+                                                          typename ST::T rho0) {
+    using S = typename ST::S;
+    using T = typename ST::T;
+    constexpr int Q = LT::Q, M = LT::MAXC;
+    const int nz = gridDim.y;
+    const int lane = threadIdx.x & 31;
+    const int z = blockIdx.y;
+    const int total = ncx * ny;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < total;
+    if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
+    const int y = t / ncx;
+    const int chunk = t - y * ncx;
+    const int x0 = chunk * V;
+
+    int ys[2 * M + 1], zs[2 * M + 1];
+#pragma unroll
+    for (int k = -M; k <= M; ++k) {
+        ys[k + M] = wrap1(y - k, ny);  // dims >= max|c| is checked on the host
+        zs[k + M] = wrap1(z - k, nz);
+    }
+
+    T f[Q][V];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = vel<LT>(i, 0), cy = vel<LT>(i, 1), cz = vel<LT>(i, 2);
+        const S *row = src + (long long)i * P + (long long)(zs[cz + M] * ny + ys[cy + M]) * nx;
+        S raw[V];
+        load_vec<S, V>(row + x0, raw);
+        T v[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] = decode<ST, LT>(raw[j], i);
+        if (cx == 0) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) f[i][j] = v[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int e = j - cx;  // source element relative to x0
+                const int dl = floordiv(e, V);
+                const int ei = e - dl * V;
+                if (dl == 0) {
+                    f[i][j] = v[ei];
+                } else {
+                    const int sl = lane + dl;
+                    T sh = __shfl_sync(kFull, v[ei], sl < 0 ? 0 : (sl > 31 ? 31 : sl));
+                    const bool ok = sl >= 0 && sl <= 31 && chunk + dl >= 0 && chunk + dl < ncx;
+                    if (!ok) sh = decode<ST, LT>(row[wrapn(x0 + e, nx)], i);
+                    f[i][j] = sh;
+                }
+            }
+        }
+    }
+
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        T g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = f[i][j];
+        collide<LT, K, T>(g, relax, rho0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i][j] = g[i];
+    }
+
+    if (active) {
+        S *out = dst + (long long)(z * ny + y) * nx + x0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            S raw[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) raw[j] = encode<ST, LT>(f[i][j], i);
+            store_vec<S, V>(out + (long long)i * P, raw);
+        }
+    }
+}
+
+template <class LT, int K, class ST, int V>
+cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream) {
+    using T = typename ST::T;
+    if (a.nx % V) return cudaErrorInvalidValue;
+    const int ncx = a.nx / V;
+    const long long total = (long long)ncx * a.ny;
+    if (block <= 0) block = 256;
+    if (block > 256) block = 256;  // __launch_bounds__(256)
+    const long long gx = (total + block - 1) / block;
+    if (gx > 0x7fffffffLL || a.nz > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)gx, (unsigned)a.nz);
+    step_direct_kernel<LT, K, ST, V><<<grid, block, 0, stream>>>(
+        static_cast<const typename ST::S *>(a.src), static_cast<typename ST::S *>(a.dst), a.nx, a.ny, ncx, a.P,
+        T(a.relax), T(a.rho0));
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ set_fields
+// f_i(x, 0) = f^eq_i(rho(x), u(x)) is computed in the collision's arithmetic type
+// and written to the stored field at x - c_i, so that the first pull of step 0
+// reads it back at x.
+template <class LT, int K, class ST>
+__global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__restrict__ rho,
+                            const double *__restrict__ u, long long ustride, long long c0, long long count, int nx,
+                            int ny, int nz, long long P, double rho0) {
+    using S = typename ST::S;
+    using T = typename ST::T;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long cell = c0 + k;
+        const int x = int(cell % nx);
+        const int y = int((cell / nx) % ny);
+        const int z = int(cell / ((long long)nx * ny));
+        const double r = rho[k];
+        T uu[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int a = 0; a < LT::D; ++a) uu[a] = T(u[a * ustride + k]);
+        T g[LT::Q];
+        equilibrium_shifted<LT, K, T>(T(r), T(r - rho0), uu, g);
+#pragma unroll
+        for (int i = 0; i < LT::Q; ++i) {
+            const int xs = wrapn(x - vel<LT>(i, 0), nx);
+            const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
+            const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
+            dst[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs] = encode<ST, LT>(T(g[i]), i);
+        }
+    }
+}
+
+template <class LT, int K, class ST>
+cudaError_t launch_init(const InitArgs &a, cudaStream_t stream) {
+    if (a.count <= 0) return cudaSuccess;
+    long long blocks = (a.count + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    init_kernel<LT, K, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<typename ST::S *>(a.dst), a.rho, a.u,
+                                                                  a.ustride, a.c0, a.count, a.nx, a.ny, a.nz, a.P,
+                                                                  a.rho0);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pulled observables
+// Pre-collision f_i(x, t) = g_i(x - c_i) decoded to FP64; rho and u per Eq. mme.
+template <class LT, class ST>
+__device__ __forceinline__ void pull_cell(const typename ST::S *__restrict__ src, long long cell, int nx, int ny,
+                                          int nz, long long P, double (&gt)[LT::Q]) {
+    const int x = int(cell % nx);
+    const int y = int((cell / nx) % ny);
+    const int z = int(cell / ((long long)nx * ny));
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        const int xs = wrapn(x - vel<LT>(i, 0), nx);
+        const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
+        const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
+        gt[i] = double(decode<ST, LT>(src[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs], i));
+    }
+}
+
+template <class LT, class ST>
+__global__ void moments_kernel(const typename ST::S *__restrict__ src, double *__restrict__ rho,
+                               double *__restrict__ u, double *__restrict__ f, long long ustride, long long fstride,
+                               long long c0, long long count, int nx, int ny, int nz, long long P, double rho0) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+         k += (long long)gridDim.x * blockDim.x) {
+        double gt[LT::Q];
+        pull_cell<LT, ST>(src, c0 + k, nx, ny, nz, P, gt);
+        if (f) {
+#pragma unroll
+            for (int i = 0; i < LT::Q; ++i) f[i * fstride + k] = gt[i] + weight<LT>(i) * rho0;
+        }
+        if (rho || u) {
+            double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int i = 0; i < LT::Q; ++i) {
+                dr += gt[i];
+#pragma unroll
+                for (int a = 0; a < LT::D; ++a) j[a] += double(vel<LT>(i, a)) * gt[i];
+            }
+            const double r = rho0 + dr;
+            if (rho) rho[k] = r;
+            if (u) {
+#pragma unroll
+                for (int a = 0; a < LT::D; ++a) u[a * ustride + k] = j[a] / r;
+            }
+        }
+    }
+}
+
+template <class LT, class ST>
+cudaError_t launch_moments(const PullArgs &a, cudaStream_t stream) {
+    if (a.count <= 0) return cudaSuccess;
+    long long blocks = (a.count + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    moments_kernel<LT, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const typename ST::S *>(a.src), a.rho,
+                                                                  a.u, nullptr, a.ustride, a.fstride, a.c0, a.count,
+                                                                  a.nx, a.ny, a.nz, a.P, a.rho0);
+    return cudaGetLastError();
+}
+
+template <class LT, class ST>
+cudaError_t launch_pull_f(const PullArgs &a, cudaStream_t stream) {
+    if (a.count <= 0) return cudaSuccess;
+    long long blocks = (a.count + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    moments_kernel<LT, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const typename ST::S *>(a.src), nullptr,
+                                                                  nullptr, a.f, a.ustride, a.fstride, a.c0, a.count,
+                                                                  a.nx, a.ny, a.nz, a.P, a.rho0);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FP64 reductions
+// Deterministic two-pass sums: each block reduces a fixed cell range with warp
+// shuffles and shared memory, writes its partials, and one block adds the
+// partials in block order.
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double *__restrict__ partials) {
+    __shared__ double sh[kReduceThreads / 32][NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(kFull, v[q], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[warp][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < kReduceThreads / 32; ++w) s += sh[w][q];
+            partials[blockIdx.x * NV + q] = s;
+        }
+    }
+}
+
+template <int NV>
+__global__ void final_reduce_kernel(const double *__restrict__ partials, int blocks, double *__restrict__ out) {
+    // one warp per value, lanes stride over blocks in a fixed order
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (q >= NV) return;
+    double s = 0.0;
+    for (int b = lane; b < blocks; b += 32) s += partials[b * NV + q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
+    if (lane == 0) out[q] = s;
+}
+
+// Total mass and momentum: shift-invariant sums, so the stored field is summed
+// plane by plane without pulling: sum_x rho = C rho0 + sum_i sum_y g~_i(y).
+template <class LT, class ST>
+__global__ void __launch_bounds__(kReduceThreads) conservation_kernel(const typename ST::S *__restrict__ src,
+                                                                      long long P, double rho0,
+                                                                      double *__restrict__ partials) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long per = (P + gridDim.x - 1) / gridDim.x;
+    const long long b0 = blockIdx.x * per;
+    const long long b1 = b0 + per < P ? b0 + per : P;
+    // one FP64 accumulator per velocity plane (FP64 adds are scarce on this GPU);
+    // the lattice velocities weight the plane sums once at the end
+    double acc[LT::Q];
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) acc[i] = 0.0;
+    long long n = 0;
+    for (long long k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST, LT>(src[(long long)i * P + k], i));
+        ++n;
+    }
+    v[0] = double(n) * rho0;
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) {
+        v[0] += acc[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int c = vel<LT>(i, a);
+            if (c == 1) v[1 + a] += acc[i];
+            else if (c == -1) v[1 + a] -= acc[i];
+            else if (c != 0) v[1 + a] += double(c) * acc[i];
+        }
+    }
+    block_reduce_store<4>(v, partials);
+}
+
+template <class LT, class ST>
+cudaError_t launch_conservation(const ReduceArgs &a, cudaStream_t stream) {
+    conservation_kernel<LT, ST><<<a.blocks, kReduceThreads, 0, stream>>>(static_cast<const typename ST::S *>(a.src),
+                                                                         a.P, a.rho0, a.partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    final_reduce_kernel<4><<<1, 4 * 32, 0, stream>>>(a.partials, a.blocks, a.out);
+    return cudaGetLastError();
+}
+
+// Fourier amplitude of u_comp at wave vector k (FP64, pulled moments per cell).
+template <class LT, class ST>
+__global__ void __launch_bounds__(kReduceThreads) mode_kernel(const typename ST::S *__restrict__ src, int nx, int ny,
+                                                              int nz, long long P, double rho0, int kx, int ky,
+                                                              int kz, int comp, double *__restrict__ partials) {
+    double v[2] = {0.0, 0.0};
+    const long long per = (P + gridDim.x - 1) / gridDim.x;
+    const long long b0 = blockIdx.x * per;
+    const long long b1 = b0 + per < P ? b0 + per : P;
+    for (long long cell = b0 + threadIdx.x; cell < b1; cell += blockDim.x) {
+        double gt[LT::Q];
+        pull_cell<LT, ST>(src, cell, nx, ny, nz, P, gt);
+        double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 0; i < LT::Q; ++i) {
+            dr += gt[i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) j[a] += double(vel<LT>(i, a)) * gt[i];
+        }
+        const double uc = (comp == 0 ? j[0] : (comp == 1 ? j[1] : j[2])) / (rho0 + dr);
+        const int x = int(cell % nx);
+        const int y = int((cell / nx) % ny);
+        const int z = int(cell / ((long long)nx * ny));
+        // phase / pi = 2 (kx x/nx + ky y/ny + kz z/nz), reduced modulo 2 before sincospi
+        double ph = 2.0 * ((double)((long long)kx * x % nx) / nx + (double)((long long)ky * y % ny) / ny +
+                           (double)((long long)kz * z % nz) / nz);
+        double sn, cs;
+        sincospi(ph, &sn, &cs);
+        v[0] += uc * cs;
+        v[1] -= uc * sn;
+    }
+    block_reduce_store<2>(v, partials);
+}
+
+template <class LT, class ST>
+cudaError_t launch_mode(const ReduceArgs &a, cudaStream_t stream) {
+    mode_kernel<LT, ST><<<a.blocks, kReduceThreads, 0, stream>>>(static_cast<const typename ST::S *>(a.src), a.nx,
+                                                                 a.ny, a.nz, a.P, a.rho0, a.k[0], a.k[1], a.k[2],
+                                                                 a.component, a.partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    final_reduce_kernel<2><<<1, 2 * 32, 0, stream>>>(a.partials, a.blocks, a.out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ kernel sets
+template <class LT, int K, class ST, int V>
+constexpr step_fn direct_if_built() {
+    // Register budget: at most 160 stored values per thread (80 for FP64, whose
+    // values take two registers); vectors of up to 32 bytes.
+    if constexpr (int(sizeof(typename ST::S)) * V > 32) return nullptr;
+    else if constexpr (LT::Q * V * (sizeof(typename ST::T) == 8 ? 2 : 1) > 160) return nullptr;
+    else return &launch_step_direct<LT, K, ST, V>;
+}
+
+template <class LT, int K, class ST>
+const KernelSet *make_kernel_set() {
+    static const KernelSet ks = {
+        {direct_if_built<LT, K, ST, 1>(), direct_if_built<LT, K, ST, 2>(), direct_if_built<LT, K, ST, 4>(),
+         direct_if_built<LT, K, ST, 8>()},
+        nullptr,
+        0,
+        &launch_init<LT, K, ST>,
+        &launch_moments<LT, ST>,
+        &launch_pull_f<LT, ST>,
+        &launch_conservation<LT, ST>,
+        &launch_mode<LT, ST>,
+    };
+    return &ks;
+}
+
+template <class LT, int K>
+const KernelSet *kernel_set_for_storage(lbm_storage st) {
+    switch (st) {
+    case LBM_STORE_F32: return make_kernel_set<LT, K, StoreF32>();
+    case LBM_STORE_F16: return make_kernel_set<LT, K, StoreF16>();
+    case LBM_STORE_BF16: return make_kernel_set<LT, K, StoreBF16>();
+    case LBM_STORE_F64: return make_kernel_set<LT, K, StoreF64>();
+    }
+    return nullptr;
+}
+
+}  // namespace lbm

@@ -77,6 +77,28 @@ def random_fields(dims, D, config_index=0, salt=0, drho=0.01, umax=0.05):
     return rho, u
 
 
+def random_smooth_fields(dims, D, config_index=0, salt=0, u0=0.05, drho=0.01, kmax=1):
+    """Seeded smooth fields: a sum of Fourier modes with |k_a| <= kmax per axis, random amplitudes
+    and phases, scaled so that max|u| = u0 and max|rho - 1| = drho."""
+    g = rng(config_index, 100 + salt)
+    x, y, z, n = _grid(dims)
+    C = int(np.prod(n))
+    pos = (x.reshape(C), y.reshape(C), z.reshape(C))
+
+    def field():
+        out = np.zeros(C)
+        for _ in range(6):
+            k = [int(g.integers(-kmax, kmax + 1)) if n[a] > 1 else 0 for a in range(3)]
+            ph = 2 * np.pi * sum(k[a] * pos[a] / n[a] for a in range(3)) + g.uniform(0, 2 * np.pi)
+            out += g.standard_normal() * np.cos(ph)
+        m = np.max(np.abs(out))
+        return out / m if m > 0 else out
+
+    rho = 1.0 + drho * field()
+    u = np.stack([u0 * field() for _ in range(D)])
+    return rho, u
+
+
 def random_distributions(Q, C, config_index=0, salt=0, scale=0.02):
     """Strictly positive random distributions around 1/Q, with arbitrary non-equilibrium content."""
     g = rng(config_index, salt)

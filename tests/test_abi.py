@@ -1,0 +1,103 @@
+"""The C-ABI library loads, exports every entry point include/lbm.h declares, and
+validates arguments on the host before any device work (no GPU needed).
+
+No compute call is made here: only table queries and argument rejections."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_02503_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(lbm.LIB_PATH):
+        from paper_2002_02503_gb300 import build
+        build.build()
+    return lbm.lib()
+
+
+def test_every_declared_symbol_is_exported_and_bound(L):
+    declared = _declared()
+    assert len(declared) >= 18
+    for name in declared:
+        assert hasattr(L, name), name
+    bound = {n for n, _, _ in lbm.SIGNATURES}
+    assert declared <= bound, declared - bound
+
+
+def test_lattice_tables_match_oracle_velocity_sets(L):
+    for name in lbm.LATTICES:
+        g = lbm.lbm_lattice_info(name)
+        o = oracle.lattice(name)
+        assert g["Q"] == o["Q"] and g["D"] == o["D"] and g["T0"] == o["T0"]
+        gw = {tuple(c): w for c, w in zip(g["c"], g["w"])}
+        ow = {tuple(int(v) for v in c): w for c, w in zip(o["c"], o["w"])}
+        assert gw.keys() == ow.keys()
+        for k in gw:
+            assert abs(gw[k] - ow[k]) < 1e-16
+        # pair order: rest first, then (+c, -c) adjacent
+        assert not g["c"][0].any()
+        for p in range((g["Q"] - 1) // 2):
+            np.testing.assert_array_equal(g["c"][2 * p + 1], -g["c"][2 * p + 2])
+    assert [lbm.lbm_lattice_info(n)["kmax"] for n in lbm.LATTICES] == [3, 3, 3, 5]
+
+
+def test_workspace_bytes(L):
+    n = lbm.lbm_workspace_bytes("D3Q19", (256, 256, 256), "f32")
+    assert n >= 2 * 19 * 256 ** 3 * 4
+    assert n < 2 * 19 * 256 ** 3 * 4 + (1 << 20)
+    assert lbm.lbm_workspace_bytes("D3Q19", (256, 256, 256), "f16") < n // 2 + (1 << 20)
+    assert lbm.lbm_workspace_bytes("D2Q9", (64, 64, 2), "f32") == 0  # 2-D needs nz == 1
+    assert lbm.lbm_workspace_bytes("D3Q39", (2, 8, 8), "f32") == 0   # dims >= max|c| = 3
+
+
+def _create_status(lattice="D3Q19", dims=(8, 8, 8), tau=0.6, K=3, storage="f32", rho0=1.0, ws=4096 * 256,
+                   nbytes=None):
+    h = ctypes.c_void_p()
+    if nbytes is None:
+        nbytes = 1 << 40
+    d = (ctypes.c_int64 * 3)(*dims)
+    return lbm.lib().lbm_create(lbm.LATTICES[lattice], d, tau, K, lbm.STORAGES[storage], rho0,
+                                ctypes.c_void_p(ws), nbytes, None, ctypes.byref(h)), h
+
+
+def test_create_rejects_bad_arguments_before_device_work(L):
+    assert _create_status(tau=0.5)[0] == lbm.LBM_ERR_INVALID_ARG
+    assert _create_status(tau=float("nan"))[0] == lbm.LBM_ERR_INVALID_ARG
+    assert _create_status(K=4)[0] == lbm.LBM_ERR_UNSUPPORTED        # D3Q19 supports K <= 3
+    assert _create_status(K=1)[0] == lbm.LBM_ERR_UNSUPPORTED
+    assert _create_status(lattice="D3Q39", K=6)[0] == lbm.LBM_ERR_UNSUPPORTED
+    assert _create_status(ws=0)[0] == lbm.LBM_ERR_INVALID_ARG
+    assert _create_status(ws=4096 * 256 + 8)[0] == lbm.LBM_ERR_INVALID_ARG  # misaligned
+    assert _create_status(nbytes=1024)[0] == lbm.LBM_ERR_OUT_OF_MEMORY
+    assert _create_status(lattice="D2Q9", dims=(8, 8, 2))[0] == lbm.LBM_ERR_INVALID_ARG
+    assert _create_status(lattice="D3Q39", dims=(8, 2, 8), K=4)[0] == lbm.LBM_ERR_INVALID_ARG
+    assert _create_status(rho0=0.0)[0] == lbm.LBM_ERR_INVALID_ARG
+    st, h = _create_status(tau=0.4)
+    assert h.value is None
+    assert b"tau" in lbm.lib().lbm_last_error()
+
+
+def test_null_solver_is_rejected(L):
+    assert lbm.lib().lbm_step(None, 1) == lbm.LBM_ERR_INVALID_ARG
+    assert lbm.lib().lbm_destroy(None) == lbm.LBM_OK
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_step(None, 1)
+    assert e.value.status == lbm.LBM_ERR_INVALID_ARG

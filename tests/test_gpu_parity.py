@@ -1,0 +1,246 @@
+"""Parity of the CUDA library (through its C-ABI) with the FP64 oracle.
+
+Tolerances: FP32 storage and arithmetic within 1e-5 relative after 100 steps
+(f and rho per element, u as max|du| / max|u|); FP64 storage within 1e-12;
+shifted FP16 storage within 1e-3 relative on u."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_02503_gb300 import fields, lbm
+
+from _lbmtest import (DIMS, TOL_F32, TOL_F64, oracle_reference, perm_lib_to_oracle, raw_from_f, rel_f, rel_u,
+                      to_lib_order)
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("D2Q9", 2), ("D2Q9", 3), ("D3Q19", 2), ("D3Q19", 3), ("D3Q27", 2), ("D3Q27", 3),
+         ("D3Q39", 2), ("D3Q39", 3), ("D3Q39", 4), ("D3Q39", 5)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    lbm.lib()
+    yield
+    torch.cuda.synchronize()
+
+
+def _run_gpu(name, K, tau, dims, rho, u, steps, storage, variant=None):
+    s = lbm.Solver(name, dims, tau, K, storage)
+    if variant is not None:
+        lbm.lbm_set_kernel(s.handle, *variant)
+    s.set_fields(rho, u)
+    s.step(steps)
+    r, uu = s.moments()
+    f = s.f()
+    s.close()
+    return f, r, uu
+
+
+@pytest.mark.parametrize("name,K", CASES)
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_smooth_fields_100_steps(name, K, storage):
+    """Seeded smooth fields (u0 = 0.05) keep max|u| of order u0 over the 100 steps."""
+    dims = DIMS[name]
+    D = lbm.lbm_lattice_info(name)["D"]
+    rho, u = fields.random_smooth_fields(dims, D, config_index=0, salt=K)
+    tau = 0.55
+    f_ref, r_ref, u_ref = oracle_reference(name, K, tau, dims, rho, u, 100)
+    f, r, uu = _run_gpu(name, K, tau, dims, rho, u, 100, storage)
+    tol = TOL_F32 if storage == "f32" else TOL_F64
+    assert rel_f(r, r_ref) < tol
+    assert rel_u(uu, u_ref) < tol
+    assert rel_f(f, to_lib_order(name, f_ref)) < tol
+
+
+@pytest.mark.parametrize("name,K", CASES)
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_white_noise_fields_20_steps(name, K, storage):
+    """Independent random rho, u per cell exercise every branch.  Their velocity decays by orders
+    of magnitude within ~100 steps while the FP32 absolute error stays ~1e-8, so the relative
+    check runs at 20 steps."""
+    dims = DIMS[name]
+    D = lbm.lbm_lattice_info(name)["D"]
+    rho, u = fields.random_fields(dims, D, config_index=0, salt=K)
+    tau = 0.6
+    f_ref, r_ref, u_ref = oracle_reference(name, K, tau, dims, rho, u, 20)
+    f, r, uu = _run_gpu(name, K, tau, dims, rho, u, 20, storage)
+    tol = TOL_F32 if storage == "f32" else TOL_F64
+    assert rel_f(r, r_ref) < tol
+    assert rel_u(uu, u_ref) < tol
+    assert rel_f(f, to_lib_order(name, f_ref)) < tol
+
+
+@pytest.mark.parametrize("name,K", [("D3Q19", 3), ("D3Q39", 4), ("D2Q9", 3)])
+def test_nonequilibrium_start_through_checkpoint_api(name, K):
+    """Arbitrary (non-equilibrium) distributions set through lbm_set_distributions."""
+    dims = DIMS[name]
+    info = lbm.lbm_lattice_info(name)
+    C = int(np.prod(dims))
+    f0 = fields.random_distributions(info["Q"], C, salt=7) * info["w"][:, None] * info["Q"]
+    f0_oracle = np.empty_like(f0)
+    f0_oracle[perm_lib_to_oracle(name)] = f0
+    f_ref = oracle.run(name, K, 0.7, dims, f0_oracle, 20)
+    s = lbm.Solver(name, dims, 0.7, K, "f32")
+    lbm.lbm_set_distributions(s.handle, raw_from_f(name, dims, f0, "f32"), 0)
+    np.testing.assert_allclose(s.f(), f0, rtol=1e-6)
+    s.step(20)
+    assert s.time() == 20
+    assert rel_f(s.f(), to_lib_order(name, f_ref)) < TOL_F32
+    s.close()
+
+
+def _built_variants(name, K, storage, nx):
+    out = []
+    s = lbm.Solver(name, DIMS[name], 0.6, K, storage)
+    for V in (1, 2, 4, 8):
+        for block in (64, 128, 256):
+            try:
+                lbm.lbm_set_kernel(s.handle, 0, V, block)
+                out.append((0, V, block))
+            except lbm.LbmError:
+                pass
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("name,K,storage", [("D3Q19", 3, "f32"), ("D3Q39", 4, "f32"), ("D3Q19", 2, "f16"),
+                                            ("D2Q9", 2, "f64"), ("D3Q27", 3, "bf16")])
+def test_every_kernel_configuration(name, K, storage):
+    dims = DIMS[name]
+    D = lbm.lbm_lattice_info(name)["D"]
+    rho, u = fields.random_fields(dims, D, salt=11)
+    f_ref, r_ref, u_ref = oracle_reference(name, K, 0.6, dims, rho, u, 10)
+    variants = _built_variants(name, K, storage, dims[0])
+    assert len(variants) >= 3
+    tol = {"f32": TOL_F32, "f64": TOL_F64, "f16": 2e-3, "bf16": 2e-2}[storage]
+    results = []
+    for v in variants:
+        f, r, uu = _run_gpu(name, K, 0.6, dims, rho, u, 10, storage, variant=v)
+        assert rel_u(uu, u_ref) < tol, v
+        results.append(f)
+    same = {"f32": 1e-5, "f64": 1e-13, "f16": 5e-3, "bf16": 3e-2}[storage]
+    for f in results[1:]:  # every configuration computes the same per-cell arithmetic
+        np.testing.assert_allclose(f, results[0], rtol=same)
+
+
+def test_d2q9_shear_wave_fp64_1000_steps():
+    """D2Q9 64 x 64, FP64, K = 2, tau = 0.8, u_x = 0.01 sin(2 pi y / 64), 1000 steps."""
+    dims = (64, 64, 1)
+    rho, u = fields.shear_wave(dims, 0.01, 2, 0, 1)
+    f_ref, r_ref, u_ref = oracle_reference("D2Q9", 2, 0.8, dims, rho, u, 1000)
+    f, r, uu = _run_gpu("D2Q9", 2, 0.8, dims, rho, u, 1000, "f64")
+    assert rel_u(uu, u_ref) < TOL_F64
+    assert rel_f(r, r_ref) < TOL_F64
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 1e-3), ("bf16", 1e-2)])
+def test_shifted_16bit_storage_taylor_green(storage, tol):
+    dims = (32, 32, 32)
+    rho, u = fields.taylor_green_3d(dims, 0.05, 1.0 / 3.0)
+    _, r_ref, u_ref = oracle_reference("D3Q19", 3, 0.55, dims, rho, u, 100)
+    _, r, uu = _run_gpu("D3Q19", 3, 0.55, dims, rho, u, 100, storage)
+    err = rel_u(uu, u_ref)
+    print("%s u error vs FP64 oracle after 100 steps: %.3e" % (storage, err))
+    assert err < tol
+
+
+def test_checkpoint_resume_is_bitwise():
+    name, K, dims = "D3Q27", 3, DIMS["D3Q27"]
+    rho, u = fields.random_fields(dims, 3, salt=12)
+    a = lbm.Solver(name, dims, 0.6, K, "f32")
+    a.set_fields(rho, u)
+    a.step(10)
+    raw = np.empty(a.raw_bytes(), dtype=np.uint8)
+    t = lbm.lbm_get_distributions(a.handle, raw)
+    assert t == 10
+    a.step(10)
+    final_a = np.empty_like(raw)
+    lbm.lbm_get_distributions(a.handle, final_a)
+    b = lbm.Solver(name, dims, 0.6, K, "f32")
+    lbm.lbm_set_distributions(b.handle, raw, t)
+    b.step(10)
+    final_b = np.empty_like(raw)
+    assert lbm.lbm_get_distributions(b.handle, final_b) == 20
+    np.testing.assert_array_equal(final_a, final_b)
+    a.close()
+    b.close()
+
+
+def test_conservation_and_mode_reductions_match_fields():
+    name, K, dims = "D3Q19", 3, DIMS["D3Q19"]
+    rho, u = fields.random_fields(dims, 3, salt=13)
+    s = lbm.Solver(name, dims, 0.6, K, "f32")
+    s.set_fields(rho, u)
+    s.step(5)
+    r, uu = s.moments()
+    cons = s.conservation()
+    np.testing.assert_allclose(cons[0], r.sum(), rtol=1e-12)
+    np.testing.assert_allclose(cons[1:], (r * uu).sum(1), rtol=0, atol=1e-10 * r.sum())
+    nx, ny, nz = dims
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for k, comp in [((1, 0, 0), 1), ((2, 3, 1), 0), ((0, 1, 0), 2)]:
+        ph = 2 * np.pi * (k[0] * x / nx + k[1] * y / ny + k[2] * z / nz)
+        want = np.sum(uu[comp] * np.exp(-1j * ph.reshape(-1)))
+        got = s.mode(k, comp)
+        assert abs(got - want) < 1e-10 * np.abs(uu[comp]).sum()
+    s.close()
+
+
+def test_autotune_keeps_state():
+    name, K, dims = "D3Q19", 3, (64, 32, 16)
+    rho, u = fields.random_fields(dims, 3, salt=14)
+    s = lbm.Solver(name, dims, 0.6, K, "f32")
+    s.set_fields(rho, u)
+    s.step(3)
+    before = np.empty(s.raw_bytes(), dtype=np.uint8)
+    lbm.lbm_get_distributions(s.handle, before)
+    us = lbm.lbm_autotune(s.handle, 3)
+    assert us > 0
+    after = np.empty_like(before)
+    assert lbm.lbm_get_distributions(s.handle, after) == 3
+    np.testing.assert_array_equal(before, after)
+    s.close()
+
+
+def test_unstable_run_reports_nonfinite():
+    """A Mach-1.5 start on D3Q19 with K = 2 blows up; the FP64 reduction reports it."""
+    dims = (16, 16, 16)
+    rho = np.ones(16 ** 3)
+    u = np.zeros((3, 16 ** 3))
+    u[0] = 0.9 * np.sign(np.sin(2 * np.pi * np.arange(16 ** 3) / 16 + 0.1))
+    s = lbm.Solver("D3Q19", dims, 0.5001, 2, "f32")
+    s.set_fields(rho, u)
+    s.step(400)
+    with pytest.raises(lbm.LbmError) as e:
+        s.conservation()
+    assert e.value.status == lbm.LBM_ERR_NONFINITE
+    s.close()
+
+
+def test_full_size_d3q19_256_one_step_and_conservation():
+    """The bench configuration (D3Q19 256^3 FP32 Taylor-Green, u0 = 0.05, tau = 0.55, K = 2) in the
+    launch configuration the benchmark uses: one step compared with the oracle on the full field,
+    then 1000 steps of mass and momentum conservation."""
+    dims = (256, 256, 256)
+    rho, u = fields.taylor_green_3d(dims, 0.05, 1.0 / 3.0)
+    s = lbm.Solver("D3Q19", dims, 0.55, 2, "f32")
+    s.set_fields(rho, u)
+    c0 = s.conservation()
+    s.step(1)
+    r, uu = s.moments()
+    f0 = oracle.init_eq("D3Q19", 2, dims, rho, u)
+    f1 = oracle.run("D3Q19", 2, 0.55, dims, f0, 1)
+    del f0
+    r_ref, u_ref = oracle.moments("D3Q19", dims, f1)
+    del f1
+    assert rel_f(r, r_ref) < TOL_F32
+    assert rel_u(uu, u_ref) < TOL_F32
+    s.step(999)
+    c1 = s.conservation()
+    assert abs(c1[0] - c0[0]) < 1e-7 * c0[0]
+    assert np.max(np.abs(c1[1:] - c0[1:])) < 1e-7 * c0[0]
+    s.close()
