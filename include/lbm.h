@@ -140,6 +140,27 @@ lbm_status lbm_get_kernel(const lbm_solver *s, int *variant, int *cells_per_thre
  * NULL, receives the average step time of the chosen configuration. */
 lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us);
 
+/* Global FP64 sums {sum rho, sum rho u_x, sum rho u_y, sum rho u_z} of stored
+ * distributions the caller passes in, for callers that cannot allocate device
+ * memory: a plugin whose host framework owns all device memory through its own
+ * pool, a process whose memory another allocator has fully reserved, or a
+ * latency-critical loop where an allocation (which may synchronise the device)
+ * is forbidden.  It needs no solver and no workspace, and it calls no
+ * cudaMalloc, cudaFree or other allocating routine.  The paper has no
+ * counterpart to this call: it is a deployment convenience.
+ *   distributions  device pointer to Q*nx*ny*nz stored values in the layout
+ *                  lbm_get_distributions produces (any solver's raw state)
+ *   out            four doubles, host or device memory as out_mem says; a host
+ *                  output makes the call synchronise the stream
+ * Scratch: a fixed device array inside the library (about 128 KiB per GPU that
+ * loads it, held until the process exits) with room for nz <= 4096 z-planes;
+ * larger nz is rejected with LBM_ERR_INVALID_ARG.  The first call on a device
+ * looks up that array's device address, so make it before any stream capture.
+ * All calls share the array: calls whose GPU work overlaps race on it and must
+ * be serialised by the caller. */
+lbm_status lbm_conservation_noalloc(lbm_lattice lattice, lbm_storage storage, const int64_t dims[3], double rho0,
+                                   const void *distributions, double out[4], lbm_mem out_mem, void *cuda_stream);
+
 /* Release the solver (not the workspace).  Synchronises its stream. */
 lbm_status lbm_destroy(lbm_solver *s);
 

@@ -114,6 +114,11 @@ std::string dims_problem(const LatInfo &li, const int64_t *dims) {
 
 }  // namespace
 
+namespace lbm {
+// Records a message for lbm_last_error (used by the other C-ABI units).
+lbm_status set_error(lbm_status s, const char *msg) { return fail(s, "%s", msg); }
+}  // namespace lbm
+
 struct lbm_solver {
     lbm_lattice lat;
     LatInfo li;

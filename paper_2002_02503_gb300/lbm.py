@@ -43,6 +43,7 @@ SIGNATURES = [
     ("lbm_set_kernel", _c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int]),
     ("lbm_get_kernel", _c.c_int, [_P, _IP, _IP, _IP]),
     ("lbm_autotune", _c.c_int, [_P, _c.c_int, _DP]),
+    ("lbm_conservation_noalloc", _c.c_int, [_c.c_int, _c.c_int, _I64P, _c.c_double, _P, _P, _c.c_int, _P]),
     ("lbm_destroy", _c.c_int, [_P]),
     ("lbm_status_string", _c.c_char_p, [_c.c_int]),
     ("lbm_last_error", _c.c_char_p, []),
@@ -209,6 +210,18 @@ def lbm_autotune(h, iters=10):
     us = ctypes.c_double()
     _check(lib().lbm_autotune(h, int(iters), ctypes.byref(us)))
     return us.value
+
+
+def lbm_conservation_noalloc(lattice, storage, dims, rho0, distributions, out, stream_ptr=0):
+    """Allocation-free conservation sums over caller-owned stored distributions (device).
+
+    ``out``: a float64 array/tensor of 4 elements (host or device)."""
+    pd, md = _ptr(distributions)
+    if md != MEM_DEVICE:
+        raise ValueError("distributions must be device memory")
+    po, mo = _ptr(out)
+    _check(lib().lbm_conservation_noalloc(_lat(lattice), _st(storage), _dims(dims), float(rho0), pd, po, mo,
+                                          ctypes.c_void_p(stream_ptr)))
 
 
 def lbm_destroy(h):
