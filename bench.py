@@ -51,7 +51,56 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    p.add_argument("--no-extras", action="store_true", help="skip the per-lattice and serving measurements")
+    p.add_argument("--serve", type=int, default=200,
+                   help="requests of the serving trace (2000 = the full Poisson workload; 0 = skip)")
+    p.add_argument("--serve-rate", type=float, default=50.0)
+    p.add_argument("--extra-steps", type=int, default=200)
     return p.parse_args()
+
+
+# (lattice, dims, K, storage, tau, u0): the other lattices and storages of the workload family
+PER_LATTICE = [
+    ("D3Q19", (256, 256, 256), 3, "f32", 0.55, 0.05),
+    ("D3Q27", (192, 192, 192), 3, "f32", 0.6, 0.05),
+    ("D3Q39", (192, 192, 192), 4, "f32", 0.6, 0.05),
+    ("D3Q19", (512, 512, 512), 2, "f32", 0.52, 0.05),
+    ("D3Q19", (512, 512, 512), 2, "f16", 0.52, 0.05),
+    ("D3Q19", (512, 512, 512), 2, "bf16", 0.52, 0.05),
+]
+
+
+def measure_lattice(lattice, dims, K, storage, tau, u0, steps, stream):
+    """Autotuned MLUPS and HBM fraction of one configuration (CUDA events on the solver stream)."""
+    import torch
+
+    from paper_2002_02503_gb300 import fields, lbm
+
+    rho, u = fields.taylor_green_3d(dims, u0, LATTICE_T0[lattice])
+    s = lbm.Solver(lattice, dims, tau, K, storage, stream=stream)
+    s.set_fields(rho, u)
+    del rho, u
+    lbm.lbm_autotune(s.handle, 10)
+    variant, cpt, block = lbm.lbm_get_kernel(s.handle)
+    s.step(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    C = int(np.prod(dims))
+    bpu = 2 * LATTICE_Q[lattice] * STORE_BYTES[storage]
+    peak, _ = measured_peak()
+    mlups = C * steps / (ms / 1e3) / 1e6
+    return {"workload": "%s %dx%dx%d %s K=%d" % (lattice, dims[0], dims[1], dims[2], storage, K),
+            "MLUPS": mlups, "bytes_per_update": bpu, "achieved_GBs": mlups * 1e6 * bpu / 1e9,
+            "frac_of_measured_hbm": mlups * 1e6 * bpu / 1e9 / peak, "ms_per_step": ms / steps,
+            "kernel": {"variant": variant, "cells_per_thread": cpt, "block": block}}
 
 
 def workload_name(a):
@@ -318,6 +367,20 @@ def run_ours(a):
         cpu = None
         if not a.no_cpu_baseline:
             cpu = oracle_sample(a, a.cpu_seconds)
+        extras = {}
+        if not a.no_extras:
+            with torch.cuda.stream(stream):
+                extras["per_lattice"] = [measure_lattice(*cfg, a.extra_steps, stream) for cfg in PER_LATTICE]
+            if a.serve > 0:
+                from paper_2002_02503_gb300 import serve
+
+                trace = serve.make_trace(a.serve, rate=a.serve_rate)
+                pool_stats, _ = serve.serve_pool(trace)
+                plain_stats, _ = serve.serve_plain(trace)
+                extras["serving"] = {
+                    "workload": "%d D3Q19 Taylor-Green solves, side log-uniform 32-128, tau U[0.52,1], "
+                                "u0 U[0.01,0.08], 100-2000 steps, Poisson %g/s, FP32, K=3" % (a.serve, a.serve_rate),
+                    "pool": pool_stats, "plain_fifo": plain_stats}
         out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": DTYPE_NAME[a.storage], "data": "synthetic (Taylor-Green initial field)",
@@ -326,6 +389,7 @@ def run_ours(a):
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps,
                "clocks": clocks.summary(),
                "conservation": {"mass": cons[0], "momentum": list(cons[1:])}}
+        out.update(extras)
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -164,6 +164,59 @@ lbm_status lbm_conservation_noalloc(lbm_lattice lattice, lbm_storage storage, co
 /* Release the solver (not the workspace).  Synchronises its stream. */
 lbm_status lbm_destroy(lbm_solver *s);
 
+/* ------------------------------------------------------------------------
+ * Pool: many independent periodic lattices (uneven sizes, own tau and rho0,
+ * own step budget) advanced together -- each launch of the persistent batch
+ * kernel performs one step of Eq. lbe-reg on every resident lattice -- with
+ * admission by device memory and continuous batching: requests join and leave
+ * at chunk boundaries while the others keep running.  One pool serves one
+ * (lattice, truncation order, storage) class.  The per-lattice arithmetic is the
+ * single-lattice step's; results do not depend on what else is resident.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_pool lbm_pool;
+
+/* Device bytes one request of these dims occupies in a pool's arena. */
+size_t lbm_pool_request_bytes(lbm_lattice lattice, const int64_t dims[3], lbm_storage storage);
+
+/* arena: caller-owned device memory (256-byte aligned) that the pool carves
+ * request buffers from; max_slots bounds the resident requests.  compute_stream
+ * runs the batched steps, io_stream the uploads and result downloads (either may
+ * be NULL; distinct non-NULL streams let transfers overlap the steps). */
+lbm_status lbm_pool_create(lbm_lattice lattice, int truncation_order, lbm_storage storage, void *arena,
+                           size_t arena_bytes, int max_slots, void *compute_stream, void *io_stream, lbm_pool **out);
+
+/* Admit one solve: f = f^eq(rho, u) (Eq. hermite) on a periodic lattice of dims,
+ * to be advanced `steps` steps.  rho: double[C], u: double[D][C], in memory `mem`.
+ * The inputs are consumed before the call returns.  LBM_ERR_BUSY when the arena
+ * or the slot count has no room now (retry after results are collected). */
+lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, double rho0, const double *rho,
+                           const double *u, lbm_mem mem, int64_t steps, int64_t *id);
+
+/* Launch the next chunk of up to chunk_steps steps for every resident, unfinished
+ * request (asynchronous; at most two chunks are in flight).  active receives the
+ * number of requests in the launched chunk (0: nothing to do). */
+lbm_status lbm_pool_advance(lbm_pool *p, int64_t chunk_steps, int *active);
+
+/* done = 1 once the request's last step has completed on the device. */
+lbm_status lbm_pool_poll(lbm_pool *p, int64_t id, int *done, int64_t *steps_done);
+
+/* For a done request: rho and u after its steps (Eq. mme, pre-collision state),
+ * then the request's memory returns to the arena.  Synchronises the io stream. */
+lbm_status lbm_pool_result(lbm_pool *p, int64_t id, double *rho, double *u, lbm_mem mem);
+
+/* Wait for every launched chunk. */
+lbm_status lbm_pool_sync(lbm_pool *p);
+
+/* Free arena bytes, resident requests, and requests done but not collected. */
+lbm_status lbm_pool_stats(const lbm_pool *p, size_t *free_bytes, int *resident, int *done);
+
+/* Autotuner for the batch kernel: times each built block size on the current
+ * resident set (state unchanged) and keeps the fastest.  best_us: time per step. */
+lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us);
+
+/* Release the pool (not the arena).  Synchronises both streams. */
+lbm_status lbm_pool_destroy(lbm_pool *p);
+
 const char *lbm_status_string(lbm_status status);
 const char *lbm_last_error(void);
 

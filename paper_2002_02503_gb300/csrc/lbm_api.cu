@@ -117,6 +117,24 @@ std::string dims_problem(const LatInfo &li, const int64_t *dims) {
 namespace lbm {
 // Records a message for lbm_last_error (used by the other C-ABI units).
 lbm_status set_error(lbm_status s, const char *msg) { return fail(s, "%s", msg); }
+lbm_status set_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+
+bool lattice_query(lbm_lattice lat, int *D, int *Q, int *maxc, int *kmax) {
+    LatInfo li;
+    if (!lattice_info(lat, &li)) return false;
+    *D = li.D;
+    *Q = li.Q;
+    *maxc = li.maxc;
+    *kmax = li.kmax;
+    return true;
+}
+size_t storage_bytes(lbm_storage st) { return storage_size(st); }
+const KernelSet *kernel_set(lbm_lattice lat, int K, lbm_storage st) { return kernels_for(lat, K, st); }
+std::string dims_check(lbm_lattice lat, const int64_t *dims) {
+    LatInfo li;
+    if (!lattice_info(lat, &li)) return "unknown lattice";
+    return dims_problem(li, dims);
+}
 }  // namespace lbm
 
 struct lbm_solver {

@@ -1,0 +1,600 @@
+// lbm_batch.cu -- the pool of include/lbm.h: many independent periodic lattices
+// advanced together by the persistent batch kernel, admitted by device memory
+// and batched continuously (requests join and leave at chunk boundaries).
+//
+// Execution model
+//   compute stream : per chunk, an H2D copy of the slot table then one graph of
+//                    `chunk` batch-kernel launches (step_index 0..chunk-1).  Each
+//                    launch is one step of every resident lattice that still has
+//                    steps left; the kernel boundary is the step's global barrier.
+//   io stream      : fields upload + f^eq initialisation of new requests, and the
+//                    pull of rho, u of finished ones, overlapping the chunks.
+// The slot table and its pinned host mirror are double-buffered, so at most two
+// chunks are in flight.  Step counts are scheduled on the host: a request's
+// parity and remaining steps after each chunk are known without reading back.
+#include <cuda_runtime.h>
+
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr int kEventRing = 64;
+
+struct Arena {
+    char *base = nullptr;
+    size_t bytes = 0;
+    std::map<size_t, size_t> free_;  // offset -> size, coalesced
+
+    void init(char *b, size_t n) {
+        base = b;
+        bytes = n;
+        free_.clear();
+        if (n) free_[0] = n;
+    }
+    bool alloc(size_t n, size_t *off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *off = it->first;
+                const size_t rest = it->second - n;
+                const size_t roff = it->first + n;
+                free_.erase(it);
+                if (rest) free_[roff] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t free_bytes() const {
+        size_t s = 0;
+        for (auto &kv : free_) s += kv.second;
+        return s;
+    }
+};
+
+struct Request {
+    int64_t id;
+    int nx, ny, nz;
+    long long C;
+    double relax, rho0;
+    int64_t steps_total, steps_sched;  // steps launched so far
+    int parity;                        // buffer holding the state after the launched steps
+    size_t off, bytes;
+    void *buf[2];
+    bool waited_init;                  // compute stream already waits on its init event
+    cudaEvent_t init_event;
+    long long finish_chunk;            // chunk counter of its last step (-1 while running)
+};
+
+}  // namespace
+
+struct lbm_pool {
+    lbm_lattice lat;
+    int K;
+    lbm_storage st;
+    int D, Q, maxc;
+    size_t ssize;
+    const KernelSet *ks;
+    Arena arena;
+    int max_slots;
+    cudaStream_t compute, io, capture;
+    bool own_io;
+    int block, grid;
+    // double-buffered slot tables
+    BatchSlot *d_table[2];
+    int *d_header[2];
+    BatchSlot *h_table[2];
+    int *h_header[2];
+    void *d_meta;  // one allocation-free region: carved from the arena's tail
+    std::map<int64_t, Request> reqs;
+    std::vector<int64_t> order;       // resident request ids in admission order
+    int64_t next_id;
+    long long chunks;                 // chunks launched
+    long long completed;              // all chunks < completed are known done
+    cudaEvent_t chunk_events[kEventRing];
+    std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;  // (chunk length, table buffer)
+    std::mutex mu;
+};
+
+namespace {
+
+lbm_status ensure_completed(lbm_pool *p, long long upto_exclusive, bool wait) {
+    while (p->completed < upto_exclusive) {
+        cudaEvent_t ev = p->chunk_events[p->completed % kEventRing];
+        cudaError_t e = wait ? cudaEventSynchronize(ev) : cudaEventQuery(ev);
+        if (e == cudaErrorNotReady) return LBM_OK;
+        if (e != cudaSuccess) return set_cuda_error(e, "pool: chunk event");
+        p->completed += 1;
+    }
+    return LBM_OK;
+}
+
+size_t request_bytes(int Q, size_t ssize, long long C) { return 2 * align_up(size_t(C) * Q * ssize); }
+
+lbm_status get_graph(lbm_pool *p, long long chunk, int b, cudaGraphExec_t *out) {
+    auto key = std::make_pair(chunk, b);
+    auto it = p->graphs.find(key);
+    if (it != p->graphs.end()) {
+        *out = it->second;
+        return LBM_OK;
+    }
+    cudaError_t e = cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: begin capture");
+    cudaError_t le = cudaSuccess;
+    for (long long s = 0; s < chunk && le == cudaSuccess; ++s)
+        le = p->ks->batch(p->d_table[b], p->d_header[b], int(s), p->grid, p->block, p->capture);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(p->capture, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return set_cuda_error(le, "pool: capture launch");
+    }
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: end capture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: instantiate");
+    p->graphs[key] = ex;
+    *out = ex;
+    return LBM_OK;
+}
+
+void drop_graphs(lbm_pool *p) {
+    for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
+    p->graphs.clear();
+}
+
+lbm_status set_geometry(lbm_pool *p, int block) {
+    int occ = p->ks->batch_occupancy(block);
+    if (occ <= 0) return set_error(LBM_ERR_CUDA, "pool: batch kernel occupancy query failed");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: device query");
+    p->block = block;
+    p->grid = occ * sms;
+    drop_graphs(p);
+    return LBM_OK;
+}
+
+// Writes the table of resident requests with steps left into buffer b; returns slot count.
+int build_table(lbm_pool *p, int b, int *units_total) {
+    int n = 0, units = 0;
+    for (int64_t id : p->order) {
+        Request &r = p->reqs[id];
+        const int64_t left = r.steps_total - r.steps_sched;
+        if (left <= 0) continue;
+        BatchSlot &s = p->h_table[b][n];
+        s.buf[0] = r.buf[0];
+        s.buf[1] = r.buf[1];
+        s.nx = r.nx;
+        s.ny = r.ny;
+        s.nz = r.nz;
+        s.ncx = r.nx;  // V = 1
+        s.P = r.C;
+        s.relax = r.relax;
+        s.rho0 = r.rho0;
+        s.parity = r.parity;
+        s.steps_left = int(std::min<int64_t>(left, 1 << 30));
+        s.unit0 = units;
+        s.units = int((r.C + p->block - 1) / p->block);
+        units += s.units;
+        ++n;
+    }
+    p->h_header[b][0] = units;
+    p->h_header[b][1] = n;
+    *units_total = units;
+    return n;
+}
+
+lbm_status pull_to(lbm_pool *p, Request &r, double *rho, double *u, lbm_mem mem) {
+    const int cur = r.parity;
+    PullArgs a;
+    a.src = r.buf[cur];
+    a.nx = r.nx;
+    a.ny = r.ny;
+    a.nz = r.nz;
+    a.P = r.C;
+    a.rho0 = r.rho0;
+    a.f = nullptr;
+    cudaError_t e;
+    if (mem == LBM_MEM_DEVICE) {
+        a.rho = rho;
+        a.u = u;
+        a.ustride = r.C;
+        a.fstride = r.C;
+        a.c0 = 0;
+        a.count = r.C;
+        e = p->ks->moments(a, p->io);
+        if (e != cudaSuccess) return set_cuda_error(e, "pool: moments");
+    } else {
+        double *stage = static_cast<double *>(r.buf[cur ^ 1]);
+        const size_t cap = align_up(size_t(r.C) * p->Q * p->ssize);
+        const int per_cell = (rho ? 1 : 0) + (u ? p->D : 0);
+        if (per_cell == 0) return LBM_OK;
+        const long long per = (long long)(cap / (sizeof(double) * per_cell));
+        for (long long c0 = 0; c0 < r.C; c0 += per) {
+            const long long n = std::min(per, r.C - c0);
+            a.rho = rho ? stage : nullptr;
+            a.u = u ? stage + (rho ? n : 0) : nullptr;
+            a.ustride = n;
+            a.fstride = n;
+            a.c0 = c0;
+            a.count = n;
+            e = p->ks->moments(a, p->io);
+            if (e != cudaSuccess) return set_cuda_error(e, "pool: moments");
+            if (rho) {
+                e = cudaMemcpyAsync(rho + c0, a.rho, n * sizeof(double), cudaMemcpyDeviceToHost, p->io);
+                if (e != cudaSuccess) return set_cuda_error(e, "pool: copy rho");
+            }
+            if (u)
+                for (int d = 0; d < p->D; ++d) {
+                    e = cudaMemcpyAsync(u + (long long)d * r.C + c0, a.u + (long long)d * n, n * sizeof(double),
+                                        cudaMemcpyDeviceToHost, p->io);
+                    if (e != cudaSuccess) return set_cuda_error(e, "pool: copy u");
+                }
+        }
+    }
+    e = cudaStreamSynchronize(p->io);
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: io synchronize");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_pool_request_bytes(lbm_lattice lat, const int64_t dims[3], lbm_storage st) {
+    int D, Q, maxc, kmax;
+    if (!lattice_query(lat, &D, &Q, &maxc, &kmax) || storage_bytes(st) == 0) return 0;
+    if (!dims_check(lat, dims).empty()) return 0;
+    return request_bytes(Q, storage_bytes(st), (long long)dims[0] * dims[1] * dims[2]);
+}
+
+lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, size_t arena_bytes, int max_slots,
+                           void *compute_stream, void *io_stream, lbm_pool **out) {
+    if (!out) return set_error(LBM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int D, Q, maxc, kmax;
+    if (!lattice_query(lat, &D, &Q, &maxc, &kmax)) return set_error(LBM_ERR_INVALID_ARG, "unknown lattice");
+    if (storage_bytes(st) == 0) return set_error(LBM_ERR_UNSUPPORTED, "unknown storage");
+    if (K < 2 || K > kmax) return set_error(LBM_ERR_UNSUPPORTED, "truncation order outside [2, 2N-1]");
+    if (!arena || reinterpret_cast<uintptr_t>(arena) % kAlign)
+        return set_error(LBM_ERR_INVALID_ARG, "arena must be non-NULL and 256-byte aligned");
+    if (max_slots < 1 || max_slots > 65536) return set_error(LBM_ERR_INVALID_ARG, "max_slots out of range");
+    const size_t meta = 2 * align_up(sizeof(BatchSlot) * max_slots) + 2 * kAlign;
+    if (arena_bytes < meta + kAlign) return set_error(LBM_ERR_OUT_OF_MEMORY, "arena too small for the slot tables");
+    const KernelSet *ks = kernel_set(lat, K, st);
+    if (!ks || !ks->batch) return set_error(LBM_ERR_UNSUPPORTED, "no batch kernel built for this class");
+
+    lbm_pool *p = new lbm_pool();
+    p->lat = lat;
+    p->K = K;
+    p->st = st;
+    p->D = D;
+    p->Q = Q;
+    p->maxc = maxc;
+    p->ssize = storage_bytes(st);
+    p->ks = ks;
+    p->max_slots = max_slots;
+    p->compute = static_cast<cudaStream_t>(compute_stream);
+    p->io = static_cast<cudaStream_t>(io_stream);
+    p->own_io = false;
+    p->next_id = 1;
+    p->chunks = 0;
+    p->completed = 0;
+    // tables live at the tail of the arena: the pool allocates no device memory itself
+    char *base = static_cast<char *>(arena);
+    const size_t tab = align_up(sizeof(BatchSlot) * max_slots);
+    char *tail = base + (arena_bytes - meta) / kAlign * kAlign;
+    p->d_table[0] = reinterpret_cast<BatchSlot *>(tail);
+    p->d_table[1] = reinterpret_cast<BatchSlot *>(tail + tab);
+    p->d_header[0] = reinterpret_cast<int *>(tail + 2 * tab);
+    p->d_header[1] = reinterpret_cast<int *>(tail + 2 * tab + kAlign);
+    p->arena.init(base, size_t(tail - base));
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaMallocHost(reinterpret_cast<void **>(&p->h_table[b]), sizeof(BatchSlot) * max_slots);
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&p->h_header[b]), 2 * sizeof(int));
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking);
+    for (int k = 0; k < kEventRing && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&p->chunk_events[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        lbm_pool_destroy(p);
+        return set_cuda_error(e, "pool: host setup");
+    }
+    lbm_status rs = set_geometry(p, 256);
+    if (rs != LBM_OK) {
+        lbm_pool_destroy(p);
+        return rs;
+    }
+    *out = p;
+    return LBM_OK;
+}
+
+lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, double rho0, const double *rho,
+                           const double *u, lbm_mem mem, int64_t steps, int64_t *id) {
+    if (!p || !dims || !rho || !u || !id) return set_error(LBM_ERR_INVALID_ARG, "pool, dims, rho, u, id required");
+    std::lock_guard<std::mutex> lock(p->mu);
+    std::string dp = dims_check(p->lat, dims);
+    if (!dp.empty()) return set_error(LBM_ERR_INVALID_ARG, dp.c_str());
+    if (!(tau > 0.5) || !isfinite(tau)) return set_error(LBM_ERR_INVALID_ARG, "tau must be finite and > 1/2");
+    if (!(rho0 > 0.0) || !isfinite(rho0)) return set_error(LBM_ERR_INVALID_ARG, "rho0 must be > 0");
+    if (steps < 0) return set_error(LBM_ERR_INVALID_ARG, "steps must be >= 0");
+    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return set_error(LBM_ERR_INVALID_ARG, "bad lbm_mem");
+    if ((int)p->reqs.size() >= p->max_slots) return set_error(LBM_ERR_BUSY, "pool: all slots in use");
+    Request r;
+    r.nx = int(dims[0]);
+    r.ny = int(dims[1]);
+    r.nz = int(dims[2]);
+    r.C = (long long)dims[0] * dims[1] * dims[2];
+    r.relax = 1.0 - 1.0 / tau;
+    r.rho0 = rho0;
+    r.steps_total = steps;
+    r.steps_sched = 0;
+    r.parity = 0;
+    r.bytes = request_bytes(p->Q, p->ssize, r.C);
+    if (!p->arena.alloc(r.bytes, &r.off)) return set_error(LBM_ERR_BUSY, "pool: arena has no room for this request");
+    r.buf[0] = p->arena.base + r.off;
+    r.buf[1] = p->arena.base + r.off + r.bytes / 2;
+    r.waited_init = false;
+    r.finish_chunk = steps == 0 ? p->chunks - 1 : -1;
+    cudaError_t e = cudaEventCreateWithFlags(&r.init_event, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        p->arena.release(r.off, r.bytes);
+        return set_cuda_error(e, "pool: event");
+    }
+    InitArgs a;
+    a.dst = r.buf[0];
+    a.nx = r.nx;
+    a.ny = r.ny;
+    a.nz = r.nz;
+    a.P = r.C;
+    a.rho0 = rho0;
+    if (mem == LBM_MEM_DEVICE) {
+        a.rho = rho;
+        a.u = u;
+        a.ustride = r.C;
+        a.c0 = 0;
+        a.count = r.C;
+        e = p->ks->init(a, p->io);
+    } else {
+        double *stage = static_cast<double *>(r.buf[1]);
+        const long long per = (long long)((r.bytes / 2) / (sizeof(double) * (1 + p->D)));
+        for (long long c0 = 0; c0 < r.C && e == cudaSuccess; c0 += per) {
+            const long long n = std::min(per, r.C - c0);
+            e = cudaMemcpyAsync(stage, rho + c0, n * sizeof(double), cudaMemcpyHostToDevice, p->io);
+            for (int d = 0; d < p->D && e == cudaSuccess; ++d)
+                e = cudaMemcpyAsync(stage + (1 + d) * n, u + (long long)d * r.C + c0, n * sizeof(double),
+                                    cudaMemcpyHostToDevice, p->io);
+            a.rho = stage;
+            a.u = stage + n;
+            a.ustride = n;
+            a.c0 = c0;
+            a.count = n;
+            if (e == cudaSuccess) e = p->ks->init(a, p->io);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(r.init_event, p->io);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->io);  // host inputs consumed before returning
+    if (e != cudaSuccess) {
+        cudaEventDestroy(r.init_event);
+        p->arena.release(r.off, r.bytes);
+        return set_cuda_error(e, "pool: upload");
+    }
+    r.id = p->next_id++;
+    p->reqs[r.id] = r;
+    p->order.push_back(r.id);
+    *id = r.id;
+    return LBM_OK;
+}
+
+lbm_status lbm_pool_advance(lbm_pool *p, int64_t chunk, int *active) {
+    if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    if (chunk < 1 || chunk > 100000) return set_error(LBM_ERR_INVALID_ARG, "chunk_steps out of range");
+    std::lock_guard<std::mutex> lock(p->mu);
+    if (active) *active = 0;
+    const int b = int(p->chunks & 1);
+    // table buffer b was last used by chunk (chunks - 2): wait until every chunk before
+    // (chunks - 1) has completed (this also keeps the event ring from overrunning)
+    lbm_status rs = ensure_completed(p, p->chunks - 1, true);
+    if (rs != LBM_OK) return rs;
+    int units = 0;
+    const int n = build_table(p, b, &units);
+    if (n == 0) return LBM_OK;
+    cudaError_t e = cudaSuccess;
+    for (int64_t id : p->order) {
+        Request &r = p->reqs[id];
+        if (!r.waited_init && r.steps_total > r.steps_sched) {
+            e = cudaStreamWaitEvent(p->compute, r.init_event, 0);
+            if (e != cudaSuccess) return set_cuda_error(e, "pool: wait init");
+            r.waited_init = true;
+        }
+    }
+    e = cudaMemcpyAsync(p->d_table[b], p->h_table[b], sizeof(BatchSlot) * n, cudaMemcpyHostToDevice, p->compute);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], 2 * sizeof(int), cudaMemcpyHostToDevice, p->compute);
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: table upload");
+    cudaGraphExec_t g;
+    rs = get_graph(p, chunk, b, &g);
+    if (rs != LBM_OK) return rs;
+    e = cudaGraphLaunch(g, p->compute);
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: graph launch");
+    e = cudaEventRecord(p->chunk_events[p->chunks % kEventRing], p->compute);
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: chunk event");
+    for (int64_t id : p->order) {
+        Request &r = p->reqs[id];
+        const int64_t left = r.steps_total - r.steps_sched;
+        if (left <= 0) continue;
+        const int64_t done = std::min<int64_t>(left, chunk);
+        r.steps_sched += done;
+        r.parity ^= int(done & 1);
+        if (r.steps_sched == r.steps_total) r.finish_chunk = p->chunks;
+    }
+    p->chunks += 1;
+    if (active) *active = n;
+    return LBM_OK;
+}
+
+lbm_status lbm_pool_poll(lbm_pool *p, int64_t id, int *done, int64_t *steps_done) {
+    if (!p || !done) return set_error(LBM_ERR_INVALID_ARG, "pool and done are required");
+    std::lock_guard<std::mutex> lock(p->mu);
+    auto it = p->reqs.find(id);
+    if (it == p->reqs.end()) return set_error(LBM_ERR_NOT_FOUND, "unknown request id");
+    lbm_status rs = ensure_completed(p, p->chunks, false);
+    if (rs != LBM_OK) return rs;
+    const Request &r = it->second;
+    *done = (r.finish_chunk >= -1 && r.steps_sched == r.steps_total && r.finish_chunk < p->completed) ? 1 : 0;
+    if (steps_done) *steps_done = *done ? r.steps_total : r.steps_sched;
+    return LBM_OK;
+}
+
+lbm_status lbm_pool_result(lbm_pool *p, int64_t id, double *rho, double *u, lbm_mem mem) {
+    if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return set_error(LBM_ERR_INVALID_ARG, "bad lbm_mem");
+    std::lock_guard<std::mutex> lock(p->mu);
+    auto it = p->reqs.find(id);
+    if (it == p->reqs.end()) return set_error(LBM_ERR_NOT_FOUND, "unknown request id");
+    Request &r = it->second;
+    if (r.steps_sched != r.steps_total) return set_error(LBM_ERR_BUSY, "request has steps left");
+    cudaError_t e = cudaStreamWaitEvent(p->io, r.init_event, 0);
+    if (e == cudaSuccess && r.finish_chunk >= 0)
+        e = cudaStreamWaitEvent(p->io, p->chunk_events[r.finish_chunk % kEventRing], 0);
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: order result");
+    if (r.finish_chunk >= 0 && r.finish_chunk + kEventRing <= p->chunks) {
+        // its chunk event was reused by a later chunk; later completion implies this one
+        lbm_status rs = ensure_completed(p, r.finish_chunk + 1, true);
+        if (rs != LBM_OK) return rs;
+    }
+    lbm_status rs = pull_to(p, r, rho, u, mem);
+    if (rs != LBM_OK) return rs;
+    cudaEventDestroy(r.init_event);
+    p->arena.release(r.off, r.bytes);
+    p->order.erase(std::find(p->order.begin(), p->order.end(), id));
+    p->reqs.erase(it);
+    return LBM_OK;
+}
+
+lbm_status lbm_pool_sync(lbm_pool *p) {
+    if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    std::lock_guard<std::mutex> lock(p->mu);
+    return ensure_completed(p, p->chunks, true);
+}
+
+lbm_status lbm_pool_stats(const lbm_pool *p, size_t *free_bytes, int *resident, int *done) {
+    if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    if (free_bytes) *free_bytes = p->arena.free_bytes();
+    int res = 0, dn = 0;
+    for (auto &kv : p->reqs) {
+        ++res;
+        if (kv.second.steps_sched == kv.second.steps_total && kv.second.finish_chunk < p->completed) ++dn;
+    }
+    if (resident) *resident = res;
+    if (done) *done = dn;
+    return LBM_OK;
+}
+
+lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us) {
+    if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    if (iters < 1) iters = 1;
+    std::lock_guard<std::mutex> lock(p->mu);
+    lbm_status rs = ensure_completed(p, p->chunks, true);
+    if (rs != LBM_OK) return rs;
+    const int b = int(p->chunks & 1);
+    int units = 0;
+    // step_index 0 with steps_left >= 1: every launch re-reads the current state and rewrites the idle
+    // buffer, so the state is unchanged
+    const int n = build_table(p, b, &units);
+    if (n == 0) return set_error(LBM_ERR_INVALID_ARG, "pool: no resident request to tune on");
+    cudaError_t e = cudaMemcpyAsync(p->d_table[b], p->h_table[b], sizeof(BatchSlot) * n, cudaMemcpyHostToDevice,
+                                    p->compute);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], 2 * sizeof(int), cudaMemcpyHostToDevice, p->compute);
+    for (int64_t id : p->order) {
+        Request &r = p->reqs[id];
+        if (!r.waited_init && e == cudaSuccess) e = cudaStreamWaitEvent(p->compute, r.init_event, 0);
+    }
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: autotune setup");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_block = p->block;
+    for (int block : {128, 256}) {
+        rs = set_geometry(p, block);
+        if (rs != LBM_OK) break;
+        build_table(p, b, &units);  // units depend on the block size
+        e = cudaMemcpyAsync(p->d_table[b], p->h_table[b], sizeof(BatchSlot) * n, cudaMemcpyHostToDevice, p->compute);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], 2 * sizeof(int), cudaMemcpyHostToDevice, p->compute);
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w)
+            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grid, p->block, p->compute);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, p->compute);
+        for (int it = 0; it < iters && e == cudaSuccess; ++it)
+            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grid, p->block, p->compute);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, p->compute);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rs = set_cuda_error(e, "pool: autotune launch");
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            best_block = block;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs != LBM_OK) return rs;
+    rs = set_geometry(p, best_block);
+    if (rs != LBM_OK) return rs;
+    if (best_us) *best_us = 1000.0 * best / iters;
+    return LBM_OK;
+}
+
+lbm_status lbm_pool_destroy(lbm_pool *p) {
+    if (!p) return LBM_OK;
+    cudaStreamSynchronize(p->compute);
+    cudaStreamSynchronize(p->io);
+    drop_graphs(p);
+    for (auto &kv : p->reqs) cudaEventDestroy(kv.second.init_event);
+    for (int k = 0; k < kEventRing; ++k)
+        if (p->chunk_events[k]) cudaEventDestroy(p->chunk_events[k]);
+    for (int b = 0; b < 2; ++b) {
+        if (p->h_table[b]) cudaFreeHost(p->h_table[b]);
+        if (p->h_header[b]) cudaFreeHost(p->h_header[b]);
+    }
+    if (p->capture) cudaStreamDestroy(p->capture);
+    delete p;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/lbm.h"
 
 namespace lbm {
@@ -60,7 +62,23 @@ struct ReduceArgs {
     int component;         // mode velocity component
 };
 
+// One lattice of a batch (device-resident table entry).
+struct BatchSlot {
+    void *buf[2];      // the two distribution buffers of this lattice
+    int nx, ny, nz;
+    int ncx;           // nx / V
+    long long P;       // cells per velocity plane
+    double relax;      // 1 - 1/tau
+    double rho0;
+    int parity;        // buffer holding the state at the start of the chunk
+    int steps_left;    // steps still to run at the start of the chunk
+    int unit0;         // first work unit of this slot (table sorted by unit0)
+    int units;         // work units of this slot
+};
+
 typedef cudaError_t (*step_fn)(const StepArgs &, int block_threads, cudaStream_t);
+typedef cudaError_t (*batch_fn)(const BatchSlot *slots, const int *header, int step_index, int grid, int block,
+                                cudaStream_t);
 typedef cudaError_t (*init_fn)(const InitArgs &, cudaStream_t);
 typedef cudaError_t (*pull_fn)(const PullArgs &, cudaStream_t);
 typedef cudaError_t (*reduce_fn)(const ReduceArgs &, cudaStream_t);
@@ -74,6 +92,8 @@ struct KernelSet {
     pull_fn pull_f;
     reduce_fn conservation;  // nvals = 4
     reduce_fn mode;          // nvals = 2
+    batch_fn batch;          // persistent multi-lattice step (V = 1)
+    int (*batch_occupancy)(int block);
 };
 
 // Defined in the instantiation units, one per lattice.
@@ -82,7 +102,16 @@ const KernelSet *kernels_d3q19(int K, lbm_storage st);
 const KernelSet *kernels_d3q27(int K, lbm_storage st);
 const KernelSet *kernels_d3q39(int K, lbm_storage st);
 
+// Shared helpers of the C-ABI units (defined in lbm_api.cu).
+lbm_status set_error(lbm_status s, const char *msg);
+lbm_status set_cuda_error(cudaError_t e, const char *what);
+bool lattice_query(lbm_lattice lat, int *D, int *Q, int *maxc, int *kmax);
+size_t storage_bytes(lbm_storage st);
+const KernelSet *kernel_set(lbm_lattice lat, int K, lbm_storage st);
+
 constexpr int kReduceBlocks = 1216;  // 8 x 152 SMs
 constexpr int kReduceThreads = 256;
+
+std::string dims_check(lbm_lattice lat, const int64_t *dims);  // empty when valid
 
 }  // namespace lbm

@@ -76,24 +76,18 @@ __host__ __device__ constexpr int floordiv(int e, int V) { return e >= 0 ? e / V
 // the source row's aligned V-vector (same x range), then realigns the x shift
 // with warp shuffles from the neighbouring lanes; lanes whose neighbour does not
 // hold the adjacent chunk of the same row (warp or row edge, periodic wrap) read
-// the missing values directly.
+// the missing values directly.  Every lane of the warp must call this (the
+// shuffles use the full mask); lanes with active == false compute on a valid
+// clamped position and store nothing.
 template <class LT, int K, class ST, int V>
-__global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *__restrict__ src,
-                                                          typename ST::S *__restrict__ dst, int nx, int ny,
-                                                          int ncx, long long P, typename ST::T relax,
-                                                          typename ST::T rho0) {
+__device__ __forceinline__ void pull_collide_store(const typename ST::S *__restrict__ src,
+                                                   typename ST::S *__restrict__ dst, int nx, int ny, int nz, int ncx,
+                                                   long long P, int y, int z, int chunk, bool active,
+                                                   typename ST::T relax, typename ST::T rho0) {
     using S = typename ST::S;
     using T = typename ST::T;
     constexpr int Q = LT::Q, M = LT::MAXC;
-    const int nz = gridDim.y;
     const int lane = threadIdx.x & 31;
-    const int z = blockIdx.y;
-    const int total = ncx * ny;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = t < total;
-    if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
-    const int y = t / ncx;
-    const int chunk = t - y * ncx;
     const int x0 = chunk * V;
 
     int ys[2 * M + 1], zs[2 * M + 1];
@@ -155,6 +149,79 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
             store_vec<S, V>(out + (long long)i * P, raw);
         }
     }
+}
+
+template <class LT, int K, class ST, int V>
+__global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *__restrict__ src,
+                                                          typename ST::S *__restrict__ dst, int nx, int ny,
+                                                          int ncx, long long P, typename ST::T relax,
+                                                          typename ST::T rho0) {
+    const int z = blockIdx.y;
+    const int total = ncx * ny;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t < total;
+    if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
+    const int y = t / ncx;
+    const int chunk = t - y * ncx;
+    pull_collide_store<LT, K, ST, V>(src, dst, nx, ny, gridDim.y, ncx, P, y, z, chunk, active, relax, rho0);
+}
+
+// ------------------------------------------------------------------ batched step
+// Persistent kernel over the work units of every slot in a table (one unit =
+// blockDim.x consecutive V-chunks of one lattice).  One launch advances every
+// slot with step_index < steps_left by one step; the slot's buffers alternate
+// with its parity.  The table lives in device memory, so a captured graph of
+// launches stays valid while the host rewrites the table between chunks.
+template <class LT, int K, class ST, int V>
+__global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__restrict__ slots,
+                                                         const int *__restrict__ header, int step_index) {
+    __shared__ int sh_slot;
+    const int total_units = header[0];
+    const int nslots = header[1];
+    for (int unit = blockIdx.x; unit < total_units; unit += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = nslots - 1;  // last slot with unit0 <= unit
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (slots[mid].unit0 <= unit) lo = mid;
+                else hi = mid - 1;
+            }
+            sh_slot = lo;
+        }
+        __syncthreads();
+        const BatchSlot &sl = slots[sh_slot];
+        __syncthreads();  // sh_slot is rewritten in the next iteration
+        if (step_index >= sl.steps_left) continue;
+        const int cur = (sl.parity + step_index) & 1;
+        const int per_plane = sl.ncx * sl.ny;
+        const int total = per_plane * sl.nz;
+        int t = (unit - sl.unit0) * blockDim.x + threadIdx.x;
+        const bool active = t < total;
+        if (!active) t = total - 1;
+        const int z = t / per_plane;
+        const int rem = t - z * per_plane;
+        const int y = rem / sl.ncx;
+        const int chunk = rem - y * sl.ncx;
+        pull_collide_store<LT, K, ST, V>(static_cast<const typename ST::S *>(sl.buf[cur]),
+                                         static_cast<typename ST::S *>(sl.buf[cur ^ 1]), sl.nx, sl.ny, sl.nz, sl.ncx,
+                                         sl.P, y, z, chunk, active, typename ST::T(sl.relax),
+                                         typename ST::T(sl.rho0));
+    }
+}
+
+template <class LT, int K, class ST>
+cudaError_t launch_batch(const BatchSlot *slots, const int *header, int step_index, int grid, int block,
+                         cudaStream_t stream) {
+    batch_step_kernel<LT, K, ST, 1><<<grid, block, 0, stream>>>(slots, header, step_index);
+    return cudaGetLastError();
+}
+
+template <class LT, int K, class ST>
+int batch_occupancy(int block) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 1>, block, 0) != cudaSuccess)
+        return 0;
+    return n;
 }
 
 template <class LT, int K, class ST, int V>
@@ -437,6 +504,8 @@ const KernelSet *make_kernel_set() {
         &launch_pull_f<LT, ST>,
         &launch_conservation<LT, ST>,
         &launch_mode<LT, ST>,
+        &launch_batch<LT, K, ST>,
+        &batch_occupancy<LT, K, ST>,
     };
     return &ks;
 }

@@ -112,9 +112,6 @@ cudaError_t dispatch_storage(lbm_storage st, const void *src, int nx, int ny, in
 
 }  // namespace
 
-// Error reporting shared with the rest of the C-ABI (defined in lbm_api.cu).
-lbm_status set_error(lbm_status s, const char *msg);
-
 }  // namespace lbm
 
 using namespace lbm;

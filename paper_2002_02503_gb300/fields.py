@@ -41,15 +41,17 @@ def taylor_green_3d(dims, u0, cs2, rho0=1.0):
 
     u = u0 ( sin kx cos ky cos kz, -cos kx sin ky cos kz, 0 ),
     p = rho0 u0^2 / 16 (cos 2kx + cos 2ky)(cos 2kz + 2),  rho = rho0 + p / cs2."""
-    x, y, z, (nx, ny, nz) = _grid(dims)
-    kx, ky, kz = 2 * np.pi / nx, 2 * np.pi / ny, 2 * np.pi / nz
+    nx, ny, nz = (list(dims) + [1, 1, 1])[:3]
+    x = np.arange(nx) * (2 * np.pi / nx)
+    y = (np.arange(ny) * (2 * np.pi / ny))[:, None]
+    z = (np.arange(nz) * (2 * np.pi / nz))[:, None, None]
     C = nx * ny * nz
-    ux = u0 * np.sin(kx * x) * np.cos(ky * y) * np.cos(kz * z)
-    uy = -u0 * np.cos(kx * x) * np.sin(ky * y) * np.cos(kz * z)
-    p = rho0 * u0 * u0 / 16.0 * (np.cos(2 * kx * x) + np.cos(2 * ky * y)) * (np.cos(2 * kz * z) + 2.0)
-    rho = rho0 + p / cs2
-    u = np.stack([ux.reshape(C), uy.reshape(C), np.zeros(C)])
-    return rho.reshape(C), u
+    u = np.zeros((3, C))
+    u[0] = (u0 * np.sin(x) * np.cos(y) * np.cos(z)).reshape(C)
+    u[1] = (-u0 * np.cos(x) * np.sin(y) * np.cos(z)).reshape(C)
+    p = rho0 * u0 * u0 / 16.0 * (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2.0)
+    rho = (rho0 + p / cs2).reshape(C)
+    return rho, u
 
 
 def taylor_green_2d(dims, u0, cs2, D=2, rho0=1.0):

@@ -45,6 +45,17 @@ SIGNATURES = [
     ("lbm_autotune", _c.c_int, [_P, _c.c_int, _DP]),
     ("lbm_conservation_noalloc", _c.c_int, [_c.c_int, _c.c_int, _I64P, _c.c_double, _P, _P, _c.c_int, _P]),
     ("lbm_destroy", _c.c_int, [_P]),
+    ("lbm_pool_request_bytes", _c.c_size_t, [_c.c_int, _I64P, _c.c_int]),
+    ("lbm_pool_create", _c.c_int, [_c.c_int, _c.c_int, _c.c_int, _P, _c.c_size_t, _c.c_int, _P, _P, _c.POINTER(_P)]),
+    ("lbm_pool_submit", _c.c_int, [_P, _I64P, _c.c_double, _c.c_double, _P, _P, _c.c_int, _c.c_int64,
+                                   _c.POINTER(_c.c_int64)]),
+    ("lbm_pool_advance", _c.c_int, [_P, _c.c_int64, _IP]),
+    ("lbm_pool_poll", _c.c_int, [_P, _c.c_int64, _IP, _c.POINTER(_c.c_int64)]),
+    ("lbm_pool_result", _c.c_int, [_P, _c.c_int64, _P, _P, _c.c_int]),
+    ("lbm_pool_sync", _c.c_int, [_P]),
+    ("lbm_pool_stats", _c.c_int, [_P, _c.POINTER(_c.c_size_t), _IP, _IP]),
+    ("lbm_pool_autotune", _c.c_int, [_P, _c.c_int, _DP]),
+    ("lbm_pool_destroy", _c.c_int, [_P]),
     ("lbm_status_string", _c.c_char_p, [_c.c_int]),
     ("lbm_last_error", _c.c_char_p, []),
 ]
@@ -291,3 +302,121 @@ class Solver:
 
     def raw_bytes(self):
         return self.info["Q"] * self.C * STORAGE_BYTES[self.storage]
+
+
+# ----------------------------------------------------------------- pool (batched / served solves)
+def lbm_pool_request_bytes(lattice, dims, storage):
+    return int(lib().lbm_pool_request_bytes(_lat(lattice), _dims(dims), _st(storage)))
+
+
+def lbm_pool_create(lattice, truncation_order, storage, arena_ptr, arena_bytes, max_slots, compute_stream_ptr=0,
+                    io_stream_ptr=0):
+    h = ctypes.c_void_p()
+    _check(lib().lbm_pool_create(_lat(lattice), int(truncation_order), _st(storage), ctypes.c_void_p(arena_ptr),
+                                 int(arena_bytes), int(max_slots), ctypes.c_void_p(compute_stream_ptr),
+                                 ctypes.c_void_p(io_stream_ptr), ctypes.byref(h)))
+    return h
+
+
+def lbm_pool_submit(h, dims, tau, rho0, rho, u, steps):
+    """Returns the request id, or None when the pool is busy (LBM_ERR_BUSY)."""
+    pr, mr = _ptr(rho)
+    pu, mu = _ptr(u)
+    if mr != mu:
+        raise ValueError("rho and u must both be host or both be device memory")
+    rid = ctypes.c_int64()
+    st = lib().lbm_pool_submit(h, _dims(dims), float(tau), float(rho0), pr, pu, mr, int(steps), ctypes.byref(rid))
+    if st == LBM_ERR_BUSY:
+        return None
+    _check(st)
+    return rid.value
+
+
+def lbm_pool_advance(h, chunk_steps):
+    n = ctypes.c_int()
+    _check(lib().lbm_pool_advance(h, int(chunk_steps), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_pool_poll(h, rid):
+    d = ctypes.c_int()
+    sd = ctypes.c_int64()
+    _check(lib().lbm_pool_poll(h, int(rid), ctypes.byref(d), ctypes.byref(sd)))
+    return bool(d.value), sd.value
+
+
+def lbm_pool_result(h, rid, rho, u):
+    pr, mr = _ptr(rho)
+    pu, mu = _ptr(u)
+    mem = mr if rho is not None else mu
+    _check(lib().lbm_pool_result(h, int(rid), pr, pu, mem))
+
+
+def lbm_pool_sync(h):
+    _check(lib().lbm_pool_sync(h))
+
+
+def lbm_pool_stats(h):
+    fb = ctypes.c_size_t()
+    res, dn = ctypes.c_int(), ctypes.c_int()
+    _check(lib().lbm_pool_stats(h, ctypes.byref(fb), ctypes.byref(res), ctypes.byref(dn)))
+    return {"free_bytes": fb.value, "resident": res.value, "done": dn.value}
+
+
+def lbm_pool_autotune(h, iters=5):
+    us = ctypes.c_double()
+    _check(lib().lbm_pool_autotune(h, int(iters), ctypes.byref(us)))
+    return us.value
+
+
+def lbm_pool_destroy(h):
+    _check(lib().lbm_pool_destroy(h))
+
+
+class Pool:
+    """Owns a pool handle plus its device arena (a torch uint8 tensor) and two streams."""
+
+    def __init__(self, lattice, K, storage, arena_bytes, max_slots=256, device=None):
+        import torch
+
+        self.lattice = lattice
+        self.info = lbm_lattice_info(lattice)
+        self.storage = storage
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.compute = torch.cuda.Stream(dev)
+        self.io = torch.cuda.Stream(dev)
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=dev)
+        self.handle = lbm_pool_create(lattice, K, storage, self.arena.data_ptr(), int(arena_bytes), max_slots,
+                                      self.compute.cuda_stream, self.io.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            lbm_pool_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, dims, tau, rho, u, steps, rho0=1.0):
+        return lbm_pool_submit(self.handle, dims, tau, rho0, rho, u, steps)
+
+    def advance(self, chunk):
+        return lbm_pool_advance(self.handle, chunk)
+
+    def poll(self, rid):
+        return lbm_pool_poll(self.handle, rid)
+
+    def result(self, rid, C):
+        rho = np.empty(C)
+        u = np.empty((self.info["D"], C))
+        lbm_pool_result(self.handle, rid, rho, u)
+        return rho, u
+
+    def sync(self):
+        lbm_pool_sync(self.handle)
+
+    def stats(self):
+        return lbm_pool_stats(self.handle)

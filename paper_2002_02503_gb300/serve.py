@@ -1,0 +1,130 @@
+"""Serving loop: independent periodic D3Q19 solves arriving as a Poisson stream.
+
+Two schedulers over the same seeded request trace:
+  * ``serve_pool``  -- continuous batching on the pool (``lbm_pool_*``): requests are
+    admitted while the arena has room, every resident request advances inside the same
+    batched kernel launches, finished ones leave at chunk boundaries and new ones join;
+  * ``serve_plain`` -- first in, first out, one request at a time on the single-lattice
+    kernel (``lbm_create`` / ``lbm_step`` / ``lbm_get_moments``), the comparison baseline.
+Latency of a request = time its result reaches the host minus its arrival time.
+
+Trace (seeded): cube side round(exp(U(ln 32, ln 128))), tau ~ U[0.52, 1.0], Taylor-Green
+u0 ~ U[0.01, 0.08], steps ~ U{100..2000}, Poisson arrivals at ``rate`` per second.
+"""
+import collections
+import math
+import time
+
+import numpy as np
+
+from . import fields, lbm
+
+T0_D3Q19 = 1.0 / 3.0
+
+
+def make_trace(n, rate=50.0, config_index=4, salt=0, side=(32, 128), tau=(0.52, 1.0), u0=(0.01, 0.08),
+               steps=(100, 2000)):
+    g = fields.rng(config_index, salt)
+    gaps = g.exponential(1.0 / rate, size=n)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    sides = np.rint(np.exp(g.uniform(math.log(side[0]), math.log(side[1]), size=n))).astype(int)
+    taus = g.uniform(tau[0], tau[1], size=n)
+    u0s = g.uniform(u0[0], u0[1], size=n)
+    nsteps = g.integers(steps[0], steps[1] + 1, size=n)
+    return [{"i": i, "arrival": float(arrivals[i]), "side": int(sides[i]), "tau": float(taus[i]),
+             "u0": float(u0s[i]), "steps": int(nsteps[i])} for i in range(n)]
+
+
+def request_fields(r):
+    d = (r["side"],) * 3
+    return fields.taylor_green_3d(d, r["u0"], T0_D3Q19)
+
+
+def _summary(lat, t_total, cells):
+    lat = np.array(sorted(lat))
+    return {"solves": int(len(lat)), "seconds": t_total, "solves_per_s": len(lat) / t_total,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "glups": cells / t_total / 1e9}
+
+
+def serve_pool(trace, K=3, storage="f32", arena_bytes=48 << 30, max_slots=512, chunk=50, keep=None,
+               autotune=True):
+    """Continuous batching.  keep: optional set of request indices whose results are returned."""
+    pool = lbm.Pool("D3Q19", K, storage, arena_bytes, max_slots)
+    pending = collections.deque(sorted(trace, key=lambda r: r["arrival"]))
+    waiting = collections.deque()
+    active = {}
+    lat, results = [], {}
+    cells = 0
+    tuned = not autotune
+    t0 = time.perf_counter()
+    while pending or waiting or active:
+        now = time.perf_counter() - t0
+        while pending and pending[0]["arrival"] <= now:
+            waiting.append(pending.popleft())
+        while waiting:
+            r = waiting[0]
+            rho, u = request_fields(r)
+            rid = pool.submit((r["side"],) * 3, r["tau"], rho, u, r["steps"])
+            if rid is None:
+                break
+            active[rid] = r
+            waiting.popleft()
+        if not tuned and len(active) >= 8:
+            lbm.lbm_pool_autotune(pool.handle, 3)
+            tuned = True
+        n = pool.advance(chunk) if active else 0
+        for rid in list(active):
+            done, _ = pool.poll(rid)
+            if done:
+                r = active.pop(rid)
+                C = r["side"] ** 3
+                rho, u = pool.result(rid, C)
+                lat.append(time.perf_counter() - t0 - r["arrival"])
+                cells += C * r["steps"]
+                if keep is not None and r["i"] in keep:
+                    results[r["i"]] = (rho, u)
+        if n == 0 and not active:
+            if pending and not waiting:
+                time.sleep(max(0.0, min(0.01, pending[0]["arrival"] - (time.perf_counter() - t0))))
+        elif n == 0:
+            pool.sync()
+    t_total = time.perf_counter() - t0
+    pool.close()
+    out = _summary(lat, t_total, cells)
+    out["chunk"] = chunk
+    return out, results
+
+
+def serve_plain(trace, K=3, storage="f32", keep=None):
+    """FIFO, one request at a time on the single-lattice kernel (one reused workspace)."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    smax = max(r["side"] for r in trace)
+    ws_bytes = lbm.lbm_workspace_bytes("D3Q19", (smax,) * 3, storage)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    order = sorted(trace, key=lambda r: r["arrival"])
+    lat, results = [], {}
+    cells = 0
+    t0 = time.perf_counter()
+    for r in order:
+        now = time.perf_counter() - t0
+        if r["arrival"] > now:
+            time.sleep(r["arrival"] - now)
+        d = (r["side"],) * 3
+        C = r["side"] ** 3
+        rho, u = request_fields(r)
+        h = lbm.lbm_create("D3Q19", d, r["tau"], K, storage, 1.0, ws.data_ptr(), ws_bytes, stream.cuda_stream)
+        lbm.lbm_set_fields(h, rho, u)
+        lbm.lbm_step(h, r["steps"])
+        ro = np.empty(C)
+        uo = np.empty((3, C))
+        lbm.lbm_get_moments(h, ro, uo)
+        lbm.lbm_destroy(h)
+        lat.append(time.perf_counter() - t0 - r["arrival"])
+        cells += C * r["steps"]
+        if keep is not None and r["i"] in keep:
+            results[r["i"]] = (ro, uo)
+    t_total = time.perf_counter() - t0
+    return _summary(lat, t_total, cells), results

@@ -1,0 +1,145 @@
+"""Batched multi-lattice step and the continuous-batching pool (through the C-ABI).
+
+Each request's result must not depend on what else is resident: the same request run
+alone and in a mix gives identical results, both match the single-lattice solver within
+the FP32 tolerance, and small cases match the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_02503_gb300 import fields, lbm, serve
+
+from _lbmtest import TOL_F32, rel_f, rel_u
+
+pytestmark = pytest.mark.gpu
+
+
+def _tg(side, u0):
+    return fields.taylor_green_3d((side,) * 3, u0, 1.0 / 3.0)
+
+
+def _run_pool(reqs, chunk=7, arena=2 << 30, submit_after=None):
+    """reqs: list of (side, tau, u0, steps).  submit_after[k] = chunk index at which request k joins."""
+    pool = lbm.Pool("D3Q19", 3, "f32", arena, 64)
+    submit_after = submit_after or [0] * len(reqs)
+    ids = {}
+    out = {}
+    c = 0
+    while len(out) < len(reqs):
+        for k, (side, tau, u0, steps) in enumerate(reqs):
+            if k not in ids and submit_after[k] <= c:
+                rho, u = _tg(side, u0)
+                rid = pool.submit((side,) * 3, tau, rho, u, steps)
+                assert rid is not None
+                ids[k] = rid
+        pool.advance(chunk)
+        c += 1
+        pool.sync()
+        for k, rid in ids.items():
+            if k in out:
+                continue
+            done, sd = pool.poll(rid)
+            if done:
+                out[k] = pool.result(rid, reqs[k][0] ** 3)
+        assert c < 10000
+    pool.close()
+    return out
+
+
+def _single(side, tau, u0, steps):
+    s = lbm.Solver("D3Q19", (side,) * 3, tau, 3, "f32")
+    rho, u = _tg(side, u0)
+    s.set_fields(rho, u)
+    s.step(steps)
+    r = s.moments()
+    s.close()
+    return r
+
+
+def test_result_same_alone_and_in_mix():
+    target = (33, 0.7, 0.05, 40)
+    alone = _run_pool([target])[0]
+    mix = [(20, 0.9, 0.03, 13), target, (47, 0.55, 0.08, 61), (12, 0.6, 0.02, 5), (64, 0.52, 0.07, 29)]
+    joined = [0, 2, 0, 1, 3]  # the target joins while others run; some leave before it ends
+    res = _run_pool(mix, submit_after=joined)
+    np.testing.assert_array_equal(res[1][0], alone[0])
+    np.testing.assert_array_equal(res[1][1], alone[1])
+    r1, u1 = _single(*target)
+    assert rel_f(alone[0], r1) < TOL_F32
+    assert rel_u(alone[1], u1) < TOL_F32
+    for k, req in enumerate(mix):  # every other member matches its own single-lattice run
+        r, u = _single(*req)
+        assert rel_f(res[k][0], r) < TOL_F32
+        assert rel_u(res[k][1], u) < TOL_F32
+
+
+def test_pool_matches_oracle_on_small_odd_lattice():
+    side, tau, u0, steps = 13, 0.6, 0.05, 30
+    res = _run_pool([(side, tau, u0, steps), (17, 0.8, 0.03, 11)], chunk=4)[0]
+    rho, u = _tg(side, u0)
+    d = (side,) * 3
+    f = oracle.run("D3Q19", 3, tau, d, oracle.init_eq("D3Q19", 3, d, rho, u), steps)
+    r_ref, u_ref = oracle.moments("D3Q19", d, f)
+    assert rel_f(res[0], r_ref) < TOL_F32
+    assert rel_u(res[1], u_ref) < TOL_F32
+
+
+def test_admission_by_memory_and_zero_steps():
+    side = 32
+    per = lbm.lbm_pool_request_bytes("D3Q19", (side,) * 3, "f32")
+    pool = lbm.Pool("D3Q19", 3, "f32", 2 * per + (1 << 20), 64)
+    rho, u = _tg(side, 0.05)
+    a = pool.submit((side,) * 3, 0.7, rho, u, 5)
+    b = pool.submit((side,) * 3, 0.7, rho, u, 0)
+    assert a is not None and b is not None
+    assert pool.submit((side,) * 3, 0.7, rho, u, 5) is None  # arena full: BUSY
+    done, _ = pool.poll(b)
+    assert done
+    r0, u0 = pool.result(b, side ** 3)
+    np.testing.assert_allclose(u0, u, rtol=0, atol=1e-7)  # zero steps: moments of f^eq(rho, u)
+    c = pool.submit((side,) * 3, 0.7, rho, u, 5)  # room again
+    assert c is not None
+    while not (pool.poll(a)[0] and pool.poll(c)[0]):
+        pool.advance(3)
+        pool.sync()
+    pool.result(a, side ** 3)
+    pool.result(c, side ** 3)
+    assert pool.stats()["resident"] == 0
+    pool.close()
+
+
+def test_pool_autotune_keeps_results():
+    reqs = [(24, 0.7, 0.05, 20), (31, 0.6, 0.04, 20)]
+    base = _run_pool(reqs)
+    pool = lbm.Pool("D3Q19", 3, "f32", 1 << 30, 64)
+    ids = []
+    for side, tau, u0, steps in reqs:
+        rho, u = _tg(side, u0)
+        ids.append(pool.submit((side,) * 3, tau, rho, u, steps))
+    us = lbm.lbm_pool_autotune(pool.handle, 2)
+    assert us > 0
+    while not all(pool.poll(i)[0] for i in ids):
+        pool.advance(7)
+        pool.sync()
+    for k, i in enumerate(ids):
+        r, u = pool.result(i, reqs[k][0] ** 3)
+        np.testing.assert_array_equal(u, base[k][1])
+    pool.close()
+
+
+def test_served_results_same_as_alone():
+    """A short Poisson trace through the continuous-batching server: sampled results equal the
+    same requests run alone on the single-lattice path, within the FP32 tolerance."""
+    trace = serve.make_trace(24, rate=400.0, salt=3, side=(16, 48), steps=(20, 120))
+    keep = {0, 5, 11, 23}
+    stats, res = serve.serve_pool(trace, chunk=16, arena_bytes=4 << 30, keep=keep)
+    assert stats["solves"] == 24
+    for i in keep:
+        r = trace[i]
+        rr, uu = _single(r["side"], r["tau"], r["u0"], r["steps"])
+        assert rel_f(res[i][0], rr) < TOL_F32
+        assert rel_u(res[i][1], uu) < TOL_F32
+    plain, pres = serve.serve_plain(trace, keep=keep)
+    assert plain["solves"] == 24
+    for i in keep:
+        np.testing.assert_allclose(pres[i][1], res[i][1], rtol=0, atol=TOL_F32 * np.abs(res[i][1]).max())
