@@ -5,8 +5,9 @@
 //   s  = xi.V = c.u/T0          v2 = V.V = u.u/T0
 //   A  = (c c/T0 - I) : Pi      B  = c.Pi.u/T0          R = u.Pi.u/T0
 // The Hermite tensors enter only through full contractions, which reduce to
-// scalars: H^(n)(xi):V^[n] = h_n with h_0 = 1, h_1 = s, h_{n+1} = s h_n - n v2 h_{n-1}
-// (the scalar form of Eq. recurG).  With E_n = sum_{m<=n} h_m/m! (E_n = 0 for n < 0):
+// scalars (the Appendix identity): H^(n)(xi):V^[n] = h_n with h_0 = 1, h_1 = s,
+// h_{n+1} = s h_n - n v2 h_{n-1} (the scalar form of Eq. recurG).  With
+// E_n = sum_{m<=n} h_m/m! (E_n = 0 for n < 0):
 //   truncated Eq. hermite        f^eq_i  = w_i rho E_K
 //   truncated Eq. hermite-coll   fhat_i  = w_i/(2 T0) [E_{K-2} A - 2 E_{K-3} B + E_{K-4} R]
 // which for K = 2, 3, 4 are Eq. filter-Pi, Eq. filter-1st and Eq. filter-2nd.
@@ -67,61 +68,21 @@ __device__ __forceinline__ typename ST::S encode(typename ST::T x, int i) {
     return ST::enc(x, typename ST::T(1.0 / weight<LT>(i)));
 }
 
-// ------------------------------------------------------------------ Hermite sums
-__host__ __device__ constexpr double inv_fact(int m) {
-    double r = 1.0;
-    for (int k = 2; k <= m; ++k) r /= k;
-    return r;
+// ------------------------------------------------------------------ moments
+// Accumulators start at -0.0: x + (-0.0) == x for every x, so the compiler drops
+// the first addition (it cannot drop x + 0.0, which differs for x = -0.0).
+template <typename T>
+__device__ __forceinline__ constexpr T neg_zero() {
+    return T(-0.0);
 }
 
-// Even and odd parts (under c -> -c) of E_n = sum_{m<=n} h_m/m! for n = -1..K.
-// ev[n+1], od[n+1] hold E_n's even / odd parts (index 0 is n = -1, all zero).
-template <int K, typename T>
-struct HermiteSums {
-    T ev[K + 2], od[K + 2];
-    __device__ __forceinline__ HermiteSums(T s, T v2) {
-        T h[K + 1];
-        h[0] = T(1);
-        if (K >= 1) h[1] = s;
-#pragma unroll
-        for (int m = 1; m < K; ++m) h[m + 1] = s * h[m] - T(m) * v2 * h[m - 1];
-        ev[0] = T(0);
-        od[0] = T(0);
-#pragma unroll
-        for (int n = 0; n <= K; ++n) {
-            T add = (n == 0) ? T(1) : h[n] * T(inv_fact(n));
-            ev[n + 1] = ev[n] + ((n & 1) ? T(0) : add);
-            od[n + 1] = od[n] + ((n & 1) ? add : T(0));
-        }
-    }
-    __device__ __forceinline__ T E_even(int n) const { return n < 0 ? T(0) : ev[n + 1]; }
-    __device__ __forceinline__ T E_odd(int n) const { return n < 0 ? T(0) : od[n + 1]; }
-};
-
-// Rest velocity (s = 0): h_m = He_m(0) |V|^m, only even m survive.
-template <int K, typename T>
-struct HermiteSumsRest {
-    T ev[K + 2];
-    __device__ __forceinline__ explicit HermiteSumsRest(T v2) {
-        T h[K + 1];
-        h[0] = T(1);
-        if (K >= 1) h[1] = T(0);
-#pragma unroll
-        for (int m = 1; m < K; ++m) h[m + 1] = (m & 1) ? -T(m) * v2 * h[m - 1] : T(0);
-        ev[0] = T(0);
-#pragma unroll
-        for (int n = 0; n <= K; ++n) ev[n + 1] = ev[n] + ((n & 1) ? T(0) : ((n == 0) ? T(1) : h[n] * T(inv_fact(n))));
-    }
-    __device__ __forceinline__ T E(int n) const { return n < 0 ? T(0) : ev[n + 1]; }
-};
-
-// ------------------------------------------------------------------ moments
-template <class LT, typename T>
-struct Moments {
-    T drho, rho;
-    T j[3], u[3];
-    T m2[3][3];  // sum c c g~ (upper triangle used)
-};
+// c * v for a small integer constant c (no multiply for c = +-1).
+template <typename T>
+__device__ __forceinline__ void accumulate_scaled(T &acc, int c, T v) {
+    if (c == 1) acc += v;
+    else if (c == -1) acc -= v;
+    else if (c != 0) acc += T(c) * v;
+}
 
 // Accumulate drho, j, sum c c g~ from shifted values in pair order.
 template <class LT, typename T>
@@ -129,9 +90,9 @@ __device__ __forceinline__ void accumulate_moments(const T (&g)[LT::Q], T &drho,
     drho = g[0];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        j[a] = T(0);
+        j[a] = neg_zero<T>();
 #pragma unroll
-        for (int b = 0; b < 3; ++b) m2[a][b] = T(0);
+        for (int b = 0; b < 3; ++b) m2[a][b] = neg_zero<T>();
     }
 #pragma unroll
     for (int p = 0; p < LT::NP; ++p) {
@@ -141,25 +102,45 @@ __device__ __forceinline__ void accumulate_moments(const T (&g)[LT::Q], T &drho,
 #pragma unroll
         for (int a = 0; a < LT::D; ++a) {
             const int ca = LT::c(p, a);
-            if (ca == 1) j[a] += dp;
-            else if (ca == -1) j[a] -= dp;
-            else if (ca != 0) j[a] += T(ca) * dp;
+            accumulate_scaled(j[a], ca, dp);
 #pragma unroll
-            for (int b = a; b < LT::D; ++b) {
-                const int cab = ca * LT::c(p, b);
-                if (cab == 1) m2[a][b] += sp;
-                else if (cab == -1) m2[a][b] -= sp;
-                else if (cab != 0) m2[a][b] += T(cab) * sp;
-            }
+            for (int b = a; b < LT::D; ++b) accumulate_scaled(m2[a][b], ca * LT::c(p, b), sp);
         }
     }
 }
 
 // ------------------------------------------------------------------ collision
+// Scalar Hermite values h_2..h_K at (s, v2): h_{n+1} = s h_n - n v2 h_{n-1}.
+// Only the orders that exist for this K are formed.
+template <int K, typename T>
+struct ScalarHermite {
+    T h2, h3, h4, h5;
+    __device__ __forceinline__ ScalarHermite(T s, T v2) {
+        h2 = s * s - v2;
+        if constexpr (K >= 3) h3 = s * (h2 - T(2) * v2);
+        if constexpr (K >= 4) h4 = s * h3 - T(3) * v2 * h2;
+        if constexpr (K >= 5) h5 = s * h4 - T(4) * v2 * h3;
+    }
+    // E_K - 1 split into even and odd parts (truncated Eq. hermite without its constant term)
+    __device__ __forceinline__ T feq_even() const {
+        if constexpr (K >= 4) return h2 * T(0.5) + h4 * T(1.0 / 24.0);
+        else return h2 * T(0.5);
+    }
+    __device__ __forceinline__ T feq_odd(T s) const {
+        if constexpr (K >= 5) return s + h3 * T(1.0 / 6.0) + h5 * T(1.0 / 120.0);
+        else if constexpr (K >= 3) return s + h3 * T(1.0 / 6.0);
+        else return s;
+    }
+};
+
 // g: shifted pre-collision values in pair order; overwritten with the shifted
 // post-collision values of Eq. lbe-reg.  relax = 1 - 1/tau.
+//   f^eq  - w rho0 = w drho + w rho (E_K - 1)
+//   fhat          = w/(2 T0) [E_{K-2} A - 2 E_{K-3} B + E_{K-4} R]
+// with the even/odd parts of E_n written out for K = 2..5 (E_n = 0 for n < 0).
 template <class LT, int K, typename T>
 __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
+    static_assert(K >= 2 && K <= 5, "truncation order");
     constexpr int D = LT::D;
     const T iT0 = T(1.0 / LT::T0);
     const T T0 = T(LT::T0);
@@ -167,15 +148,14 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
     accumulate_moments<LT, T>(g, drho, j, m2);
     const T rho = rho0 + drho;
     const T irho = T(1) / rho;
-    T u[3] = {T(0), T(0), T(0)};
+    T u[3], us[3];  // u and u / T0
 #pragma unroll
-    for (int a = 0; a < D; ++a) u[a] = j[a] * irho;
+    for (int a = 0; a < D; ++a) {
+        u[a] = j[a] * irho;
+        us[a] = u[a] * iT0;
+    }
     // Pi^neq = sum c c g~ - T0 drho I - j u  (Eq. coeff-2; equal to Eq. Pi_def)
     T P[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) P[a][b] = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -185,60 +165,78 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
             P[a][b] = v;
             P[b][a] = v;
         }
-    T v2 = T(0), trP = T(0);
+    T v2 = neg_zero<T>(), trP = neg_zero<T>();
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        v2 += u[a] * u[a];
+        v2 += u[a] * us[a];  // u.u / T0
         trP += P[a][a];
     }
-    v2 *= iT0;
-    T Pu[3] = {T(0), T(0), T(0)};
+    T Pu[3] = {neg_zero<T>(), neg_zero<T>(), neg_zero<T>()};  // Pi u / T0
+    T R = neg_zero<T>();                                      // u.Pi.u / T0
+    if constexpr (K >= 3) {
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+        for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int b = 0; b < D; ++b) Pu[a] += P[a][b] * u[b];
-    T R = T(0);
+            for (int b = 0; b < D; ++b) Pu[a] += P[a][b] * us[b];
+    }
+    if constexpr (K >= 4) {
 #pragma unroll
-    for (int a = 0; a < D; ++a) R += u[a] * Pu[a];
-    R *= iT0;
+        for (int a = 0; a < D; ++a) R += u[a] * Pu[a];
+    }
+    const T kappa = relax * T(1.0 / (2.0 * LT::T0));  // (1 - 1/tau) / (2 T0)
 
-    // rest velocity: A = -tr Pi, B = 0
+    // rest velocity: s = 0, A = -tr Pi, B = 0; h2 = -v2, h4 = 3 v2^2
     {
-        HermiteSumsRest<K, T> H(v2);
         const T w = T(LT::w0);
-        const T feq = w * drho + w * rho * (H.E(K) - T(1));
-        const T fh = T(LT::w0 / (2.0 * LT::T0)) * (-trP * H.E(K - 2) + R * H.E(K - 4));
-        g[0] = feq + relax * fh;
+        T feq = w * drho;
+        T fh = -trP;
+        if constexpr (K >= 4) {
+            feq += w * rho * (v2 * v2 * T(3.0 / 24.0) - v2 * T(0.5));
+            fh = -trP * (T(1) - v2 * T(0.5)) + R;
+        } else {
+            feq -= w * rho * v2 * T(0.5);
+        }
+        g[0] = feq + kappa * T(LT::w0) * fh;
     }
 #pragma unroll
     for (int p = 0; p < LT::NP; ++p) {
-        T s = T(0), cPc = T(0), cPu = T(0);
+        T s = neg_zero<T>(), cPc = neg_zero<T>(), B = neg_zero<T>();
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             const int ca = LT::c(p, a);
             if (ca == 0) continue;
-            s += T(ca) * u[a];
-            cPu += T(ca) * Pu[a];
+            accumulate_scaled(s, ca, us[a]);
+            if constexpr (K >= 3) accumulate_scaled(B, ca, Pu[a]);
+            accumulate_scaled(cPc, ca * ca, P[a][a]);
 #pragma unroll
-            for (int b = 0; b < D; ++b) {
-                const int cb = LT::c(p, b);
-                if (cb == 0) continue;
-                cPc += T(ca * cb) * P[a][b];
-            }
+            for (int b = a + 1; b < D; ++b) accumulate_scaled(cPc, 2 * ca * LT::c(p, b), P[a][b]);
         }
-        s *= iT0;
         const T A = cPc * iT0 - trP;
-        const T B = cPu * iT0;
-        HermiteSums<K, T> H(s, v2);
+        const ScalarHermite<K, T> H(s, v2);
         const T w = T(LT::w(p));
         const T wr = w * rho;
-        const T feq_e = w * drho + wr * (H.E_even(K) - T(1));
-        const T feq_o = wr * H.E_odd(K);
-        const T cw = T(LT::w(p) / (2.0 * LT::T0));
-        const T fh_e = cw * (A * H.E_even(K - 2) - T(2) * B * H.E_odd(K - 3) + R * H.E_even(K - 4));
-        const T fh_o = cw * (A * H.E_odd(K - 2) - T(2) * B * H.E_even(K - 3) + R * H.E_odd(K - 4));
-        g[2 * p + 1] = feq_e + feq_o + relax * (fh_e + fh_o);
-        g[2 * p + 2] = feq_e - feq_o + relax * (fh_e - fh_o);
+        const T feq_e = w * drho + wr * H.feq_even();
+        const T feq_o = wr * H.feq_odd(s);
+        T fh_e, fh_o;  // bracket of Eq. hermite-coll, even / odd parts
+        if constexpr (K == 2) {
+            fh_e = A;
+        } else if constexpr (K == 3) {
+            fh_e = A;
+            fh_o = A * s - T(2) * B;
+        } else if constexpr (K == 4) {
+            fh_e = A * (T(1) + H.h2 * T(0.5)) - T(2) * B * s + R;
+            fh_o = A * s - T(2) * B;
+        } else {
+            const T e2 = T(1) + H.h2 * T(0.5);
+            fh_e = A * e2 - T(2) * B * s + R;
+            fh_o = A * (s + H.h3 * T(1.0 / 6.0)) - T(2) * B * e2 + R * s;
+        }
+        const T kw = kappa * w;
+        const T e = feq_e + kw * fh_e;
+        T o = feq_o;
+        if constexpr (K >= 3) o += kw * fh_o;
+        g[2 * p + 1] = e + o;
+        g[2 * p + 2] = e - o;
     }
 }
 
@@ -247,25 +245,28 @@ template <class LT, int K, typename T>
 __device__ __forceinline__ void equilibrium_shifted(T rho, T drho, const T (&u)[3], T (&g)[LT::Q]) {
     constexpr int D = LT::D;
     const T iT0 = T(1.0 / LT::T0);
-    T v2 = T(0);
+    T us[3] = {T(0), T(0), T(0)};
+    T v2 = neg_zero<T>();
 #pragma unroll
-    for (int a = 0; a < D; ++a) v2 += u[a] * u[a];
-    v2 *= iT0;
+    for (int a = 0; a < D; ++a) {
+        us[a] = u[a] * iT0;
+        v2 += u[a] * us[a];
+    }
     {
-        HermiteSumsRest<K, T> H(v2);
         const T w = T(LT::w0);
-        g[0] = w * drho + w * rho * (H.E(K) - T(1));
+        T e = -v2 * T(0.5);
+        if constexpr (K >= 4) e += v2 * v2 * T(3.0 / 24.0);
+        g[0] = w * drho + w * rho * e;
     }
 #pragma unroll
     for (int p = 0; p < LT::NP; ++p) {
-        T s = T(0);
+        T s = neg_zero<T>();
 #pragma unroll
-        for (int a = 0; a < D; ++a) s += T(LT::c(p, a)) * u[a];
-        s *= iT0;
-        HermiteSums<K, T> H(s, v2);
+        for (int a = 0; a < D; ++a) accumulate_scaled(s, LT::c(p, a), us[a]);
+        const ScalarHermite<K, T> H(s, v2);
         const T w = T(LT::w(p));
-        const T feq_e = w * drho + w * rho * (H.E_even(K) - T(1));
-        const T feq_o = w * rho * H.E_odd(K);
+        const T feq_e = w * drho + w * rho * H.feq_even();
+        const T feq_o = w * rho * H.feq_odd(s);
         g[2 * p + 1] = feq_e + feq_o;
         g[2 * p + 2] = feq_e - feq_o;
     }

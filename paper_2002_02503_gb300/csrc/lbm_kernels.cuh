@@ -96,6 +96,12 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         ys[k + M] = wrap1(y - k, ny);  // dims >= max|c| is checked on the host
         zs[k + M] = wrap1(z - k, nz);
     }
+    // lane offsets dl of the x shift: |dl| <= ceil(M / V); ok[dl] = neighbour lane holds chunk + dl
+    constexpr int kMaxDl = (M + V - 1) / V;
+    bool ok[2 * kMaxDl + 1];
+#pragma unroll
+    for (int dl = -kMaxDl; dl <= kMaxDl; ++dl)
+        ok[dl + kMaxDl] = lane + dl >= 0 && lane + dl <= 31 && chunk + dl >= 0 && chunk + dl < ncx;
 
     T f[Q][V];
 #pragma unroll
@@ -119,10 +125,10 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
                 if (dl == 0) {
                     f[i][j] = v[ei];
                 } else {
+                    // source lane lane+dl holds chunk+dl of the same row unless at a warp or row edge
                     const int sl = lane + dl;
                     T sh = __shfl_sync(kFull, v[ei], sl < 0 ? 0 : (sl > 31 ? 31 : sl));
-                    const bool ok = sl >= 0 && sl <= 31 && chunk + dl >= 0 && chunk + dl < ncx;
-                    if (!ok) sh = decode<ST, LT>(row[wrapn(x0 + e, nx)], i);
+                    if (!ok[dl + kMaxDl]) sh = decode<ST, LT>(row[wrap1(x0 + e, nx)], i);
                     f[i][j] = sh;
                 }
             }
