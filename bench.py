@@ -30,7 +30,7 @@ LATTICE_Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27, "D3Q39": 39}
 LATTICE_T0 = {"D2Q9": 1.0 / 3.0, "D3Q19": 1.0 / 3.0, "D3Q27": 1.0 / 3.0, "D3Q39": 2.0 / 3.0}
 STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}
 DTYPE_NAME = {"f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)", "f64": "f64"}
-KERNEL_SOURCES = ["lbm_core.cuh", "lbm_kernels.cuh", "lbm_lattice.cuh", "lbm_staged.cuh"]
+KERNEL_SOURCES = ["lbm_core.cuh", "lbm_kernels.cuh", "lbm_lattice.cuh"]
 
 
 def parse():
@@ -236,7 +236,7 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(a, variant):
+def recorded_traffic(a, variant, cpt):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -244,7 +244,7 @@ def recorded_traffic(a, variant):
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    key = "%s_%dx%dx%d_%s_K%d_v%d" % (a.lattice, a.dims[0], a.dims[1], a.dims[2], a.storage, a.K, variant)
+    key = "%s_%dx%dx%d_%s_K%d_v%d_c%d" % (a.lattice, a.dims[0], a.dims[1], a.dims[2], a.storage, a.K, variant, cpt)
     r = rec.get(key)
     if not r or r.get("kernel_hash") != kernel_hash():
         return None
@@ -361,7 +361,7 @@ def run_ours(a):
         achieved = bpu * C / per_launch_s / 1e9
         peak, peak_kind = measured_peak()
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(a, variant), "peak_kind": peak_kind,
+                "traffic": recorded_traffic(a, variant, cpt), "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bpu * C,
                 "kernel": "step_%s" % ("direct" if variant == 0 else "staged")}
         cpu = None

@@ -51,8 +51,8 @@ typedef enum {
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2, LBM_D3Q39 = 3 } lbm_lattice;
 
 /* How distributions are stored in HBM.  The collision always computes in FP32
- * (FP64 for LBM_STORE_F64).  Every form stores the shifted value
- * g~_i = g_i - w_i rho0; the 16-bit forms store round_to_nearest(g~_i / w_i). */
+ * (FP64 for LBM_STORE_F64).  Every form stores the shifted, scaled value
+ * h_i = (g_i - w_i rho0) / w_i, rounded to nearest (even) in the storage type. */
 typedef enum {
     LBM_STORE_F32 = 0,
     LBM_STORE_F16 = 1,

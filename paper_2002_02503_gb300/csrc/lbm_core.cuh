@@ -13,11 +13,12 @@
 // which for K = 2, 3, 4 are Eq. filter-Pi, Eq. filter-1st and Eq. filter-2nd.
 // The post-collision value is Eq. lbe-reg: f'_i = f^eq_i + (1 - 1/tau) fhat_i.
 //
-// Shifted storage: every kernel works with g~_i = g_i - w_i rho0, so that
-//   rho - rho0 = sum g~_i,   rho u = sum c_i g~_i   (sum_i w_i c_i = 0),
-//   Pi = sum c c g~ - T0 (rho - rho0) I - rho u u   (sum_i w_i c_i c_i = T0 I),
-// and the output is f^eq - w rho0 = w (rho - rho0) + w rho (E_K - 1) plus the
-// filtered part: no large constant is ever added and then subtracted.
+// Shifted, scaled storage: every kernel works with h_i = (g_i - w_i rho0) / w_i, so that
+//   rho - rho0 = sum w h,   rho u = sum w c h   (sum_i w_i c_i = 0),
+//   Pi = sum w c c h - T0 (rho - rho0) I - rho u u   (sum_i w_i c_i c_i = T0 I),
+// and the output is (f^eq - w rho0)/w = (rho - rho0) + rho (E_K - 1) plus the
+// filtered part over w: no large constant is ever added and then subtracted, and
+// every weight multiplies only inside the moment sums.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -29,43 +30,47 @@
 namespace lbm {
 
 // ------------------------------------------------------------------ codecs
+// Every storage form holds the scaled shifted value h_i = (g_i - w_i rho0) / w_i:
+// all velocities then share one magnitude range (the D3Q39 weights span 1/12 to
+// 1/1620), and the collision below works on h directly, so neither decoding nor
+// encoding multiplies by a weight.
 struct StoreF32 {
     using S = float;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_F32;
-    __device__ __forceinline__ static T dec(S v, T) { return v; }
-    __device__ __forceinline__ static S enc(T x, T) { return x; }
+    __device__ __forceinline__ static T dec(S v) { return v; }
+    __device__ __forceinline__ static S enc(T x) { return x; }
 };
 struct StoreF64 {
     using S = double;
     using T = double;
     static constexpr lbm_storage id = LBM_STORE_F64;
-    __device__ __forceinline__ static T dec(S v, T) { return v; }
-    __device__ __forceinline__ static S enc(T x, T) { return x; }
+    __device__ __forceinline__ static T dec(S v) { return v; }
+    __device__ __forceinline__ static S enc(T x) { return x; }
 };
-// 16-bit forms store g~_i / w_i (all velocities then share one magnitude range).
 struct StoreF16 {
     using S = __half;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_F16;
-    __device__ __forceinline__ static T dec(S v, T w) { return w * __half2float(v); }
-    __device__ __forceinline__ static S enc(T x, T inv_w) { return __float2half_rn(x * inv_w); }
+    __device__ __forceinline__ static T dec(S v) { return __half2float(v); }
+    __device__ __forceinline__ static S enc(T x) { return __float2half_rn(x); }
 };
 struct StoreBF16 {
     using S = __nv_bfloat16;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_BF16;
-    __device__ __forceinline__ static T dec(S v, T w) { return w * __bfloat162float(v); }
-    __device__ __forceinline__ static S enc(T x, T inv_w) { return __float2bfloat16_rn(x * inv_w); }
+    __device__ __forceinline__ static T dec(S v) { return __bfloat162float(v); }
+    __device__ __forceinline__ static S enc(T x) { return __float2bfloat16_rn(x); }
 };
 
+// Scaled value h of velocity i (the weight index is kept for call sites that need it).
 template <class ST, class LT>
-__device__ __forceinline__ typename ST::T decode(typename ST::S v, int i) {
-    return ST::dec(v, typename ST::T(weight<LT>(i)));
+__device__ __forceinline__ typename ST::T decode(typename ST::S v, int) {
+    return ST::dec(v);
 }
 template <class ST, class LT>
-__device__ __forceinline__ typename ST::S encode(typename ST::T x, int i) {
-    return ST::enc(x, typename ST::T(1.0 / weight<LT>(i)));
+__device__ __forceinline__ typename ST::S encode(typename ST::T x, int) {
+    return ST::enc(x);
 }
 
 // ------------------------------------------------------------------ moments
@@ -84,10 +89,11 @@ __device__ __forceinline__ void accumulate_scaled(T &acc, int c, T v) {
     else if (c != 0) acc += T(c) * v;
 }
 
-// Accumulate drho, j, sum c c g~ from shifted values in pair order.
+// Accumulate drho = sum w h, j = sum w c h, sum w c c h from scaled values h in
+// pair order (each term is one fused multiply-add with a compile-time constant).
 template <class LT, typename T>
 __device__ __forceinline__ void accumulate_moments(const T (&g)[LT::Q], T &drho, T (&j)[3], T (&m2)[3][3]) {
-    drho = g[0];
+    drho = T(LT::w0) * g[0];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         j[a] = neg_zero<T>();
@@ -96,15 +102,19 @@ __device__ __forceinline__ void accumulate_moments(const T (&g)[LT::Q], T &drho,
     }
 #pragma unroll
     for (int p = 0; p < LT::NP; ++p) {
+        const T w = T(LT::w(p));
         const T sp = g[2 * p + 1] + g[2 * p + 2];
         const T dp = g[2 * p + 1] - g[2 * p + 2];
-        drho += sp;
+        drho += w * sp;
 #pragma unroll
         for (int a = 0; a < LT::D; ++a) {
             const int ca = LT::c(p, a);
-            accumulate_scaled(j[a], ca, dp);
+            if (ca != 0) j[a] += T(ca * LT::w(p)) * dp;
 #pragma unroll
-            for (int b = a; b < LT::D; ++b) accumulate_scaled(m2[a][b], ca * LT::c(p, b), sp);
+            for (int b = a; b < LT::D; ++b) {
+                const int cab = ca * LT::c(p, b);
+                if (cab != 0) m2[a][b] += T(cab * LT::w(p)) * sp;
+            }
         }
     }
 }
@@ -133,10 +143,11 @@ struct ScalarHermite {
     }
 };
 
-// g: shifted pre-collision values in pair order; overwritten with the shifted
-// post-collision values of Eq. lbe-reg.  relax = 1 - 1/tau.
-//   f^eq  - w rho0 = w drho + w rho (E_K - 1)
-//   fhat          = w/(2 T0) [E_{K-2} A - 2 E_{K-3} B + E_{K-4} R]
+// g: scaled shifted pre-collision values h = (f - w rho0)/w in pair order;
+// overwritten with the scaled post-collision values of Eq. lbe-reg.
+// relax = 1 - 1/tau.  Divided by w_i, the two parts read
+//   (f^eq - w rho0)/w = drho + rho (E_K - 1)
+//   fhat / w          = 1/(2 T0) [E_{K-2} A - 2 E_{K-3} B + E_{K-4} R]
 // with the even/odd parts of E_n written out for K = 2..5 (E_n = 0 for n < 0).
 template <class LT, int K, typename T>
 __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
@@ -187,16 +198,15 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
 
     // rest velocity: s = 0, A = -tr Pi, B = 0; h2 = -v2, h4 = 3 v2^2
     {
-        const T w = T(LT::w0);
-        T feq = w * drho;
+        T feq = drho;
         T fh = -trP;
         if constexpr (K >= 4) {
-            feq += w * rho * (v2 * v2 * T(3.0 / 24.0) - v2 * T(0.5));
+            feq += rho * (v2 * v2 * T(3.0 / 24.0) - v2 * T(0.5));
             fh = -trP * (T(1) - v2 * T(0.5)) + R;
         } else {
-            feq -= w * rho * v2 * T(0.5);
+            feq -= rho * v2 * T(0.5);
         }
-        g[0] = feq + kappa * T(LT::w0) * fh;
+        g[0] = feq + kappa * fh;
     }
 #pragma unroll
     for (int p = 0; p < LT::NP; ++p) {
@@ -213,10 +223,8 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
         }
         const T A = cPc * iT0 - trP;
         const ScalarHermite<K, T> H(s, v2);
-        const T w = T(LT::w(p));
-        const T wr = w * rho;
-        const T feq_e = w * drho + wr * H.feq_even();
-        const T feq_o = wr * H.feq_odd(s);
+        const T feq_e = drho + rho * H.feq_even();
+        const T feq_o = rho * H.feq_odd(s);
         T fh_e, fh_o;  // bracket of Eq. hermite-coll, even / odd parts
         if constexpr (K == 2) {
             fh_e = A;
@@ -231,16 +239,15 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
             fh_e = A * e2 - T(2) * B * s + R;
             fh_o = A * (s + H.h3 * T(1.0 / 6.0)) - T(2) * B * e2 + R * s;
         }
-        const T kw = kappa * w;
-        const T e = feq_e + kw * fh_e;
+        const T e = feq_e + kappa * fh_e;
         T o = feq_o;
-        if constexpr (K >= 3) o += kw * fh_o;
+        if constexpr (K >= 3) o += kappa * fh_o;
         g[2 * p + 1] = e + o;
         g[2 * p + 2] = e - o;
     }
 }
 
-// Shifted equilibrium f^eq_K(rho, u) - w rho0 for every velocity (set_fields).
+// Scaled shifted equilibrium (f^eq_K(rho, u) - w rho0) / w for every velocity (set_fields).
 template <class LT, int K, typename T>
 __device__ __forceinline__ void equilibrium_shifted(T rho, T drho, const T (&u)[3], T (&g)[LT::Q]) {
     constexpr int D = LT::D;
@@ -253,10 +260,9 @@ __device__ __forceinline__ void equilibrium_shifted(T rho, T drho, const T (&u)[
         v2 += u[a] * us[a];
     }
     {
-        const T w = T(LT::w0);
         T e = -v2 * T(0.5);
         if constexpr (K >= 4) e += v2 * v2 * T(3.0 / 24.0);
-        g[0] = w * drho + w * rho * e;
+        g[0] = drho + rho * e;
     }
 #pragma unroll
     for (int p = 0; p < LT::NP; ++p) {
@@ -264,9 +270,8 @@ __device__ __forceinline__ void equilibrium_shifted(T rho, T drho, const T (&u)[
 #pragma unroll
         for (int a = 0; a < D; ++a) accumulate_scaled(s, LT::c(p, a), us[a]);
         const ScalarHermite<K, T> H(s, v2);
-        const T w = T(LT::w(p));
-        const T feq_e = w * drho + w * rho * H.feq_even();
-        const T feq_o = w * rho * H.feq_odd(s);
+        const T feq_e = drho + rho * H.feq_even();
+        const T feq_o = rho * H.feq_odd(s);
         g[2 * p + 1] = feq_e + feq_o;
         g[2 * p + 2] = feq_e - feq_o;
     }

@@ -101,9 +101,22 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
     bool ok[2 * kMaxDl + 1];
 #pragma unroll
     for (int dl = -kMaxDl; dl <= kMaxDl; ++dl)
-        ok[dl + kMaxDl] = lane + dl >= 0 && lane + dl <= 31 && chunk + dl >= 0 && chunk + dl < ncx;
+        ok[dl + kMaxDl] = V > 1 && lane + dl >= 0 && lane + dl <= 31 && chunk + dl >= 0 && chunk + dl < ncx;
 
     T f[Q][V];
+    if constexpr (V == 1) {
+        // one cell per thread: load the x-shifted element directly (the warp's load is still
+        // one contiguous span; the neighbour warps' loads keep the extra sector in cache)
+        int xs[2 * M + 1];
+#pragma unroll
+        for (int k = -M; k <= M; ++k) xs[k + M] = wrap1(x0 - k, nx);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = vel<LT>(i, 0), cy = vel<LT>(i, 1), cz = vel<LT>(i, 2);
+            const S *row = src + (long long)i * P + (long long)(zs[cz + M] * ny + ys[cy + M]) * nx;
+            f[i][0] = decode<ST, LT>(row[xs[cx + M]], i);
+        }
+    } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = vel<LT>(i, 0), cy = vel<LT>(i, 1), cz = vel<LT>(i, 2);
@@ -133,6 +146,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
                 }
             }
         }
+    }
     }
 
 #pragma unroll
@@ -303,7 +317,7 @@ __device__ __forceinline__ void pull_cell(const typename ST::S *__restrict__ src
         const int xs = wrapn(x - vel<LT>(i, 0), nx);
         const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
         const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
-        gt[i] = double(decode<ST, LT>(src[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs], i));
+        gt[i] = weight<LT>(i) * double(decode<ST, LT>(src[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs], i));
     }
 }
 
@@ -421,13 +435,14 @@ __global__ void __launch_bounds__(kReduceThreads) conservation_kernel(const type
     v[0] = double(n) * rho0;
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) {
-        v[0] += acc[i];
+        const double gsum = weight<LT>(i) * acc[i];  // stored values are scaled by 1/w_i
+        v[0] += gsum;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const int c = vel<LT>(i, a);
-            if (c == 1) v[1 + a] += acc[i];
-            else if (c == -1) v[1 + a] -= acc[i];
-            else if (c != 0) v[1 + a] += double(c) * acc[i];
+            if (c == 1) v[1 + a] += gsum;
+            else if (c == -1) v[1 + a] -= gsum;
+            else if (c != 0) v[1 + a] += double(c) * gsum;
         }
     }
     block_reduce_store<4>(v, partials);

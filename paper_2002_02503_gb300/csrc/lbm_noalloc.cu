@@ -79,9 +79,10 @@ __global__ void __launch_bounds__(kNoallocThreads) plane_sums_kernel(const typen
     double v[4] = {double(n) * rho0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) {
-        v[0] += acc[i];
+        const double gsum = weight<LT>(i) * acc[i];  // stored values are scaled by 1/w_i
+        v[0] += gsum;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) v[1 + a] += double(vel<LT>(i, a)) * acc[i];
+        for (int a = 0; a < 3; ++a) v[1 + a] += double(vel<LT>(i, a)) * gsum;
     }
     block_reduce_store<4>(v, partials);
 }

@@ -32,7 +32,8 @@ def to_lib_order(name, f_oracle):
 
 
 def raw_from_f(name, dims, f_lib, storage, rho0=1.0):
-    """Stored representation of pre-collision f (library order): g_i(y) = f_i(y + c_i), shifted by w_i rho0."""
+    """Stored representation of pre-collision f (library order): g_i(y) = f_i(y + c_i), stored as
+    (g_i - w_i rho0) / w_i in the storage type."""
     import torch
 
     info = lbm.lbm_lattice_info(name)
@@ -43,11 +44,11 @@ def raw_from_f(name, dims, f_lib, storage, rho0=1.0):
         cx, cy, cz = info["c"][i]
         a = np.roll(a, (-cz, -cy, -cx), axis=(0, 1, 2))  # a'[y] = a[y + c]
         out[i] = a.reshape(-1) - info["w"][i] * rho0
+    scaled = out / info["w"][:, None]  # every storage form holds (g - w rho0) / w
     if storage == "f64":
-        return out.astype(np.float64)
+        return scaled.astype(np.float64)
     if storage == "f32":
-        return out.astype(np.float32)
-    scaled = out / info["w"][:, None]
+        return scaled.astype(np.float32)
     if storage == "f16":
         return scaled.astype(np.float16)
     if storage == "bf16":
