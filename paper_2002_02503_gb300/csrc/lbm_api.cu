@@ -157,6 +157,12 @@ struct lbm_solver {
     long long t;
     const KernelSet *ks;
     int variant, V, block;
+    // Captured graphs of kGraphSteps consecutive steps, one per starting buffer; rebuilt
+    // when the kernel configuration changes.  They cut the per-step launch cost, which
+    // dominates on small lattices.
+    cudaGraphExec_t graph[2];
+    int graph_cfg[3];
+    cudaStream_t capture;
 };
 
 namespace {
@@ -308,9 +314,13 @@ lbm_status lbm_create(lbm_lattice lat, const int64_t dims[3], double tau, int K,
     return LBM_OK;
 }
 
+static void drop_step_graphs(lbm_solver *s);
+
 lbm_status lbm_destroy(lbm_solver *s) {
     if (!s) return LBM_OK;
     cudaError_t e = cudaStreamSynchronize(s->stream);
+    drop_step_graphs(s);
+    if (s->capture) cudaStreamDestroy(s->capture);
     delete s;
     if (e != cudaSuccess) return cuda_fail(e, "lbm_destroy: stream synchronize");
     return LBM_OK;
@@ -365,11 +375,65 @@ lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm
     return LBM_OK;
 }
 
+static void drop_step_graphs(lbm_solver *s) {
+    for (int b = 0; b < 2; ++b)
+        if (s->graph[b]) {
+            cudaGraphExecDestroy(s->graph[b]);
+            s->graph[b] = nullptr;
+        }
+}
+
+constexpr int kGraphSteps = 32;  // even: a graph leaves the state in the buffer it started from
+
+// Graph of kGraphSteps steps starting from buffer `from` (captured on a private stream).
+static cudaError_t step_graph(lbm_solver *s, step_fn fn, int from, cudaGraphExec_t *out) {
+    if (s->graph_cfg[0] != s->variant || s->graph_cfg[1] != s->V || s->graph_cfg[2] != s->block) {
+        drop_step_graphs(s);
+        s->graph_cfg[0] = s->variant;
+        s->graph_cfg[1] = s->V;
+        s->graph_cfg[2] = s->block;
+    }
+    if (s->graph[from]) {
+        *out = s->graph[from];
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!s->capture) e = cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) le = fn(step_args(s, from ^ (k & 1)), s->block, s->capture);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s->capture, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le != cudaSuccess ? le : e;
+    }
+    e = cudaGraphInstantiate(&s->graph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->graph[from] = nullptr;
+        return e;
+    }
+    *out = s->graph[from];
+    return cudaSuccess;
+}
+
 lbm_status lbm_step(lbm_solver *s, int64_t n) {
     if (lbm_status r = check_solver(s)) return r;
     if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
     step_fn fn = step_for(s, s->variant, s->V);
     if (!fn) return fail(LBM_ERR_UNSUPPORTED, "kernel configuration not built");
+    while (n >= kGraphSteps) {
+        cudaGraphExec_t g = nullptr;
+        cudaError_t e = step_graph(s, fn, s->cur, &g);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_step: graph capture");
+        e = cudaGraphLaunch(g, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lbm_step: graph launch");
+        s->t += kGraphSteps;
+        n -= kGraphSteps;
+    }
     for (int64_t k = 0; k < n; ++k) {
         StepArgs a = step_args(s, s->cur);
         cudaError_t e = fn(a, s->block, s->stream);

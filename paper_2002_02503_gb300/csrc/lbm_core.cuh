@@ -63,6 +63,52 @@ struct StoreBF16 {
     __device__ __forceinline__ static S enc(T x) { return __float2bfloat16_rn(x); }
 };
 
+// Vector decode / encode of V consecutive values of one velocity plane; the 16-bit
+// forms convert two values per instruction (half2 / bfloat162).
+template <class ST, int V>
+__device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typename ST::T (&out)[V]) {
+    if constexpr (ST::id == LBM_STORE_F16 && V % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            const float2 f = __half22float2(__halves2half2(raw[j], raw[j + 1]));
+            out[j] = f.x;
+            out[j + 1] = f.y;
+        }
+    } else if constexpr (ST::id == LBM_STORE_BF16 && V % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            const float2 f = __bfloat1622float2(__halves2bfloat162(raw[j], raw[j + 1]));
+            out[j] = f.x;
+            out[j + 1] = f.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) out[j] = ST::dec(raw[j]);
+    }
+}
+
+template <class ST, int V>
+__device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typename ST::S (&raw)[V]) {
+    if constexpr (ST::id == LBM_STORE_F16 && V % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            const __half2 h = __floats2half2_rn(in[j], in[j + 1]);
+            raw[j] = __low2half(h);
+            raw[j + 1] = __high2half(h);
+        }
+    } else if constexpr (ST::id == LBM_STORE_BF16 && V % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(in[j], in[j + 1]);
+            raw[j] = __low2bfloat16(h);
+            raw[j + 1] = __high2bfloat16(h);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) raw[j] = ST::enc(in[j]);
+    }
+}
+
 // Scaled value h of velocity i (the weight index is kept for call sites that need it).
 template <class ST, class LT>
 __device__ __forceinline__ typename ST::T decode(typename ST::S v, int) {

@@ -124,8 +124,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         S raw[V];
         load_vec<S, V>(row + x0, raw);
         T v[V];
-#pragma unroll
-        for (int j = 0; j < V; ++j) v[j] = decode<ST, LT>(raw[j], i);
+        decode_vec<ST, V>(raw, v);
         if (cx == 0) {
 #pragma unroll
             for (int j = 0; j < V; ++j) f[i][j] = v[j];
@@ -164,8 +163,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             S raw[V];
-#pragma unroll
-            for (int j = 0; j < V; ++j) raw[j] = encode<ST, LT>(f[i][j], i);
+            encode_vec<ST, V>(f[i], raw);
             store_vec<S, V>(out + (long long)i * P, raw);
         }
     }

@@ -13,6 +13,8 @@ u0 ~ U[0.01, 0.08], steps ~ U{100..2000}, Poisson arrivals at ``rate`` per secon
 """
 import collections
 import math
+import queue
+import threading
 import time
 
 import numpy as np
@@ -40,6 +42,25 @@ def request_fields(r):
     return fields.taylor_green_3d(d, r["u0"], T0_D3Q19)
 
 
+class Producer:
+    """Client side: generates each request's initial fields ahead of its arrival, in arrival
+    order, on a background thread (bounded look-ahead), so that the scheduler loop only
+    admits, advances and collects."""
+
+    def __init__(self, trace, ahead=32):
+        self.order = sorted(trace, key=lambda r: r["arrival"])
+        self.q = queue.Queue(maxsize=ahead)
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def _run(self):
+        for r in self.order:
+            self.q.put((r, request_fields(r)))
+
+    def next(self):
+        return self.q.get()
+
+
 def _summary(lat, t_total, cells):
     lat = np.array(sorted(lat))
     return {"solves": int(len(lat)), "seconds": t_total, "solves_per_s": len(lat) / t_total,
@@ -51,8 +72,10 @@ def serve_pool(trace, K=3, storage="f32", arena_bytes=48 << 30, max_slots=512, c
                autotune=True):
     """Continuous batching.  keep: optional set of request indices whose results are returned."""
     pool = lbm.Pool("D3Q19", K, storage, arena_bytes, max_slots)
+    producer = Producer(trace)
     pending = collections.deque(sorted(trace, key=lambda r: r["arrival"]))
     waiting = collections.deque()
+    ready = {}
     active = {}
     lat, results = [], {}
     cells = 0
@@ -64,10 +87,14 @@ def serve_pool(trace, K=3, storage="f32", arena_bytes=48 << 30, max_slots=512, c
             waiting.append(pending.popleft())
         while waiting:
             r = waiting[0]
-            rho, u = request_fields(r)
+            while r["i"] not in ready:
+                rr, fl = producer.next()
+                ready[rr["i"]] = fl
+            rho, u = ready[r["i"]]
             rid = pool.submit((r["side"],) * 3, r["tau"], rho, u, r["steps"])
             if rid is None:
                 break
+            del ready[r["i"]]
             active[rid] = r
             waiting.popleft()
         if not tuned and len(active) >= 8:
@@ -104,17 +131,17 @@ def serve_plain(trace, K=3, storage="f32", keep=None):
     smax = max(r["side"] for r in trace)
     ws_bytes = lbm.lbm_workspace_bytes("D3Q19", (smax,) * 3, storage)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
-    order = sorted(trace, key=lambda r: r["arrival"])
+    producer = Producer(trace)
     lat, results = [], {}
     cells = 0
     t0 = time.perf_counter()
-    for r in order:
+    for _ in range(len(trace)):
+        r, (rho, u) = producer.next()
         now = time.perf_counter() - t0
         if r["arrival"] > now:
             time.sleep(r["arrival"] - now)
         d = (r["side"],) * 3
         C = r["side"] ** 3
-        rho, u = request_fields(r)
         h = lbm.lbm_create("D3Q19", d, r["tau"], K, storage, 1.0, ws.data_ptr(), ws_bytes, stream.cuda_stream)
         lbm.lbm_set_fields(h, rho, u)
         lbm.lbm_step(h, r["steps"])
