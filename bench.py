@@ -26,8 +26,8 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-LATTICE_Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27, "D3Q39": 39}
-LATTICE_T0 = {"D2Q9": 1.0 / 3.0, "D3Q19": 1.0 / 3.0, "D3Q27": 1.0 / 3.0, "D3Q39": 2.0 / 3.0}
+LATTICE_Q = {"D2Q9": 9, "D3Q15": 15, "D3Q19": 19, "D3Q27": 27, "D3Q39": 39}
+LATTICE_T0 = {"D2Q9": 1.0 / 3.0, "D3Q15": 1.0 / 3.0, "D3Q19": 1.0 / 3.0, "D3Q27": 1.0 / 3.0, "D3Q39": 2.0 / 3.0}
 STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}
 DTYPE_NAME = {"f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)", "f64": "f64"}
 KERNEL_SOURCES = ["lbm_core.cuh", "lbm_kernels.cuh", "lbm_lattice.cuh"]

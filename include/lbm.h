@@ -46,9 +46,9 @@ typedef enum {
     LBM_ERR_NOT_FOUND = 8      /* unknown request id */
 } lbm_status;
 
-/* Velocity sets.  D2Q9, D3Q19: isotropy class 2N = 4, T0 = 1/3 (Sec. 2 after
- * Eq. iso); D3Q39: 2N = 6, T0 = 2/3; D3Q27 (not in the paper): 2N = 4, T0 = 1/3. */
-typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2, LBM_D3Q39 = 3 } lbm_lattice;
+/* Velocity sets.  D2Q9, D3Q15, D3Q19: isotropy class 2N = 4, T0 = 1/3 (Sec. 2
+ * after Eq. iso); D3Q39: 2N = 6, T0 = 2/3; D3Q27 (not in the paper): 2N = 4, T0 = 1/3. */
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2, LBM_D3Q39 = 3, LBM_D3Q15 = 4 } lbm_lattice;
 
 /* How distributions are stored in HBM.  The collision always computes in FP32
  * (FP64 for LBM_STORE_F64).  Every form stores the shifted, scaled value

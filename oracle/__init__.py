@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2, "D3Q39": 3}
+LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2, "D3Q39": 3, "D3Q15": 4}
 MAX_K = 10
 
 _lib = None

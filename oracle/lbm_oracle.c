@@ -24,7 +24,7 @@
  * recursion of Eq. recurG (Appendix), H^(0)=1, H^(1)_a = xi_a.
  *
  * Lattice tables: the paper fixes T0 = 1/3 for D3Q15/D3Q19 (Sec. 2, after
- * Eq. iso) and the isotropy classes 2N (D2Q9, D3Q19: 4; D3Q39: 6), but prints
+ * Eq. iso) and the isotropy classes 2N (D2Q9, D3Q15, D3Q19: 4; D3Q39: 6), but prints
  * no weights.  The standard velocity sets below are used; the test suite checks
  * them against the isotropy identities of Eq. iso.  D3Q27 is not in the paper;
  * it is the standard 27-velocity set (isotropy class 4).
@@ -40,7 +40,7 @@
 #define ORC_MAXQ 39
 #define ORC_MAX_K 10 /* highest Hermite order the oracle builds (3^10 tensor entries) */
 
-enum { ORC_D2Q9 = 0, ORC_D3Q19 = 1, ORC_D3Q27 = 2, ORC_D3Q39 = 3 };
+enum { ORC_D2Q9 = 0, ORC_D3Q19 = 1, ORC_D3Q27 = 2, ORC_D3Q39 = 3, ORC_D3Q15 = 4 };
 
 typedef struct {
     int D, Q;
@@ -86,6 +86,13 @@ static int make_lattice(int lat, orc_lattice_t *L) {
         add_shell(L, 2, 0, 0, 0, 4.0 / 9.0);
         add_shell(L, 2, 1, 0, 0, 1.0 / 9.0);
         add_shell(L, 2, 1, 1, 0, 1.0 / 36.0);
+        break;
+    case ORC_D3Q15: /* w = 2/9, 1/9, 1/72; T0 = 1/3 */
+        L->D = 3;
+        L->T0 = 1.0 / 3.0;
+        add_shell(L, 3, 0, 0, 0, 2.0 / 9.0);
+        add_shell(L, 3, 1, 0, 0, 1.0 / 9.0);
+        add_shell(L, 3, 1, 1, 1, 1.0 / 72.0);
         break;
     case ORC_D3Q19: /* w = 1/3, 1/18, 1/36; T0 = 1/3 */
         L->D = 3;

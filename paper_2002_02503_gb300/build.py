@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
 
-UNITS = ["lbm_api.cu", "lbm_inst_d2q9.cu", "lbm_inst_d3q19.cu", "lbm_inst_d3q27.cu", "lbm_inst_d3q39.cu",
+UNITS = ["lbm_api.cu", "lbm_inst_d2q9.cu", "lbm_inst_d3q15.cu", "lbm_inst_d3q19.cu", "lbm_inst_d3q27.cu", "lbm_inst_d3q39.cu",
          "lbm_batch.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -58,6 +58,7 @@ LatInfo info_of() {
 bool lattice_info(lbm_lattice lat, LatInfo *out) {
     switch (lat) {
     case LBM_D2Q9: *out = info_of<D2Q9>(); return true;
+    case LBM_D3Q15: *out = info_of<D3Q15>(); return true;
     case LBM_D3Q19: *out = info_of<D3Q19>(); return true;
     case LBM_D3Q27: *out = info_of<D3Q27>(); return true;
     case LBM_D3Q39: *out = info_of<D3Q39>(); return true;
@@ -87,6 +88,7 @@ size_t storage_size(lbm_storage st) {
 const KernelSet *kernels_for(lbm_lattice lat, int K, lbm_storage st) {
     switch (lat) {
     case LBM_D2Q9: return kernels_d2q9(K, st);
+    case LBM_D3Q15: return kernels_d3q15(K, st);
     case LBM_D3Q19: return kernels_d3q19(K, st);
     case LBM_D3Q27: return kernels_d3q27(K, st);
     case LBM_D3Q39: return kernels_d3q39(K, st);
@@ -239,6 +241,7 @@ lbm_status lbm_lattice_info(lbm_lattice lat, int *D, int *Q, int *c, double *w, 
     if (kmax) *kmax = li.kmax;
     switch (lat) {
     case LBM_D2Q9: fill_table<D2Q9>(c, w); break;
+    case LBM_D3Q15: fill_table<D3Q15>(c, w); break;
     case LBM_D3Q19: fill_table<D3Q19>(c, w); break;
     case LBM_D3Q27: fill_table<D3Q27>(c, w); break;
     case LBM_D3Q39: fill_table<D3Q39>(c, w); break;

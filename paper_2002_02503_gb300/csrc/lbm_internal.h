@@ -98,6 +98,7 @@ struct KernelSet {
 
 // Defined in the instantiation units, one per lattice.
 const KernelSet *kernels_d2q9(int K, lbm_storage st);
+const KernelSet *kernels_d3q15(int K, lbm_storage st);
 const KernelSet *kernels_d3q19(int K, lbm_storage st);
 const KernelSet *kernels_d3q27(int K, lbm_storage st);
 const KernelSet *kernels_d3q39(int K, lbm_storage st);

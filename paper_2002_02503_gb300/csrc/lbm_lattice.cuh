@@ -5,8 +5,8 @@
 // even and odd parts of the collision (c -> -c flips s = c.u/T0 and c.Pi.u, and
 // keeps c.Pi.c), so a kernel evaluates the collision once per pair.
 //
-// The paper fixes T0 = 1/3 for D3Q19 and the isotropy classes 2N (D2Q9 and D3Q19:
-// 4, D3Q39: 6) in Sec. 2 after Eq. iso; the weights are the standard ones of each
+// The paper fixes T0 = 1/3 for D3Q15 and D3Q19 and the isotropy classes 2N (D2Q9,
+// D3Q15 and D3Q19: 4, D3Q39: 6) in Sec. 2 after Eq. iso; the weights are the standard ones of each
 // set (D3Q27 is not in the paper; its class is 4).  kmax = 2N - 1 is the highest
 // Hermite order a truncation may keep (Sec. 2 and Sec. 3 truncation rule).
 #pragma once
@@ -25,6 +25,18 @@ struct D2Q9 {
         return t[p][a];
     }
     __host__ __device__ static constexpr double w(int p) { return p < 2 ? 1.0 / 9.0 : 1.0 / 36.0; }
+};
+
+struct D3Q15 {
+    static constexpr lbm_lattice id = LBM_D3Q15;
+    static constexpr int D = 3, Q = 15, NP = 7, MAXC = 1, KMAX = 3;
+    static constexpr double T0 = 1.0 / 3.0;
+    static constexpr double w0 = 2.0 / 9.0;
+    __host__ __device__ static constexpr int c(int p, int a) {
+        constexpr int t[NP][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 1}, {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
+        return t[p][a];
+    }
+    __host__ __device__ static constexpr double w(int p) { return p < 3 ? 1.0 / 9.0 : 1.0 / 72.0; }
 };
 
 struct D3Q19 {

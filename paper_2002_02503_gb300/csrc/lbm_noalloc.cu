@@ -137,6 +137,7 @@ extern "C" lbm_status lbm_conservation_noalloc(lbm_lattice lattice, lbm_storage 
     const int nx = int(dims[0]), ny = int(dims[1]), nz = int(dims[2]);
     switch (lattice) {
     case LBM_D2Q9: e = dispatch_storage<D2Q9>(storage, distributions, nx, ny, nz, rho0, scratch, result, stream); break;
+    case LBM_D3Q15: e = dispatch_storage<D3Q15>(storage, distributions, nx, ny, nz, rho0, scratch, result, stream); break;
     case LBM_D3Q19: e = dispatch_storage<D3Q19>(storage, distributions, nx, ny, nz, rho0, scratch, result, stream); break;
     case LBM_D3Q27: e = dispatch_storage<D3Q27>(storage, distributions, nx, ny, nz, rho0, scratch, result, stream); break;
     case LBM_D3Q39: e = dispatch_storage<D3Q39>(storage, distributions, nx, ny, nz, rho0, scratch, result, stream); break;

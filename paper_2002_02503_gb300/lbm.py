@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "liblbm_gb300.so")
 
 LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
 LBM_ERR_CUDA, LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_BUSY, LBM_ERR_NOT_FOUND = 4, 5, 6, 7, 8
-LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2, "D3Q39": 3}
+LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2, "D3Q39": 3, "D3Q15": 4}
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3}
 STORAGE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}
 MEM_HOST, MEM_DEVICE = 0, 1

@@ -14,6 +14,7 @@ TOL_U16 = 1e-3   # relative error on u for shifted 16-bit storage
 
 DIMS = {  # ragged sizes: several thread blocks per plane and a partial last block
     "D2Q9": (72, 44, 1),
+    "D3Q15": (44, 22, 14),
     "D3Q19": (40, 26, 14),
     "D3Q27": (36, 22, 12),
     "D3Q39": (28, 18, 10),

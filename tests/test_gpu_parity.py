@@ -14,7 +14,7 @@ from _lbmtest import (DIMS, TOL_F32, TOL_F64, oracle_reference, perm_lib_to_orac
 
 pytestmark = pytest.mark.gpu
 
-CASES = [("D2Q9", 2), ("D2Q9", 3), ("D3Q19", 2), ("D3Q19", 3), ("D3Q27", 2), ("D3Q27", 3),
+CASES = [("D2Q9", 2), ("D2Q9", 3), ("D3Q15", 2), ("D3Q15", 3), ("D3Q19", 2), ("D3Q19", 3), ("D3Q27", 2), ("D3Q27", 3),
          ("D3Q39", 2), ("D3Q39", 3), ("D3Q39", 4), ("D3Q39", 5)]
 
 

@@ -17,8 +17,8 @@ import pytest
 
 import oracle
 
-ALL = ["D2Q9", "D3Q19", "D3Q27", "D3Q39"]
-KMAX = {"D2Q9": 3, "D3Q19": 3, "D3Q27": 3, "D3Q39": 5}
+ALL = ["D2Q9", "D3Q15", "D3Q19", "D3Q27", "D3Q39"]
+KMAX = {"D2Q9": 3, "D3Q15": 3, "D3Q19": 3, "D3Q27": 3, "D3Q39": 5}
 
 
 def _setup(name, seed=1, umag=0.1):

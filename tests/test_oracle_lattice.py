@@ -23,7 +23,7 @@ from numpy.polynomial import hermite_e
 import oracle
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_lattice_facts.txt")
-ALL = ["D2Q9", "D3Q19", "D3Q27", "D3Q39"]
+ALL = ["D2Q9", "D3Q15", "D3Q19", "D3Q27", "D3Q39"]
 
 
 def _exact(lat):
@@ -78,7 +78,7 @@ def test_weights_sum_to_one_and_velocities_distinct():
         assert sum(w) == 1
         assert len({tuple(c) for c in lat["c"]}) == lat["Q"]
         assert all(x > 0 for x in w)
-    assert [oracle.lattice(n)["Q"] for n in ALL] == [9, 19, 27, 39]
+    assert [oracle.lattice(n)["Q"] for n in ALL] == [9, 15, 19, 27, 39]
 
 
 def test_isotropy_class_matches_paper_statements():
@@ -102,7 +102,7 @@ def test_isotropy_class_matches_paper_statements():
 
 def test_isotropy_class_all_lattices():
     # D3Q27 is not in the paper: the same identities give class 4 (E^(6) fails).
-    assert [_isotropy_class(oracle.lattice(n)) for n in ALL] == [4, 4, 4, 6]
+    assert [_isotropy_class(oracle.lattice(n)) for n in ALL] == [4, 4, 4, 4, 6]
     assert Fraction(oracle.lattice("D3Q39")["T0"]).limit_denominator(100) == Fraction(2, 3)
 
 
@@ -149,7 +149,7 @@ def test_hermite_tensor_symmetric_and_explicit_low_orders(name):
             np.testing.assert_allclose(np.transpose(H5, p), H5, atol=1e-12)
 
 
-@pytest.mark.parametrize("name,twoN", [("D2Q9", 4), ("D3Q19", 4), ("D3Q27", 4), ("D3Q39", 6)])
+@pytest.mark.parametrize("name,twoN", [("D2Q9", 4), ("D3Q15", 4), ("D3Q19", 4), ("D3Q27", 4), ("D3Q39", 6)])
 def test_hermite_orthogonality_under_lattice_weights(name, twoN):
     """sum_i w_i [H^(m):a^m][H^(n):b^n] = delta_mn n! (a.b)^n whenever m+n <= 2N+1."""
     lat = oracle.lattice(name)
