@@ -251,6 +251,26 @@ def recorded_traffic(a, variant, cpt):
     return r.get("bytes_per_launch")
 
 
+# ------------------------------------------------------------------ whole-job figures
+def combine_ranks(ms, e2e_value, world, device):
+    """Independent replicas, one lattice per rank: the job's timed-region time is the slowest
+    rank's (max over ranks), and its end-to-end rate is world x the slowest rank's rate."""
+    if world == 1:
+        return ms, e2e_value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms, -(e2e_value if e2e_value is not None else 0.0)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_job = -float(t[1]) * world if e2e_value is not None else None
+    return float(t[0]), e2e_job
+
+
+def job_mlups(cells_per_rank, steps, world, t_max_ms):
+    """Whole-job million lattice-cell updates per second."""
+    return world * cells_per_rank * steps / (t_max_ms / 1e3) / 1e6
+
+
 # ------------------------------------------------------------------ main arms
 def run_reference(a):
     rank, world, _ = dist_env()
@@ -343,18 +363,10 @@ def run_ours(a):
         s.close()
     clocks.stop()
 
-    t_max = ms
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        if e2e is not None:
-            ee = torch.tensor([e2e["value"]], device="cuda", dtype=torch.float64)
-            dist.all_reduce(ee, op=dist.ReduceOp.MIN)
-            e2e["value"] = float(ee.item()) * world
-    value = world * C * a.steps / (t_max / 1e3) / 1e6
+    t_max, e2e_job = combine_ranks(ms, e2e["value"] if e2e is not None else None, world, "cuda")
+    if e2e is not None:
+        e2e["value"] = e2e_job
+    value = job_mlups(C, a.steps, world, t_max)
     if rank == 0:
         bpu = 2 * Q * STORE_BYTES[a.storage]
         per_launch_s = (ms / 1e3) / a.steps
