@@ -134,6 +134,15 @@ lbm_status lbm_time(const lbm_solver *s, int64_t *t);
 lbm_status lbm_set_kernel(lbm_solver *s, int variant, int cells_per_thread, int block_threads);
 lbm_status lbm_get_kernel(const lbm_solver *s, int *variant, int *cells_per_thread, int *block_threads);
 
+/* Collision operator of the step.  LBM_COLLISION_FILTERED_GI (the default) is
+ * the paper's filtered collision, Eq. lbe-reg with the truncated Eq. hermite-coll.
+ * LBM_COLLISION_BGK is Eq. BGK, C_i = -(f_i - f^eq_i)/tau, with the same truncated
+ * f^eq: the unfiltered comparison baseline of Sec. 1 and Sec. 4 (it relaxes every
+ * non-equilibrium moment, including those the lattice does not support).  The BGK
+ * step runs one cell per thread; selecting it resets the kernel configuration. */
+typedef enum { LBM_COLLISION_FILTERED_GI = 0, LBM_COLLISION_BGK = 1 } lbm_collision;
+lbm_status lbm_set_collision(lbm_solver *s, lbm_collision model);
+
 /* Autotuner: times every built kernel configuration for this solver on its own
  * buffers (reads the current state, writes only the idle buffer, so the state is
  * unchanged) over `iters` launches each and keeps the fastest.  best_us, if not

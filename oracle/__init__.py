@@ -39,6 +39,9 @@ def _load():
         lib.orc_init_eq.argtypes = [ctypes.c_int, ctypes.c_int, i64p, dp, dp, dp, ctypes.c_int]
         lib.orc_moments.argtypes = [ctypes.c_int, i64p, dp, dp, dp]
         lib.orc_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, i64p, dp, ctypes.c_int64, ctypes.c_int]
+        lib.orc_run_model.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, i64p, dp,
+                                      ctypes.c_int64, ctypes.c_int]
+        lib.orc_collide_bgk.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
         _lib = lib
     return _lib
 
@@ -165,15 +168,28 @@ def default_threads():
         return max(1, os.cpu_count() or 1)
 
 
-def run(name, K, tau, dims, f, nsteps, nthreads=None):
-    """Advance f [Q, C] by nsteps of collide + push (Eq. lbe-reg, Eq. lbe); returns a new array."""
+MODELS = {"filtered": 0, "bgk": 1}
+
+
+def collide_bgk(name, K, tau, f):
+    """One cell with the BGK operator (Eq. BGK) and the truncated f^eq."""
+    Q = lattice(name)["Q"]
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(Q)
+    _check(_load().orc_collide_bgk(_lat(name), int(K), float(tau), _dp(f), _dp(out)), "collide_bgk")
+    return out
+
+
+def run(name, K, tau, dims, f, nsteps, nthreads=None, model="filtered"):
+    """Advance f [Q, C] by nsteps of collide + push (Eq. lbe-reg, or Eq. BGK with model="bgk", and
+    Eq. lbe); returns a new array."""
     lat = lattice(name)
     d = _dims(dims)
     C = int(np.prod(d))
     out = np.array(f, dtype=np.float64, copy=True).reshape(lat["Q"], C)
     out = np.ascontiguousarray(out)
     nt = default_threads() if nthreads is None else int(nthreads)
-    rc = _load().orc_run(_lat(name), int(K), float(tau), d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                         _dp(out), int(nsteps), nt)
+    rc = _load().orc_run_model(_lat(name), int(K), float(tau), MODELS[model],
+                               d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out), int(nsteps), nt)
     _check(rc, "run")
     return out

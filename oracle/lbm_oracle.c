@@ -311,10 +311,25 @@ static void moments_cell(const orc_lattice_t *L, const double *f, double *rho, d
     for (int a = 0; a < 3; ++a) u[a] = j[a] / r;
 }
 
+/* Collision models: the paper's filtered collision (Eq. lbe-reg), or the BGK
+ * operator of Eq. BGK, C_i = -(f_i - f^eq_i)/tau, with the same truncated f^eq --
+ * the unfiltered baseline the paper compares against in Sec. 1 and Sec. 4. */
+enum { ORC_FILTERED = 0, ORC_BGK = 1 };
+
 /* One cell through steps 1-6 of the header.  Intermediates are returned when
  * the pointers are non-NULL. */
+static void collide_cell_model(const orc_ctx_t *ctx, orc_work_t *wk, double tau, int model, const double *f,
+                               double *fpost, double *rho_out, double *u_out, double *feq_out, double *Pi_out,
+                               double *fhat_out);
+
 static void collide_cell(const orc_ctx_t *ctx, orc_work_t *wk, double tau, const double *f, double *fpost,
                          double *rho_out, double *u_out, double *feq_out, double *Pi_out, double *fhat_out) {
+    collide_cell_model(ctx, wk, tau, ORC_FILTERED, f, fpost, rho_out, u_out, feq_out, Pi_out, fhat_out);
+}
+
+static void collide_cell_model(const orc_ctx_t *ctx, orc_work_t *wk, double tau, int model, const double *f,
+                               double *fpost, double *rho_out, double *u_out, double *feq_out, double *Pi_out,
+                               double *fhat_out) {
     const orc_lattice_t *L = &ctx->L;
     double rho, u[3], feq[ORC_MAXQ], fneq[ORC_MAXQ], fhat[ORC_MAXQ];
     moments_cell(L, f, &rho, u);
@@ -329,7 +344,10 @@ static void collide_cell(const orc_ctx_t *ctx, orc_work_t *wk, double tau, const
     }
     fneq_hat_cell(ctx, wk, u, (const double(*)[3])Pi, fhat);
     double relax = 1.0 - 1.0 / tau;
-    for (int i = 0; i < L->Q; ++i) fpost[i] = feq[i] + relax * fhat[i];
+    if (model == ORC_BGK) /* Eq. BGK: f' = f - (f - f^eq)/tau */
+        for (int i = 0; i < L->Q; ++i) fpost[i] = f[i] - (f[i] - feq[i]) / tau;
+    else
+        for (int i = 0; i < L->Q; ++i) fpost[i] = feq[i] + relax * fhat[i];
     if (rho_out) *rho_out = rho;
     if (u_out)
         for (int a = 0; a < 3; ++a) u_out[a] = u[a];
@@ -352,6 +370,7 @@ static long wrap(long v, long n) {
 typedef struct {
     const orc_ctx_t *ctx;
     double tau;
+    int model;
     long nx, ny, nz;
     const double *f;
     double *fnew;
@@ -375,7 +394,7 @@ static void *step_worker(void *arg) {
         for (long x = 0; x < job->nx; ++x) {
                 long cell = x + job->nx * (y + job->ny * z);
                 for (int i = 0; i < L->Q; ++i) fc[i] = job->f[i * C + cell];
-                collide_cell(job->ctx, &wk, job->tau, fc, fp, NULL, NULL, NULL, NULL, NULL);
+                collide_cell_model(job->ctx, &wk, job->tau, job->model, fc, fp, NULL, NULL, NULL, NULL, NULL);
                 for (int i = 0; i < L->Q; ++i) { /* Eq. lbe: push to x + c_i */
                     long xd = wrap(x + L->c[i][0], job->nx);
                     long yd = wrap(y + L->c[i][1], job->ny);
@@ -388,8 +407,8 @@ static void *step_worker(void *arg) {
     return NULL;
 }
 
-static int run_parallel(const orc_ctx_t *ctx, double tau, const int64_t *dims, const double *f, double *fnew,
-                        int nthreads) {
+static int run_parallel(const orc_ctx_t *ctx, double tau, int model, const int64_t *dims, const double *f,
+                        double *fnew, int nthreads) {
     long rows = dims[1] * dims[2];
     if (nthreads < 1) nthreads = 1;
     if (nthreads > rows) nthreads = (int)rows;
@@ -399,6 +418,7 @@ static int run_parallel(const orc_ctx_t *ctx, double tau, const int64_t *dims, c
     for (int t = 0; t < nthreads; ++t) {
         jobs[t].ctx = ctx;
         jobs[t].tau = tau;
+        jobs[t].model = model;
         jobs[t].nx = dims[0];
         jobs[t].ny = dims[1];
         jobs[t].nz = dims[2];
@@ -578,8 +598,10 @@ int orc_moments(int lat, const int64_t *dims, const double *f, double *rho, doub
     return 0;
 }
 
-/* nsteps of collide + push.  f holds f(t) on entry and f(t + nsteps) on exit. */
-int orc_run(int lat, int K, double tau, const int64_t *dims, double *f, int64_t nsteps, int nthreads) {
+/* nsteps of collide + push with the given collision model (ORC_FILTERED or ORC_BGK).
+ * f holds f(t) on entry and f(t + nsteps) on exit. */
+int orc_run_model(int lat, int K, double tau, int model, const int64_t *dims, double *f, int64_t nsteps,
+                  int nthreads) {
     orc_ctx_t ctx;
     int rc = ctx_init(lat, K, &ctx);
     if (rc) return rc;
@@ -595,13 +617,31 @@ int orc_run(int lat, int K, double tau, const int64_t *dims, double *f, int64_t 
     }
     double *a = f, *b = tmp;
     for (int64_t s = 0; s < nsteps && rc == 0; ++s) {
-        rc = run_parallel(&ctx, tau, dims, a, b, nthreads);
+        rc = run_parallel(&ctx, tau, model, dims, a, b, nthreads);
         double *t = a;
         a = b;
         b = t;
     }
     if (a != f) memcpy(f, a, n * sizeof(double));
     free(tmp);
+    ctx_free(&ctx);
+    return rc;
+}
+
+/* nsteps of the paper's filtered collision + push. */
+int orc_run(int lat, int K, double tau, const int64_t *dims, double *f, int64_t nsteps, int nthreads) {
+    return orc_run_model(lat, K, tau, ORC_FILTERED, dims, f, nsteps, nthreads);
+}
+
+/* One cell with the BGK operator (Eq. BGK) and the truncated f^eq. */
+int orc_collide_bgk(int lat, int K, double tau, const double *f, double *fpost) {
+    orc_ctx_t ctx;
+    int rc = ctx_init(lat, K, &ctx);
+    if (rc) return rc;
+    orc_work_t wk;
+    if (work_init(ctx.L.D, K, &wk)) rc = -3;
+    else collide_cell_model(&ctx, &wk, tau, ORC_BGK, f, fpost, NULL, NULL, NULL, NULL, NULL);
+    work_free(&wk);
     ctx_free(&ctx);
     return rc;
 }

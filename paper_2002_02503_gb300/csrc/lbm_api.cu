@@ -159,6 +159,7 @@ struct lbm_solver {
     long long t;
     const KernelSet *ks;
     int variant, V, block;
+    lbm_collision model;
     // Captured graphs of kGraphSteps consecutive steps, one per starting buffer; rebuilt
     // when the kernel configuration changes.  They cut the per-step launch cost, which
     // dominates on small lattices.
@@ -185,6 +186,7 @@ StepArgs step_args(const lbm_solver *s, int from) {
 }
 
 step_fn step_for(const lbm_solver *s, int variant, int V) {
+    if (s->model == LBM_COLLISION_BGK) return (variant == 0 && V == 1) ? s->ks->bgk : nullptr;
     if (variant == 0) {
         int k = v_index(V);
         if (k < 0 || s->nx % V) return nullptr;
@@ -305,6 +307,7 @@ lbm_status lbm_create(lbm_lattice lat, const int64_t dims[3], double tau, int K,
     s->stream = static_cast<cudaStream_t>(stream);
     s->t = 0;
     s->ks = ks;
+    s->model = LBM_COLLISION_FILTERED_GI;
     s->variant = 0;
     s->block = 256;
     s->V = 1;
@@ -390,11 +393,12 @@ constexpr int kGraphSteps = 32;  // even: a graph leaves the state in the buffer
 
 // Graph of kGraphSteps steps starting from buffer `from` (captured on a private stream).
 static cudaError_t step_graph(lbm_solver *s, step_fn fn, int from, cudaGraphExec_t *out) {
-    if (s->graph_cfg[0] != s->variant || s->graph_cfg[1] != s->V || s->graph_cfg[2] != s->block) {
+    const int cfg2 = s->block + (s->model == LBM_COLLISION_BGK ? 1 << 20 : 0);
+    if (s->graph_cfg[0] != s->variant || s->graph_cfg[1] != s->V || s->graph_cfg[2] != cfg2) {
         drop_step_graphs(s);
         s->graph_cfg[0] = s->variant;
         s->graph_cfg[1] = s->V;
-        s->graph_cfg[2] = s->block;
+        s->graph_cfg[2] = cfg2;
     }
     if (s->graph[from]) {
         *out = s->graph[from];
@@ -606,6 +610,27 @@ lbm_status lbm_set_kernel(lbm_solver *s, int variant, int V, int block) {
     s->variant = nv;
     s->V = nV;
     s->block = nb;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_collision(lbm_solver *s, lbm_collision model) {
+    if (lbm_status r = check_solver(s)) return r;
+    if (model != LBM_COLLISION_FILTERED_GI && model != LBM_COLLISION_BGK)
+        return fail(LBM_ERR_INVALID_ARG, "unknown collision model %d", int(model));
+    if (model == LBM_COLLISION_BGK && !s->ks->bgk) return fail(LBM_ERR_UNSUPPORTED, "BGK kernel not built");
+    s->model = model;
+    if (model == LBM_COLLISION_BGK) {
+        s->variant = 0;
+        s->V = 1;
+    } else {
+        s->V = 1;
+        for (int V : {4, 2, 1})
+            if (step_for(s, 0, V)) {
+                s->V = V;
+                break;
+            }
+        s->variant = 0;
+    }
     return LBM_OK;
 }
 

@@ -323,4 +323,23 @@ __device__ __forceinline__ void equilibrium_shifted(T rho, T drho, const T (&u)[
     }
 }
 
+// The BGK operator of Eq. BGK with the same truncated equilibrium, in scaled
+// variables: h' = h^eq + (1 - 1/tau)(h - h^eq).  A comparison baseline: it relaxes
+// every non-equilibrium moment, including those the lattice does not support.
+template <class LT, int K, typename T>
+__device__ __forceinline__ void collide_bgk(T (&g)[LT::Q], T relax, T rho0) {
+    constexpr int D = LT::D;
+    T drho, j[3], m2[3][3];
+    accumulate_moments<LT, T>(g, drho, j, m2);
+    const T rho = rho0 + drho;
+    const T irho = T(1) / rho;
+    T u[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[a] = j[a] * irho;
+    T feq[LT::Q];
+    equilibrium_shifted<LT, K, T>(rho, drho, u, feq);
+#pragma unroll
+    for (int i = 0; i < LT::Q; ++i) g[i] = feq[i] + relax * (g[i] - feq[i]);
+}
+
 }  // namespace lbm

@@ -94,6 +94,7 @@ struct KernelSet {
     reduce_fn mode;          // nvals = 2
     batch_fn batch;          // persistent multi-lattice step (V = 1)
     int (*batch_occupancy)(int block);
+    step_fn bgk;             // BGK comparison operator, register pull with V = 1
 };
 
 // Defined in the instantiation units, one per lattice.

@@ -79,7 +79,7 @@ __host__ __device__ constexpr int floordiv(int e, int V) { return e >= 0 ? e / V
 // the missing values directly.  Every lane of the warp must call this (the
 // shuffles use the full mask); lanes with active == false compute on a valid
 // clamped position and store nothing.
-template <class LT, int K, class ST, int V>
+template <class LT, int K, class ST, int V, bool BGK = false>
 __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restrict__ src,
                                                    typename ST::S *__restrict__ dst, int nx, int ny, int nz, int ncx,
                                                    long long P, int y, int z, int chunk, bool active,
@@ -153,7 +153,8 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         T g[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) g[i] = f[i][j];
-        collide<LT, K, T>(g, relax, rho0);
+        if constexpr (BGK) collide_bgk<LT, K, T>(g, relax, rho0);
+        else collide<LT, K, T>(g, relax, rho0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i][j] = g[i];
     }
@@ -169,7 +170,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
     }
 }
 
-template <class LT, int K, class ST, int V>
+template <class LT, int K, class ST, int V, bool BGK = false>
 __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *__restrict__ src,
                                                           typename ST::S *__restrict__ dst, int nx, int ny,
                                                           int ncx, long long P, typename ST::T relax,
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
     if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
     const int y = t / ncx;
     const int chunk = t - y * ncx;
-    pull_collide_store<LT, K, ST, V>(src, dst, nx, ny, gridDim.y, ncx, P, y, z, chunk, active, relax, rho0);
+    pull_collide_store<LT, K, ST, V, BGK>(src, dst, nx, ny, gridDim.y, ncx, P, y, z, chunk, active, relax, rho0);
 }
 
 // ------------------------------------------------------------------ batched step
@@ -242,7 +243,7 @@ int batch_occupancy(int block) {
     return n;
 }
 
-template <class LT, int K, class ST, int V>
+template <class LT, int K, class ST, int V, bool BGK = false>
 cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream) {
     using T = typename ST::T;
     if (a.nx % V) return cudaErrorInvalidValue;
@@ -253,7 +254,7 @@ cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream
     const long long gx = (total + block - 1) / block;
     if (gx > 0x7fffffffLL || a.nz > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)gx, (unsigned)a.nz);
-    step_direct_kernel<LT, K, ST, V><<<grid, block, 0, stream>>>(
+    step_direct_kernel<LT, K, ST, V, BGK><<<grid, block, 0, stream>>>(
         static_cast<const typename ST::S *>(a.src), static_cast<typename ST::S *>(a.dst), a.nx, a.ny, ncx, a.P,
         T(a.relax), T(a.rho0));
     return cudaGetLastError();
@@ -525,6 +526,7 @@ const KernelSet *make_kernel_set() {
         &launch_mode<LT, ST>,
         &launch_batch<LT, K, ST>,
         &batch_occupancy<LT, K, ST>,
+        &launch_step_direct<LT, K, ST, 1, true>,
     };
     return &ks;
 }

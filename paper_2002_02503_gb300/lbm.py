@@ -42,6 +42,7 @@ SIGNATURES = [
     ("lbm_time", _c.c_int, [_P, _I64P]),
     ("lbm_set_kernel", _c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int]),
     ("lbm_get_kernel", _c.c_int, [_P, _IP, _IP, _IP]),
+    ("lbm_set_collision", _c.c_int, [_P, _c.c_int]),
     ("lbm_autotune", _c.c_int, [_P, _c.c_int, _DP]),
     ("lbm_conservation_noalloc", _c.c_int, [_c.c_int, _c.c_int, _I64P, _c.c_double, _P, _P, _c.c_int, _P]),
     ("lbm_destroy", _c.c_int, [_P]),
@@ -215,6 +216,13 @@ def lbm_get_kernel(h):
     v, c, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().lbm_get_kernel(h, ctypes.byref(v), ctypes.byref(c), ctypes.byref(b)))
     return v.value, c.value, b.value
+
+
+COLLISIONS = {"filtered": 0, "bgk": 1}
+
+
+def lbm_set_collision(h, model):
+    _check(lib().lbm_set_collision(h, COLLISIONS[model] if isinstance(model, str) else int(model)))
 
 
 def lbm_autotune(h, iters=10):

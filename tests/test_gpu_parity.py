@@ -244,3 +244,51 @@ def test_full_size_d3q19_256_one_step_and_conservation():
     assert abs(c1[0] - c0[0]) < 1e-7 * c0[0]
     assert np.max(np.abs(c1[1:] - c0[1:])) < 1e-7 * c0[0]
     s.close()
+
+
+@pytest.mark.parametrize("name,K", [("D3Q19", 2), ("D3Q19", 3), ("D3Q39", 4), ("D2Q9", 3), ("D3Q15", 3)])
+def test_bgk_comparison_mode_matches_oracle(name, K):
+    dims = DIMS[name]
+    D = lbm.lbm_lattice_info(name)["D"]
+    rho, u = fields.random_smooth_fields(dims, D, salt=30 + K)
+    f0 = oracle.init_eq(name, K, dims, rho, u)
+    f_ref = oracle.run(name, K, 0.6, dims, f0, 100, model="bgk")
+    r_ref, u_ref = oracle.moments(name, dims, f_ref)
+    s = lbm.Solver(name, dims, 0.6, K, "f32")
+    lbm.lbm_set_collision(s.handle, "bgk")
+    s.set_fields(rho, u)
+    s.step(100)
+    r, uu = s.moments()
+    f = s.f()
+    s.close()
+    assert rel_f(r, r_ref) < TOL_F32
+    assert rel_u(uu, u_ref) < TOL_F32
+    assert rel_f(f, to_lib_order(name, f_ref)) < TOL_F32
+
+
+def test_gpu_bgk_diverges_where_filtered_is_stable():
+    """The oracle's stability pin on the GPU: Taylor-Green u0 = 0.15 on 24^3 at tau = 0.5005 --
+    within 500 steps the BGK step goes non-finite while the filtered GI step (K = 2, 3) stays
+    finite and conserves mass."""
+    dims = (24, 24, 24)
+    rho, u = fields.taylor_green_3d(dims, 0.15, 1.0 / 3.0)
+    for K in (2, 3):
+        results = {}
+        for model in ("bgk", "filtered"):
+            s = lbm.Solver("D3Q19", dims, 0.5005, K, "f32")
+            lbm.lbm_set_collision(s.handle, model)
+            s.set_fields(rho, u)
+            c0 = s.conservation()
+            s.step(500)
+            try:
+                c1 = s.conservation()
+                results[model] = abs(c1[0] - c0[0]) / c0[0]
+                r, uu = s.moments()
+                if np.abs(uu).max() > 1.0:
+                    results[model] = None
+            except lbm.LbmError as e:
+                assert e.status == lbm.LBM_ERR_NONFINITE
+                results[model] = None
+            s.close()
+        assert results["bgk"] is None, (K, results)
+        assert results["filtered"] is not None and results["filtered"] < 1e-6, (K, results)

@@ -177,3 +177,21 @@ def test_tau_one_gives_equilibrium_and_filter_is_idempotent(name):
         f1 = oracle.collide(name, K, 1e300, f)["fpost"]  # = f^eq + fhat (1 - 1/tau == 1)
         f2 = oracle.collide(name, K, 1e300, f1)["fpost"]
         np.testing.assert_allclose(f2, f1, atol=1e-16)
+
+
+@pytest.mark.parametrize("name", ALL)
+def test_bgk_comparison_operator(name):
+    """Eq. BGK with the same truncated f^eq: conserves mass and momentum; on a state whose
+    non-equilibrium part is already filtered it coincides with the filtered collision; on a
+    general state the filter removes content BGK keeps (Sec. 1: unsupported higher moments)."""
+    lat, D, _, _, c = _setup(name)
+    for K in range(2, KMAX[name] + 1):
+        f = _random_f(lat, 40 + K)
+        fb = oracle.collide_bgk(name, K, 0.7, f)
+        assert abs(fb.sum() - f.sum()) < 1e-14
+        np.testing.assert_allclose(c.T @ fb, c.T @ f, atol=1e-15)
+        np.testing.assert_allclose(fb, f - (f - oracle.feq(name, K, f.sum(), (c.T @ f) / f.sum())) / 0.7, atol=1e-15)
+        f1 = oracle.collide(name, K, 1e300, f)["fpost"]  # f^eq + fhat: a filtered state
+        np.testing.assert_allclose(oracle.collide_bgk(name, K, 0.7, f1), oracle.collide(name, K, 0.7, f1)["fpost"],
+                                   atol=1e-15)
+        assert np.abs(fb - oracle.collide(name, K, 0.7, f)["fpost"]).max() > 1e-6
