@@ -39,8 +39,11 @@ def _load():
         lib.orc_init_eq.argtypes = [ctypes.c_int, ctypes.c_int, i64p, dp, dp, dp, ctypes.c_int]
         lib.orc_moments.argtypes = [ctypes.c_int, i64p, dp, dp, dp]
         lib.orc_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, i64p, dp, ctypes.c_int64, ctypes.c_int]
-        lib.orc_run_model.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, i64p, dp,
-                                      ctypes.c_int64, ctypes.c_int]
+        lib.orc_run_model.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                      i64p, dp, ctypes.c_int64, ctypes.c_int]
+        lib.orc_fneq_hat_q.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        lib.orc_collide_theta.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                          dp]
         lib.orc_collide_bgk.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
         _lib = lib
     return _lib
@@ -180,16 +183,40 @@ def collide_bgk(name, K, tau, f):
     return out
 
 
-def run(name, K, tau, dims, f, nsteps, nthreads=None, model="filtered"):
-    """Advance f [Q, C] by nsteps of collide + push (Eq. lbe-reg, or Eq. BGK with model="bgk", and
-    Eq. lbe); returns a new array."""
+def fneq_hat_q(name, K, u, Qt):
+    """Truncated energy-flux filtered part fhat^{neq,q} (Eq. pq series) at one cell."""
+    Q = lattice(name)["Q"]
+    out = np.zeros(Q)
+    uu = _u3(u)
+    T = np.zeros((3, 3, 3))
+    Qt = np.asarray(Qt, dtype=np.float64)
+    d = Qt.shape[0]
+    T[:d, :d, :d] = Qt
+    _check(_load().orc_fneq_hat_q(_lat(name), int(K), _dp(uu), _dp(T), _dp(out)), "fneq_hat_q")
+    return out
+
+
+def collide_theta(name, K, tau, theta, f):
+    """One cell of the filtered collision with the energy-flux term: dict(fpost, Qt, fhatq)."""
+    Q = lattice(name)["Q"]
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    fpost, fhq = np.zeros(Q), np.zeros(Q)
+    Qt = np.zeros(27)
+    _check(_load().orc_collide_theta(_lat(name), int(K), float(tau), float(theta), _dp(f), _dp(fpost), _dp(Qt),
+                                     _dp(fhq)), "collide_theta")
+    return {"fpost": fpost, "Qt": Qt.reshape(3, 3, 3), "fhatq": fhq}
+
+
+def run(name, K, tau, dims, f, nsteps, nthreads=None, model="filtered", theta=0.0):
+    """Advance f [Q, C] by nsteps of collide + push (Eq. lbe-reg, optionally with the energy-flux
+    term theta of Eq. pq, or Eq. BGK with model="bgk"; then Eq. lbe); returns a new array."""
     lat = lattice(name)
     d = _dims(dims)
     C = int(np.prod(d))
     out = np.array(f, dtype=np.float64, copy=True).reshape(lat["Q"], C)
     out = np.ascontiguousarray(out)
     nt = default_threads() if nthreads is None else int(nthreads)
-    rc = _load().orc_run_model(_lat(name), int(K), float(tau), MODELS[model],
+    rc = _load().orc_run_model(_lat(name), int(K), float(tau), MODELS[model], float(theta),
                                d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out), int(nsteps), nt)
     _check(rc, "run")
     return out

@@ -23,6 +23,13 @@
  * The tensor Hermite polynomials H^(n)(xi) are built generically by the
  * recursion of Eq. recurG (Appendix), H^(0)=1, H^(1)_a = xi_a.
  *
+ * Energy-flux extension (Sec. 4, Eq. pq): fhat^neq = fhat^{neq,p} + theta fhat^{neq,q} with
+ *   Qt^neq = sum_i c'_i c'_i c'_i f^neq_i                                (Eq. Q_def)
+ *   fhat^{neq,q}_i = w_i/(6 T0^{3/2}) sum_{n=3}^{K} H^(n)(xi_i) : V^[n-3] Qt^neq / (n-3)!
+ * the Hermite series of the compact Eq. filter-Q (read with the 1/rho of Eq. filter-coll),
+ * obtained from the generating function of the H^(n) exactly as the Appendix obtains
+ * Eq. hermite-coll, one derivative higher; truncated at the same order K.
+ *
  * Lattice tables: the paper fixes T0 = 1/3 for D3Q15/D3Q19 (Sec. 2, after
  * Eq. iso) and the isotropy classes 2N (D2Q9, D3Q15, D3Q19: 4; D3Q39: 6), but prints
  * no weights.  The standard velocity sets below are used; the test suite checks
@@ -220,7 +227,7 @@ static double factorial(int n) {
 /* Work space for the products V^[n] and V^[n-2] Pi, one per thread. */
 typedef struct {
     double *Vp[ORC_MAX_K + 1]; /* V^[n], D^n entries */
-    double *VPi[ORC_MAX_K + 1]; /* V^[n-2] (x) Pi, D^n entries (n >= 2) */
+    double *VPi[ORC_MAX_K + 1]; /* V^[n-2] (x) Pi, D^n entries (n >= 2); reused for V^[n-3] (x) Qt */
     int D, K;
 } orc_work_t;
 
@@ -300,6 +307,36 @@ static void fneq_hat_cell(const orc_ctx_t *ctx, orc_work_t *wk, const double *u,
     }
 }
 
+/* fhat^{neq,q}_i = w_i/(6 T0^{3/2}) sum_{n=3}^{K} H^(n)(xi_i) : V^[n-3] Qt / (n-3)!
+ * Qt is a full D x D x D tensor stored in a 3x3x3 array. */
+static void fneq_hat_q_cell(const orc_ctx_t *ctx, orc_work_t *wk, const double *u, const double Qt[3][3][3],
+                            double *out) {
+    const orc_lattice_t *L = &ctx->L;
+    int D = L->D;
+    double s = 1.0 / sqrt(L->T0);
+    double V[3] = {u[0] * s, u[1] * s, u[2] * s};
+    fill_Vpowers(wk, V);
+    for (int n = 3; n <= ctx->K; ++n) {
+        long size = ipow(D, n);
+        for (long idx = 0; idx < size; ++idx) {
+            int c3 = (int)(idx % D);
+            int c2 = (int)((idx / D) % D);
+            int c1 = (int)((idx / (D * D)) % D);
+            wk->VPi[n][idx] = wk->Vp[n - 3][idx / (D * D * D)] * Qt[c1][c2][c3];
+        }
+    }
+    for (int i = 0; i < L->Q; ++i) {
+        double sum = 0.0;
+        for (int n = 3; n <= ctx->K; ++n) {
+            long size = ipow(D, n);
+            double dot = 0.0;
+            for (long k = 0; k < size; ++k) dot += ctx->herm[i].H[n][k] * wk->VPi[n][k];
+            sum += dot / factorial(n - 3);
+        }
+        out[i] = L->w[i] / (6.0 * L->T0 * sqrt(L->T0)) * sum;
+    }
+}
+
 /* Eq. mme */
 static void moments_cell(const orc_lattice_t *L, const double *f, double *rho, double *u) {
     double r = 0.0, j[3] = {0, 0, 0};
@@ -318,18 +355,19 @@ enum { ORC_FILTERED = 0, ORC_BGK = 1 };
 
 /* One cell through steps 1-6 of the header.  Intermediates are returned when
  * the pointers are non-NULL. */
-static void collide_cell_model(const orc_ctx_t *ctx, orc_work_t *wk, double tau, int model, const double *f,
-                               double *fpost, double *rho_out, double *u_out, double *feq_out, double *Pi_out,
-                               double *fhat_out);
+static void collide_cell_model(const orc_ctx_t *ctx, orc_work_t *wk, double tau, int model, double theta,
+                               const double *f, double *fpost, double *rho_out, double *u_out, double *feq_out,
+                               double *Pi_out, double *fhat_out, double *Qt_out, double *fhatq_out);
 
 static void collide_cell(const orc_ctx_t *ctx, orc_work_t *wk, double tau, const double *f, double *fpost,
                          double *rho_out, double *u_out, double *feq_out, double *Pi_out, double *fhat_out) {
-    collide_cell_model(ctx, wk, tau, ORC_FILTERED, f, fpost, rho_out, u_out, feq_out, Pi_out, fhat_out);
+    collide_cell_model(ctx, wk, tau, ORC_FILTERED, 0.0, f, fpost, rho_out, u_out, feq_out, Pi_out, fhat_out, NULL,
+                       NULL);
 }
 
-static void collide_cell_model(const orc_ctx_t *ctx, orc_work_t *wk, double tau, int model, const double *f,
-                               double *fpost, double *rho_out, double *u_out, double *feq_out, double *Pi_out,
-                               double *fhat_out) {
+static void collide_cell_model(const orc_ctx_t *ctx, orc_work_t *wk, double tau, int model, double theta,
+                               const double *f, double *fpost, double *rho_out, double *u_out, double *feq_out,
+                               double *Pi_out, double *fhat_out, double *Qt_out, double *fhatq_out) {
     const orc_lattice_t *L = &ctx->L;
     double rho, u[3], feq[ORC_MAXQ], fneq[ORC_MAXQ], fhat[ORC_MAXQ];
     moments_cell(L, f, &rho, u);
@@ -343,11 +381,28 @@ static void collide_cell_model(const orc_ctx_t *ctx, orc_work_t *wk, double tau,
             for (int b = 0; b < L->D; ++b) Pi[a][b] += cr[a] * cr[b] * fneq[i];
     }
     fneq_hat_cell(ctx, wk, u, (const double(*)[3])Pi, fhat);
+    double fhq[ORC_MAXQ] = {0};
+    double Qt[3][3][3] = {{{0}}};
+    if (theta != 0.0 || Qt_out || fhatq_out) {
+        for (int i = 0; i < L->Q; ++i) { /* Eq. Q_def: relative velocity c' = c - u */
+            double cr[3];
+            for (int a = 0; a < 3; ++a) cr[a] = L->c[i][a] - u[a];
+            for (int a = 0; a < L->D; ++a)
+                for (int b = 0; b < L->D; ++b)
+                    for (int c = 0; c < L->D; ++c) Qt[a][b][c] += cr[a] * cr[b] * cr[c] * fneq[i];
+        }
+        fneq_hat_q_cell(ctx, wk, u, (const double(*)[3][3])Qt, fhq);
+    }
     double relax = 1.0 - 1.0 / tau;
     if (model == ORC_BGK) /* Eq. BGK: f' = f - (f - f^eq)/tau */
         for (int i = 0; i < L->Q; ++i) fpost[i] = f[i] - (f[i] - feq[i]) / tau;
-    else
-        for (int i = 0; i < L->Q; ++i) fpost[i] = feq[i] + relax * fhat[i];
+    else /* Eq. lbe-reg with Eq. pq: fhat = fhat^p + theta fhat^q */
+        for (int i = 0; i < L->Q; ++i) fpost[i] = feq[i] + relax * (fhat[i] + theta * fhq[i]);
+    if (Qt_out)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                for (int c = 0; c < 3; ++c) Qt_out[9 * a + 3 * b + c] = Qt[a][b][c];
+    if (fhatq_out) memcpy(fhatq_out, fhq, sizeof(double) * L->Q);
     if (rho_out) *rho_out = rho;
     if (u_out)
         for (int a = 0; a < 3; ++a) u_out[a] = u[a];
@@ -371,6 +426,7 @@ typedef struct {
     const orc_ctx_t *ctx;
     double tau;
     int model;
+    double theta;
     long nx, ny, nz;
     const double *f;
     double *fnew;
@@ -394,7 +450,8 @@ static void *step_worker(void *arg) {
         for (long x = 0; x < job->nx; ++x) {
                 long cell = x + job->nx * (y + job->ny * z);
                 for (int i = 0; i < L->Q; ++i) fc[i] = job->f[i * C + cell];
-                collide_cell_model(job->ctx, &wk, job->tau, job->model, fc, fp, NULL, NULL, NULL, NULL, NULL);
+                collide_cell_model(job->ctx, &wk, job->tau, job->model, job->theta, fc, fp, NULL, NULL, NULL, NULL,
+                                   NULL, NULL, NULL);
                 for (int i = 0; i < L->Q; ++i) { /* Eq. lbe: push to x + c_i */
                     long xd = wrap(x + L->c[i][0], job->nx);
                     long yd = wrap(y + L->c[i][1], job->ny);
@@ -407,8 +464,8 @@ static void *step_worker(void *arg) {
     return NULL;
 }
 
-static int run_parallel(const orc_ctx_t *ctx, double tau, int model, const int64_t *dims, const double *f,
-                        double *fnew, int nthreads) {
+static int run_parallel(const orc_ctx_t *ctx, double tau, int model, double theta, const int64_t *dims,
+                        const double *f, double *fnew, int nthreads) {
     long rows = dims[1] * dims[2];
     if (nthreads < 1) nthreads = 1;
     if (nthreads > rows) nthreads = (int)rows;
@@ -419,6 +476,7 @@ static int run_parallel(const orc_ctx_t *ctx, double tau, int model, const int64
         jobs[t].ctx = ctx;
         jobs[t].tau = tau;
         jobs[t].model = model;
+        jobs[t].theta = theta;
         jobs[t].nx = dims[0];
         jobs[t].ny = dims[1];
         jobs[t].nz = dims[2];
@@ -600,8 +658,8 @@ int orc_moments(int lat, const int64_t *dims, const double *f, double *rho, doub
 
 /* nsteps of collide + push with the given collision model (ORC_FILTERED or ORC_BGK).
  * f holds f(t) on entry and f(t + nsteps) on exit. */
-int orc_run_model(int lat, int K, double tau, int model, const int64_t *dims, double *f, int64_t nsteps,
-                  int nthreads) {
+int orc_run_model(int lat, int K, double tau, int model, double theta, const int64_t *dims, double *f,
+                  int64_t nsteps, int nthreads) {
     orc_ctx_t ctx;
     int rc = ctx_init(lat, K, &ctx);
     if (rc) return rc;
@@ -617,7 +675,7 @@ int orc_run_model(int lat, int K, double tau, int model, const int64_t *dims, do
     }
     double *a = f, *b = tmp;
     for (int64_t s = 0; s < nsteps && rc == 0; ++s) {
-        rc = run_parallel(&ctx, tau, model, dims, a, b, nthreads);
+        rc = run_parallel(&ctx, tau, model, theta, dims, a, b, nthreads);
         double *t = a;
         a = b;
         b = t;
@@ -630,7 +688,7 @@ int orc_run_model(int lat, int K, double tau, int model, const int64_t *dims, do
 
 /* nsteps of the paper's filtered collision + push. */
 int orc_run(int lat, int K, double tau, const int64_t *dims, double *f, int64_t nsteps, int nthreads) {
-    return orc_run_model(lat, K, tau, ORC_FILTERED, dims, f, nsteps, nthreads);
+    return orc_run_model(lat, K, tau, ORC_FILTERED, 0.0, dims, f, nsteps, nthreads);
 }
 
 /* One cell with the BGK operator (Eq. BGK) and the truncated f^eq. */
@@ -640,7 +698,38 @@ int orc_collide_bgk(int lat, int K, double tau, const double *f, double *fpost) 
     if (rc) return rc;
     orc_work_t wk;
     if (work_init(ctx.L.D, K, &wk)) rc = -3;
-    else collide_cell_model(&ctx, &wk, tau, ORC_BGK, f, fpost, NULL, NULL, NULL, NULL, NULL);
+    else collide_cell_model(&ctx, &wk, tau, ORC_BGK, 0.0, f, fpost, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+    work_free(&wk);
+    ctx_free(&ctx);
+    return rc;
+}
+
+/* fhat^{neq,q} at one cell for a given Qt (Eq. pq series, truncated at K). */
+int orc_fneq_hat_q(int lat, int K, const double *u, const double *Qt /* [27] */, double *out) {
+    orc_ctx_t ctx;
+    int rc = ctx_init(lat, K, &ctx);
+    if (rc) return rc;
+    orc_work_t wk;
+    double T[3][3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c) T[a][b][c] = Qt[9 * a + 3 * b + c];
+    if (work_init(ctx.L.D, K, &wk)) rc = -3;
+    else fneq_hat_q_cell(&ctx, &wk, u, (const double(*)[3][3])T, out);
+    work_free(&wk);
+    ctx_free(&ctx);
+    return rc;
+}
+
+/* One cell of the filtered collision with the energy-flux term (Eq. pq); returns Qt and fhat^q too. */
+int orc_collide_theta(int lat, int K, double tau, double theta, const double *f, double *fpost, double *Qt,
+                      double *fhatq) {
+    orc_ctx_t ctx;
+    int rc = ctx_init(lat, K, &ctx);
+    if (rc) return rc;
+    orc_work_t wk;
+    if (work_init(ctx.L.D, K, &wk)) rc = -3;
+    else collide_cell_model(&ctx, &wk, tau, ORC_FILTERED, theta, f, fpost, NULL, NULL, NULL, NULL, NULL, Qt, fhatq);
     work_free(&wk);
     ctx_free(&ctx);
     return rc;

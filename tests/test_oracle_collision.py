@@ -195,3 +195,100 @@ def test_bgk_comparison_operator(name):
         np.testing.assert_allclose(oracle.collide_bgk(name, K, 0.7, f1), oracle.collide(name, K, 0.7, f1)["fpost"],
                                    atol=1e-15)
         assert np.abs(fb - oracle.collide(name, K, 0.7, f)["fpost"]).max() > 1e-6
+
+
+# ---------------------------------------------------------------- energy-flux term (Eq. pq)
+def _sym3(g):
+    Q = g.standard_normal((3, 3, 3)) * 1e-3
+    return (Q + Q.transpose(0, 2, 1) + Q.transpose(1, 0, 2) + Q.transpose(1, 2, 0) + Q.transpose(2, 0, 1)
+            + Q.transpose(2, 1, 0)) / 6
+
+
+def compact_fneq_q(lat, rho, u, Qt):
+    """Eq. filter-Q with the 1/rho of Eq. filter-coll: f^eq/(6 rho T0^3) [c'c'c' - 3 c' T0 I] (.) Qt."""
+    T0 = lat["T0"]
+    c = lat["c"].astype(np.float64) - u
+    feq = compact_feq(lat, rho, u)
+    A = np.einsum("ia,ib,ic,abc->i", c, c, c, Qt) - 3 * T0 * np.einsum("ia,abb->i", c, Qt)
+    return feq / (6 * rho * T0 ** 3) * A
+
+
+def printed_filter2_theta_term(lat, Q):
+    """The theta term of Eq. filter2 as printed: w/(6 T0^2) [ccc/T0 - 3 c I] (.) Q."""
+    T0 = lat["T0"]
+    c = lat["c"].astype(np.float64)
+    A = np.einsum("ia,ib,ic,abc->i", c, c, c, Q) / T0 - 3 * np.einsum("ia,abb->i", c, Q)
+    return lat["w"] / (6 * T0 ** 2) * A
+
+
+@pytest.mark.parametrize("name", ["D3Q15", "D3Q19", "D3Q27", "D3Q39"])
+def test_energy_flux_series_limits(name):
+    lat = oracle.lattice(name)
+    g = np.random.default_rng(9)
+    Qt = _sym3(g)
+    # u = 0, K = 3: the prior form's theta term (Eq. filter2)
+    np.testing.assert_allclose(oracle.fneq_hat_q(name, 3, np.zeros(3), Qt), printed_filter2_theta_term(lat, Qt),
+                               atol=1e-18)
+    # compact-form limit (Eq. filter-Q) with error order |u|^(K-2)
+    u = np.array([0.6, -0.3, 0.2])
+    u *= 0.1 / np.linalg.norm(u)
+    for K in range(3, 8):
+        e = [np.abs(oracle.fneq_hat_q(name, K, s * u, Qt) - compact_fneq_q(lat, 1.3, s * u, Qt)).max()
+             for s in (1.0, 0.5)]
+        assert abs(math.log2(e[0] / e[1]) - (K - 2)) < 0.3, (K, e)
+    want = compact_fneq_q(lat, 1.3, u, Qt)
+    assert np.abs(oracle.fneq_hat_q(name, 10, u, Qt) - want).max() < 1e-8 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("name,Ks", [("D3Q15", [3]), ("D3Q19", [3]), ("D3Q27", [3]), ("D3Q39", [3, 4, 5])])
+def test_energy_flux_term_adds_no_mass_momentum_or_stress(name, Ks):
+    lat = oracle.lattice(name)
+    c = lat["c"].astype(np.float64)
+    g = np.random.default_rng(10)
+    Qt = _sym3(g)
+    u = np.array([0.05, -0.03, 0.02])
+    for K in Ks:
+        fq = oracle.fneq_hat_q(name, K, u, Qt)
+        assert abs(fq.sum()) < 1e-18
+        np.testing.assert_allclose(c.T @ fq, 0, atol=1e-18)
+        np.testing.assert_allclose(np.einsum("ia,ib,i->ab", c, c, fq), 0, atol=1e-18)
+
+
+def test_energy_flux_reproduced_where_the_lattice_supports_it():
+    """On D3Q39 (2N = 6) the truncated series reproduces Qt for K <= 4 (orthogonality of H^(n) to
+    cubic polynomials needs E^(n+3)); on class-4 lattices the third moment is not supported
+    (c_a^3 = c_a there) and is not reproduced."""
+    g = np.random.default_rng(11)
+    Qt = _sym3(g)
+    u = np.array([0.05, -0.03, 0.02])
+    lat = oracle.lattice("D3Q39")
+    cr = lat["c"].astype(np.float64) - u
+    for K in (3, 4):
+        fq = oracle.fneq_hat_q("D3Q39", K, u, Qt)
+        np.testing.assert_allclose(np.einsum("ia,ib,ic,i->abc", cr, cr, cr, fq), Qt, atol=1e-17)
+    lat = oracle.lattice("D3Q19")
+    cr = lat["c"].astype(np.float64) - u
+    fq = oracle.fneq_hat_q("D3Q19", 3, u, Qt)
+    assert np.abs(np.einsum("ia,ib,ic,i->abc", cr, cr, cr, fq) - Qt).max() > 1e-5
+
+
+@pytest.mark.parametrize("name", ["D3Q19", "D3Q39"])
+def test_relative_energy_flux_and_theta_collision(name):
+    """Qt of Eq. Q_def equals sum ccc f^neq - 3 sym(u Pi) (the Discussion's linear combination of the
+    absolute flux and Pi u); the collision with the theta term still conserves mass and momentum."""
+    lat = oracle.lattice(name)
+    c = lat["c"].astype(np.float64)
+    K = KMAX[name] if name != "D3Q39" else 4
+    f = _random_f(lat, 50)
+    r = oracle.collide(name, K, 0.7, f)
+    rt = oracle.collide_theta(name, K, 0.7, 0.6, f)
+    u, Pi = r["u"], r["Pi"]
+    fneq = f - r["feq"]
+    M3 = np.einsum("ia,ib,ic,i->abc", c, c, c, fneq)
+    sym = np.einsum("a,bc->abc", u, Pi) + np.einsum("b,ac->abc", u, Pi) + np.einsum("c,ab->abc", u, Pi)
+    np.testing.assert_allclose(rt["Qt"], M3 - sym, atol=1e-16)
+    fp = rt["fpost"]
+    assert abs(fp.sum() - f.sum()) < 1e-14
+    np.testing.assert_allclose(c.T @ fp, c.T @ f, atol=1e-15)
+    np.testing.assert_allclose(fp, r["fpost"] + (1 - 1 / 0.7) * 0.6 * rt["fhatq"], atol=1e-16)
+    np.testing.assert_allclose(rt["fhatq"], oracle.fneq_hat_q(name, K, u, rt["Qt"]), atol=1e-18)
