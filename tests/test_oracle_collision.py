@@ -237,7 +237,7 @@ def test_energy_flux_series_limits(name):
              for s in (1.0, 0.5)]
         assert abs(math.log2(e[0] / e[1]) - (K - 2)) < 0.3, (K, e)
     want = compact_fneq_q(lat, 1.3, u, Qt)
-    assert np.abs(oracle.fneq_hat_q(name, 10, u, Qt) - want).max() < 1e-8 * np.abs(want).max()
+    assert np.abs(oracle.fneq_hat_q(name, 10, u, Qt) - want).max() < 1e-7 * np.abs(want).max()  # ~V^8/8!
 
 
 @pytest.mark.parametrize("name,Ks", [("D3Q15", [3]), ("D3Q19", [3]), ("D3Q27", [3]), ("D3Q39", [3, 4, 5])])
