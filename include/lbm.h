@@ -143,6 +143,13 @@ lbm_status lbm_get_kernel(const lbm_solver *s, int *variant, int *cells_per_thre
 typedef enum { LBM_COLLISION_FILTERED_GI = 0, LBM_COLLISION_BGK = 1 } lbm_collision;
 lbm_status lbm_set_collision(lbm_solver *s, lbm_collision model);
 
+/* Energy-flux term (Sec. 4, Eq. pq): fhat^neq = fhat^{neq,p} + theta fhat^{neq,q}, with
+ * fhat^{neq,q} the Hermite series of Eq. filter-Q (the relative-frame flux Qt of
+ * Eq. Q_def) truncated at the solver's K, so theta needs K >= 3.  theta = 0 (the
+ * default) is the paper's Sec. 3 collision.  Applies to the filtered collision;
+ * runs one cell per thread.  LBM_ERR_UNSUPPORTED for K = 2. */
+lbm_status lbm_set_energy_flux(lbm_solver *s, double theta);
+
 /* Autotuner: times every built kernel configuration for this solver on its own
  * buffers (reads the current state, writes only the idle buffer, so the state is
  * unchanged) over `iters` launches each and keeps the fastest.  best_us, if not

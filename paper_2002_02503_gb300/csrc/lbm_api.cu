@@ -160,6 +160,8 @@ struct lbm_solver {
     const KernelSet *ks;
     int variant, V, block;
     lbm_collision model;
+    double theta;  // energy-flux weight (Eq. pq); 0 = the paper's Sec. 3 collision
+    double graph_theta;
     // Captured graphs of kGraphSteps consecutive steps, one per starting buffer; rebuilt
     // when the kernel configuration changes.  They cut the per-step launch cost, which
     // dominates on small lattices.
@@ -182,11 +184,13 @@ StepArgs step_args(const lbm_solver *s, int from) {
     a.rho0 = s->rho0;
     a.status = s->status;
     a.grid_limit = 0;
+    a.theta = s->theta;
     return a;
 }
 
 step_fn step_for(const lbm_solver *s, int variant, int V) {
     if (s->model == LBM_COLLISION_BGK) return (variant == 0 && V == 1) ? s->ks->bgk : nullptr;
+    if (s->theta != 0.0) return (variant == 0 && V == 1) ? s->ks->theta : nullptr;
     if (variant == 0) {
         int k = v_index(V);
         if (k < 0 || s->nx % V) return nullptr;
@@ -393,7 +397,11 @@ constexpr int kGraphSteps = 32;  // even: a graph leaves the state in the buffer
 
 // Graph of kGraphSteps steps starting from buffer `from` (captured on a private stream).
 static cudaError_t step_graph(lbm_solver *s, step_fn fn, int from, cudaGraphExec_t *out) {
-    const int cfg2 = s->block + (s->model == LBM_COLLISION_BGK ? 1 << 20 : 0);
+    const int cfg2 = s->block + (s->model == LBM_COLLISION_BGK ? 1 << 20 : 0) + (s->theta != 0.0 ? 1 << 21 : 0);
+    if (s->theta != s->graph_theta) {  // theta is baked into the captured launches
+        drop_step_graphs(s);
+        s->graph_theta = s->theta;
+    }
     if (s->graph_cfg[0] != s->variant || s->graph_cfg[1] != s->V || s->graph_cfg[2] != cfg2) {
         drop_step_graphs(s);
         s->graph_cfg[0] = s->variant;
@@ -630,6 +638,27 @@ lbm_status lbm_set_collision(lbm_solver *s, lbm_collision model) {
                 break;
             }
         s->variant = 0;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_energy_flux(lbm_solver *s, double theta) {
+    if (lbm_status r = check_solver(s)) return r;
+    if (!isfinite(theta)) return fail(LBM_ERR_INVALID_ARG, "theta must be finite");
+    if (theta != 0.0 && s->K < 3)
+        return fail(LBM_ERR_UNSUPPORTED, "the energy-flux series starts at Hermite order 3: needs K >= 3");
+    if (theta != 0.0 && !s->ks->theta) return fail(LBM_ERR_UNSUPPORTED, "energy-flux kernel not built");
+    s->theta = theta;
+    s->variant = 0;
+    if (theta != 0.0) {
+        s->V = 1;
+    } else {
+        s->V = 1;
+        for (int V : {4, 2, 1})
+            if (step_for(s, 0, V)) {
+                s->V = V;
+                break;
+            }
     }
     return LBM_OK;
 }

@@ -195,9 +195,16 @@ struct ScalarHermite {
 //   (f^eq - w rho0)/w = drho + rho (E_K - 1)
 //   fhat / w          = 1/(2 T0) [E_{K-2} A - 2 E_{K-3} B + E_{K-4} R]
 // with the even/odd parts of E_n written out for K = 2..5 (E_n = 0 for n < 0).
-template <class LT, int K, typename T>
-__device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
+// Energy-flux part (Eq. pq, theta != 0): the series of Eq. filter-Q truncated at the same
+// K reduces, with Qt the relative-frame flux of Eq. Q_def and q_a = Qt_abb, to
+//   fhat^q / w = 1/(6 T0^3) sum_{m=0}^{K-3} sum_k a_k h_{m-k}/(m-k)!
+//   a_0 = Qt(c,c,c) - 3 T0 c.q,  a_1 = -3 (c.(Qt u).c - T0 u.q),  a_2 = 3 c.(Qt u u),
+// a_0, a_2 odd and a_1 even under c -> -c.  Qt = sum w c c c (h - h^eq) - 3 sym(u Pi).
+// kq = (1 - 1/tau) theta / (6 T0^3).
+template <class LT, int K, typename T, bool THETA = false>
+__device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0, T kq = T(0)) {
     static_assert(K >= 2 && K <= 5, "truncation order");
+    static_assert(!THETA || K >= 3, "the energy-flux series starts at Hermite order 3");
     constexpr int D = LT::D;
     const T iT0 = T(1.0 / LT::T0);
     const T T0 = T(LT::T0);
@@ -242,6 +249,67 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
     }
     const T kappa = relax * T(1.0 / (2.0 * LT::T0));  // (1 - 1/tau) / (2 T0)
 
+    // energy flux: Qt (symmetric, stored for a <= b <= c), q, Qt u, Qt u u
+    T Qt[3][3][3], q[3], Qu[3][3], Quu[3];
+    T uq = T(0);
+    if constexpr (THETA) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Qt[a][b][c] = neg_zero<T>();
+#pragma unroll
+        for (int p = 0; p < LT::NP; ++p) {
+            T s = neg_zero<T>();
+#pragma unroll
+            for (int a = 0; a < D; ++a) accumulate_scaled(s, LT::c(p, a), us[a]);
+            const ScalarHermite<K, T> H(s, v2);
+            const T d = (g[2 * p + 1] - g[2 * p + 2]) - T(2) * rho * H.feq_odd(s);  // odd part of h - h^eq
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = a; b < D; ++b)
+#pragma unroll
+                    for (int c = b; c < D; ++c) {
+                        const int cabc = LT::c(p, a) * LT::c(p, b) * LT::c(p, c);
+                        if (cabc != 0) Qt[a][b][c] += T(cabc * LT::w(p)) * d;
+                    }
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b)
+#pragma unroll
+                for (int c = b; c < D; ++c) {
+                    const T v = Qt[a][b][c] - (u[a] * P[b][c] + u[b] * P[a][c] + u[c] * P[a][b]);
+                    Qt[a][b][c] = v;  // fill every permutation of (a, b, c)
+                    Qt[a][c][b] = v;
+                    Qt[b][a][c] = v;
+                    Qt[b][c][a] = v;
+                    Qt[c][a][b] = v;
+                    Qt[c][b][a] = v;
+                }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            q[a] = neg_zero<T>();
+            Quu[a] = neg_zero<T>();
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+                q[a] += Qt[a][b][b];
+                Qu[a][b] = neg_zero<T>();
+#pragma unroll
+                for (int c = 0; c < D; ++c) Qu[a][b] += Qt[a][b][c] * u[c];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+#pragma unroll
+            for (int b = 0; b < D; ++b) Quu[a] += Qu[a][b] * u[b];
+            uq += u[a] * q[a];
+        }
+    }
+
     // rest velocity: s = 0, A = -tr Pi, B = 0; h2 = -v2, h4 = 3 v2^2
     {
         T feq = drho;
@@ -253,6 +321,8 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
             feq -= rho * v2 * T(0.5);
         }
         g[0] = feq + kappa * fh;
+        // energy flux at c = 0: a_0 = a_2 = 0, a_1 = 3 T0 u.q enters from K = 4 on
+        if constexpr (THETA && K >= 4) g[0] += kq * T(3.0 * LT::T0) * uq;
     }
 #pragma unroll
     for (int p = 0; p < LT::NP; ++p) {
@@ -285,9 +355,37 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0) {
             fh_e = A * e2 - T(2) * B * s + R;
             fh_o = A * (s + H.h3 * T(1.0 / 6.0)) - T(2) * B * e2 + R * s;
         }
-        const T e = feq_e + kappa * fh_e;
+        T e = feq_e + kappa * fh_e;
         T o = feq_o;
         if constexpr (K >= 3) o += kappa * fh_o;
+        if constexpr (THETA) {
+            T Qccc = neg_zero<T>(), cq = neg_zero<T>(), cQuc = neg_zero<T>(), cQuu = neg_zero<T>();
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int ca = LT::c(p, a);
+                if (ca == 0) continue;
+                accumulate_scaled(cq, ca, q[a]);
+                accumulate_scaled(cQuu, ca, Quu[a]);
+#pragma unroll
+                for (int b = 0; b < D; ++b) {
+                    const int cb = LT::c(p, b);
+                    if (cb == 0) continue;
+                    accumulate_scaled(cQuc, ca * cb, Qu[a][b]);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        const int cc = LT::c(p, c);
+                        if (cc != 0) accumulate_scaled(Qccc, ca * cb * cc, Qt[a][b][c]);
+                    }
+                }
+            }
+            const T a0 = Qccc - T(3.0 * LT::T0) * cq;
+            const T a1 = T(-3) * (cQuc - T(LT::T0) * uq);
+            T q_odd = a0, q_even = T(0);
+            if constexpr (K >= 4) q_even = a0 * s + a1;
+            if constexpr (K >= 5) q_odd = a0 * (T(1) + H.h2 * T(0.5)) + a1 * s + T(3) * cQuu;
+            if constexpr (K >= 4) e += kq * q_even;
+            o += kq * q_odd;
+        }
         g[2 * p + 1] = e + o;
         g[2 * p + 2] = e - o;
     }

@@ -25,6 +25,7 @@ struct StepArgs {
     double rho0;
     unsigned int *status;  // device status word (persistent variant), may be null
     int grid_limit;        // persistent variant: CTAs to launch (0 = one per SM slot)
+    double theta;          // weight of the energy-flux part (Eq. pq); 0 = off
 };
 
 struct InitArgs {
@@ -95,6 +96,7 @@ struct KernelSet {
     batch_fn batch;          // persistent multi-lattice step (V = 1)
     int (*batch_occupancy)(int block);
     step_fn bgk;             // BGK comparison operator, register pull with V = 1
+    step_fn theta;           // filtered collision with the energy-flux term (K >= 3), V = 1
 };
 
 // Defined in the instantiation units, one per lattice.

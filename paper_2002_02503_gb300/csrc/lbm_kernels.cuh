@@ -79,11 +79,12 @@ __host__ __device__ constexpr int floordiv(int e, int V) { return e >= 0 ? e / V
 // the missing values directly.  Every lane of the warp must call this (the
 // shuffles use the full mask); lanes with active == false compute on a valid
 // clamped position and store nothing.
-template <class LT, int K, class ST, int V, bool BGK = false>
+template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false>
 __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restrict__ src,
                                                    typename ST::S *__restrict__ dst, int nx, int ny, int nz, int ncx,
                                                    long long P, int y, int z, int chunk, bool active,
-                                                   typename ST::T relax, typename ST::T rho0) {
+                                                   typename ST::T relax, typename ST::T rho0,
+                                                   typename ST::T kq = typename ST::T(0)) {
     using S = typename ST::S;
     using T = typename ST::T;
     constexpr int Q = LT::Q, M = LT::MAXC;
@@ -154,7 +155,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
 #pragma unroll
         for (int i = 0; i < Q; ++i) g[i] = f[i][j];
         if constexpr (BGK) collide_bgk<LT, K, T>(g, relax, rho0);
-        else collide<LT, K, T>(g, relax, rho0);
+        else collide<LT, K, T, THETA>(g, relax, rho0, kq);
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i][j] = g[i];
     }
@@ -170,11 +171,11 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
     }
 }
 
-template <class LT, int K, class ST, int V, bool BGK = false>
+template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false>
 __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *__restrict__ src,
                                                           typename ST::S *__restrict__ dst, int nx, int ny,
                                                           int ncx, long long P, typename ST::T relax,
-                                                          typename ST::T rho0) {
+                                                          typename ST::T rho0, typename ST::T kq) {
     const int z = blockIdx.y;
     const int total = ncx * ny;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -182,7 +183,8 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
     if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
     const int y = t / ncx;
     const int chunk = t - y * ncx;
-    pull_collide_store<LT, K, ST, V, BGK>(src, dst, nx, ny, gridDim.y, ncx, P, y, z, chunk, active, relax, rho0);
+    pull_collide_store<LT, K, ST, V, BGK, THETA>(src, dst, nx, ny, gridDim.y, ncx, P, y, z, chunk, active, relax,
+                                                 rho0, kq);
 }
 
 // ------------------------------------------------------------------ batched step
@@ -243,7 +245,7 @@ int batch_occupancy(int block) {
     return n;
 }
 
-template <class LT, int K, class ST, int V, bool BGK = false>
+template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false>
 cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream) {
     using T = typename ST::T;
     if (a.nx % V) return cudaErrorInvalidValue;
@@ -254,9 +256,11 @@ cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream
     const long long gx = (total + block - 1) / block;
     if (gx > 0x7fffffffLL || a.nz > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)gx, (unsigned)a.nz);
-    step_direct_kernel<LT, K, ST, V, BGK><<<grid, block, 0, stream>>>(
+    // (1 - 1/tau) theta / (6 T0^3): weight of the energy-flux part (Eq. pq)
+    const double kq = a.relax * a.theta / (6.0 * LT::T0 * LT::T0 * LT::T0);
+    step_direct_kernel<LT, K, ST, V, BGK, THETA><<<grid, block, 0, stream>>>(
         static_cast<const typename ST::S *>(a.src), static_cast<typename ST::S *>(a.dst), a.nx, a.ny, ncx, a.P,
-        T(a.relax), T(a.rho0));
+        T(a.relax), T(a.rho0), T(kq));
     return cudaGetLastError();
 }
 
@@ -513,6 +517,12 @@ constexpr step_fn direct_if_built() {
 }
 
 template <class LT, int K, class ST>
+constexpr step_fn theta_if_built() {
+    if constexpr (K >= 3) return &launch_step_direct<LT, K, ST, 1, false, true>;
+    else return nullptr;
+}
+
+template <class LT, int K, class ST>
 const KernelSet *make_kernel_set() {
     static const KernelSet ks = {
         {direct_if_built<LT, K, ST, 1>(), direct_if_built<LT, K, ST, 2>(), direct_if_built<LT, K, ST, 4>(),
@@ -527,6 +537,7 @@ const KernelSet *make_kernel_set() {
         &launch_batch<LT, K, ST>,
         &batch_occupancy<LT, K, ST>,
         &launch_step_direct<LT, K, ST, 1, true>,
+        theta_if_built<LT, K, ST>(),
     };
     return &ks;
 }

@@ -43,6 +43,7 @@ SIGNATURES = [
     ("lbm_set_kernel", _c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int]),
     ("lbm_get_kernel", _c.c_int, [_P, _IP, _IP, _IP]),
     ("lbm_set_collision", _c.c_int, [_P, _c.c_int]),
+    ("lbm_set_energy_flux", _c.c_int, [_P, _c.c_double]),
     ("lbm_autotune", _c.c_int, [_P, _c.c_int, _DP]),
     ("lbm_conservation_noalloc", _c.c_int, [_c.c_int, _c.c_int, _I64P, _c.c_double, _P, _P, _c.c_int, _P]),
     ("lbm_destroy", _c.c_int, [_P]),
@@ -223,6 +224,10 @@ COLLISIONS = {"filtered": 0, "bgk": 1}
 
 def lbm_set_collision(h, model):
     _check(lib().lbm_set_collision(h, COLLISIONS[model] if isinstance(model, str) else int(model)))
+
+
+def lbm_set_energy_flux(h, theta):
+    _check(lib().lbm_set_energy_flux(h, float(theta)))
 
 
 def lbm_autotune(h, iters=10):
