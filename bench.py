@@ -390,10 +390,15 @@ def run_ours(a):
                 pool_stats, _ = serve.serve_pool(trace)
                 pool16_stats, _ = serve.serve_pool(trace, storage="f16")
                 plain_stats, _ = serve.serve_plain(trace)
+                # capacity: the same requests all arriving at once
+                burst = [dict(r, arrival=0.0) for r in trace]
+                burst_pool, _ = serve.serve_pool(burst)
+                burst_plain, _ = serve.serve_plain(burst)
                 extras["serving"] = {
                     "workload": "%d D3Q19 Taylor-Green solves, side log-uniform 32-128, tau U[0.52,1], "
                                 "u0 U[0.01,0.08], 100-2000 steps, Poisson %g/s, FP32, K=3" % (a.serve, a.serve_rate),
-                    "pool": pool_stats, "pool_f16_storage": pool16_stats, "plain_fifo": plain_stats}
+                    "pool": pool_stats, "pool_f16_storage": pool16_stats, "plain_fifo": plain_stats,
+                    "capacity_all_at_once": {"pool": burst_pool, "plain_fifo": burst_plain}}
         out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": DTYPE_NAME[a.storage], "data": "synthetic (Taylor-Green initial field)",
