@@ -1,0 +1,78 @@
+"""Edge cases of the CUDA library: degenerate lattice sizes, a no-op step, and the largest
+lattice of the benchmark family that one GPU holds.
+
+* 1x1x1 (D3Q19) and 3x3x3 (D3Q39, the smallest its velocities allow) periodic lattices and odd
+  sizes, against the oracle;
+* n = 0 steps changes nothing;
+* a uniform state (rho = 1, u = U everywhere) is a fixed point of the collision and the
+  streaming: it must stay uniform to the last bit across the lattice, on D3Q19 1024^3 with FP16
+  storage (81.6 GB of distributions), and conserve mass and momentum.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_02503_gb300 import fields, lbm
+
+from _lbmtest import TOL_F32, oracle_reference, rel_f, rel_u
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name,K,dims", [("D3Q19", 3, (1, 1, 1)), ("D3Q19", 2, (5, 7, 9)), ("D3Q39", 4, (3, 3, 3)),
+                                         ("D3Q39", 4, (7, 5, 3)), ("D2Q9", 3, (1, 1, 1)), ("D2Q9", 3, (3, 11, 1)),
+                                         ("D3Q27", 3, (2, 3, 1)), ("D3Q15", 3, (9, 1, 5))])
+def test_degenerate_and_odd_sizes(name, K, dims):
+    D = lbm.lbm_lattice_info(name)["D"]
+    rho, u = fields.random_fields(dims, D, salt=60)
+    f_ref, r_ref, u_ref = oracle_reference(name, K, 0.6, dims, rho, u, 20)
+    s = lbm.Solver(name, dims, 0.6, K, "f32")
+    s.set_fields(rho, u)
+    s.step(20)
+    r, uu = s.moments()
+    s.close()
+    assert rel_f(r, r_ref) < TOL_F32
+    assert rel_u(uu, u_ref) < TOL_F32
+
+
+def test_zero_steps_is_a_no_op():
+    dims = (16, 8, 4)
+    rho, u = fields.random_fields(dims, 3, salt=61)
+    s = lbm.Solver("D3Q19", dims, 0.6, 3, "f32")
+    s.set_fields(rho, u)
+    a = np.empty(s.raw_bytes(), dtype=np.uint8)
+    lbm.lbm_get_distributions(s.handle, a)
+    s.step(0)
+    b = np.empty_like(a)
+    assert lbm.lbm_get_distributions(s.handle, b) == 0
+    np.testing.assert_array_equal(a, b)
+    s.close()
+
+
+def test_uniform_flow_stays_uniform_at_maximum_size():
+    import torch
+
+    dims = (1024, 1024, 1024)
+    C = 1024 ** 3
+    U = (0.05, -0.02, 0.01)
+    rho = torch.ones(C, dtype=torch.float64, device="cuda")
+    u = torch.empty((3, C), dtype=torch.float64, device="cuda")
+    for a in range(3):
+        u[a].fill_(U[a])
+    s = lbm.Solver("D3Q19", dims, 0.55, 3, "f16")
+    s.set_fields(rho, u)
+    del rho, u
+    torch.cuda.empty_cache()
+    c0 = s.conservation()
+    s.step(10)
+    c1 = s.conservation()
+    np.testing.assert_allclose(c1, c0, rtol=1e-12, atol=1e-9 * C)
+    raw = torch.empty(s.raw_bytes(), dtype=torch.uint8, device="cuda")
+    lbm.lbm_get_distributions(s.handle, raw)
+    planes = raw.view(torch.int16).view(19, C)
+    first = planes[:, :1]
+    assert bool((planes == first).all())  # every cell holds the same 19 stored values
+    s.close()
+    del raw, planes
+    torch.cuda.empty_cache()
+    np.testing.assert_allclose(c1[1:] / c1[0], U, rtol=2e-3)
