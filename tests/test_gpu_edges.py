@@ -4,9 +4,9 @@ lattice of the benchmark family that one GPU holds.
 * 1x1x1 (D3Q19) and 3x3x3 (D3Q39, the smallest its velocities allow) periodic lattices and odd
   sizes, against the oracle;
 * n = 0 steps changes nothing;
-* a uniform state (rho = 1, u = U everywhere) is a fixed point of the collision and the
-  streaming: it must stay uniform to the last bit across the lattice, on D3Q19 1024^3 with FP16
-  storage (81.6 GB of distributions), and conserve mass and momentum.
+* a uniform state (rho = 1, u = U everywhere) is left uniform by the collision and the
+  streaming: every cell must hold the same stored values to the last bit, on D3Q19 1024^3 with
+  FP16 storage (81.6 GB of distributions), with mass and momentum kept to the storage rounding.
 """
 import numpy as np
 import pytest
@@ -66,7 +66,9 @@ def test_uniform_flow_stays_uniform_at_maximum_size():
     c0 = s.conservation()
     s.step(10)
     c1 = s.conservation()
-    np.testing.assert_allclose(c1, c0, rtol=1e-12, atol=1e-9 * C)
+    # FP16 storage rounds each stored value (|h| ~ 0.15, half an ulp ~ 6e-5): the sums agree to that
+    np.testing.assert_allclose(c1[0], c0[0], rtol=2e-4)
+    np.testing.assert_allclose(c1[1:], c0[1:], rtol=0, atol=2e-4 * c0[0])
     raw = torch.empty(s.raw_bytes(), dtype=torch.uint8, device="cuda")
     lbm.lbm_get_distributions(s.handle, raw)
     planes = raw.view(torch.int16).view(19, C)
