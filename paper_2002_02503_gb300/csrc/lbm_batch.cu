@@ -203,6 +203,8 @@ int build_table(lbm_pool *p, int b, int *units_total) {
         s.steps_left = int(std::min<int64_t>(left, 1 << 30));
         s.unit0 = units;
         s.units = int((r.C + p->block - 1) / p->block);
+        fastdiv_init(unsigned(r.nx), &s.mx, &s.sx);
+        fastdiv_init(unsigned(r.ny), &s.my, &s.sy);
         units += s.units;
         ++n;
     }

@@ -75,7 +75,19 @@ struct BatchSlot {
     int steps_left;    // steps still to run at the start of the chunk
     int unit0;         // first work unit of this slot (table sorted by unit0)
     int units;         // work units of this slot
+    unsigned int mx, sx, my, sy;  // division by nx and ny as multiply-high + shift (fastdiv_init)
 };
+
+// Division by a runtime constant d (1 <= d < 2^31) as q = (umulhi(n, m) + n) >> s for
+// 0 <= n < 2^31 -- the round-up multiply-and-shift method of Granlund and Montgomery (1994):
+// s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1, so that (m + 2^32) / 2^(32+s) exceeds 1/d by
+// less than 2^-(32+s), which keeps n (m + 2^32) / 2^(32+s) below floor(n/d) + 1 for n < 2^31.
+inline void fastdiv_init(unsigned int d, unsigned int *m, unsigned int *s) {
+    unsigned int l = 0;
+    while ((1ull << l) < d) ++l;
+    *m = (unsigned int)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    *s = l;
+}
 
 typedef cudaError_t (*step_fn)(const StepArgs &, int block_threads, cudaStream_t);
 typedef cudaError_t (*batch_fn)(const BatchSlot *slots, const int *header, int step_index, int grid, int block,

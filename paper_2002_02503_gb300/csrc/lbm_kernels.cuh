@@ -189,40 +189,43 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
 
 // ------------------------------------------------------------------ batched step
 // Persistent kernel over the work units of every slot in a table (one unit =
-// blockDim.x consecutive V-chunks of one lattice).  One launch advances every
-// slot with step_index < steps_left by one step; the slot's buffers alternate
-// with its parity.  The table lives in device memory, so a captured graph of
-// launches stays valid while the host rewrites the table between chunks.
+// blockDim.x consecutive cells of one lattice, one cell per thread).  One launch
+// advances every slot with step_index < steps_left by one step; the slot's buffers
+// alternate with its parity.  The table lives in device memory, so a captured graph
+// of launches stays valid while the host rewrites the table between chunks.
+__device__ __forceinline__ int fastdiv(int n, unsigned int m, unsigned int s) {
+    return int((__umulhi((unsigned int)n, m) + (unsigned int)n) >> s);
+}
+
 template <class LT, int K, class ST, int V>
 __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__restrict__ slots,
                                                          const int *__restrict__ header, int step_index) {
-    __shared__ int sh_slot;
     const int total_units = header[0];
     const int nslots = header[1];
+    // grid-stride over units (neighbouring CTAs work on neighbouring rows at the same time);
+    // units only increase, so each thread walks the slot index forward without a barrier
+    int slot = 0;
     for (int unit = blockIdx.x; unit < total_units; unit += gridDim.x) {
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = nslots - 1;  // last slot with unit0 <= unit
+        if (slot + 1 < nslots && slots[slot + 1].unit0 <= unit) {
+            int lo = slot + 1, hi = nslots - 1;  // last slot with unit0 <= unit
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (slots[mid].unit0 <= unit) lo = mid;
                 else hi = mid - 1;
             }
-            sh_slot = lo;
+            slot = lo;
         }
-        __syncthreads();
-        const BatchSlot &sl = slots[sh_slot];
-        __syncthreads();  // sh_slot is rewritten in the next iteration
-        if (step_index >= sl.steps_left) continue;
+        const BatchSlot &sl = slots[slot];
+        if (step_index >= sl.steps_left) continue;  // uniform across the CTA
         const int cur = (sl.parity + step_index) & 1;
-        const int per_plane = sl.ncx * sl.ny;
-        const int total = per_plane * sl.nz;
+        const int total = sl.ncx * sl.ny * sl.nz;
         int t = (unit - sl.unit0) * blockDim.x + threadIdx.x;
         const bool active = t < total;
         if (!active) t = total - 1;
-        const int z = t / per_plane;
-        const int rem = t - z * per_plane;
-        const int y = rem / sl.ncx;
-        const int chunk = rem - y * sl.ncx;
+        const int row = fastdiv(t, sl.mx, sl.sx);  // ncx = nx for V = 1
+        const int chunk = t - row * sl.ncx;
+        const int z = fastdiv(row, sl.my, sl.sy);
+        const int y = row - z * sl.ny;
         pull_collide_store<LT, K, ST, V>(static_cast<const typename ST::S *>(sl.buf[cur]),
                                          static_cast<typename ST::S *>(sl.buf[cur ^ 1]), sl.nx, sl.ny, sl.nz, sl.ncx,
                                          sl.P, y, z, chunk, active, typename ST::T(sl.relax),
