@@ -196,7 +196,8 @@ step_fn step_for(const lbm_solver *s, int variant, int V) {
         if (k < 0 || s->nx % V) return nullptr;
         return s->ks->direct[k];
     }
-    if (variant == 1) return s->ks->staged;
+    if (variant == 1)
+        return (s->ks->staged && s->ks->staged_applies && s->ks->staged_applies(s->nx)) ? s->ks->staged : nullptr;
     return nullptr;
 }
 
@@ -215,6 +216,20 @@ void staging(const lbm_solver *s, int busy, char **ptr, size_t *bytes) {
         *ptr = reinterpret_cast<char *>(s->partials);
         *bytes = kPartialBytes;
     }
+}
+
+// The staged step records a bounded-wait expiry in the workspace's status word; the
+// synchronous calls read (and clear) it.
+lbm_status check_device_status(lbm_solver *s) {
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, s->status, sizeof(v), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "status word");
+    if (v != 0) {
+        cudaMemsetAsync(s->status, 0, sizeof(unsigned int), s->stream);
+        return fail(LBM_ERR_TIMEOUT, "a bounded wait in the staged step expired (status 0x%x)", v);
+    }
+    return LBM_OK;
 }
 
 }  // namespace
@@ -320,6 +335,11 @@ lbm_status lbm_create(lbm_lattice lat, const int64_t dims[3], double tau, int K,
             s->V = V;
             break;
         }
+    cudaError_t me = cudaMemsetAsync(s->status, 0, sizeof(unsigned int), s->stream);
+    if (me != cudaSuccess) {
+        delete s;
+        return cuda_fail(me, "lbm_create: clear status word");
+    }
     *out = s;
     return LBM_OK;
 }
@@ -460,6 +480,7 @@ lbm_status lbm_step(lbm_solver *s, int64_t n) {
 }
 
 static lbm_status pull_out(lbm_solver *s, double *rho, double *u, double *f, lbm_mem mem) {
+    if (lbm_status st = check_device_status(s)) return st;
     const int D = s->li.D, Q = s->li.Q;
     PullArgs a;
     a.src = s->buf[s->cur];
@@ -533,6 +554,7 @@ lbm_status lbm_get_f(lbm_solver *s, double *f, lbm_mem mem) {
 }
 
 static lbm_status reduce_to_host(lbm_solver *s, reduce_fn fn, ReduceArgs &a, int nvals, double *out) {
+    if (lbm_status st = check_device_status(s)) return st;
     a.src = s->buf[s->cur];
     a.nx = s->nx;
     a.ny = s->ny;

@@ -109,6 +109,7 @@ struct KernelSet {
     int (*batch_occupancy)(int block);
     step_fn bgk;             // BGK comparison operator, register pull with V = 1
     step_fn theta;           // filtered collision with the energy-flux term (K >= 3), V = 1
+    bool (*staged_applies)(int nx);  // variant 1 needs nx * sizeof(storage) % 16 == 0 and a fitting tile
 };
 
 // Defined in the instantiation units, one per lattice.

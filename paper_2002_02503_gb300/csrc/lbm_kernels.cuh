@@ -12,6 +12,7 @@
 
 #include "lbm_core.cuh"
 #include "lbm_internal.h"
+#include "lbm_staged.cuh"
 
 namespace lbm {
 
@@ -520,6 +521,18 @@ constexpr step_fn direct_if_built() {
 }
 
 template <class LT, int K, class ST>
+constexpr step_fn staged_if_built() {
+    if constexpr (sizeof(typename ST::S) == 8) return nullptr;  // FP64 storage: register pull only
+    else return &launch_step_staged<LT, K, ST>;
+}
+
+template <class LT, class ST>
+constexpr bool (*staged_check_if_built())(int) {
+    if constexpr (sizeof(typename ST::S) == 8) return nullptr;
+    else return &staged_applies<LT, ST>;
+}
+
+template <class LT, int K, class ST>
 constexpr step_fn theta_if_built() {
     if constexpr (K >= 3) return &launch_step_direct<LT, K, ST, 1, false, true>;
     else return nullptr;
@@ -530,8 +543,8 @@ const KernelSet *make_kernel_set() {
     static const KernelSet ks = {
         {direct_if_built<LT, K, ST, 1>(), direct_if_built<LT, K, ST, 2>(), direct_if_built<LT, K, ST, 4>(),
          direct_if_built<LT, K, ST, 8>()},
-        nullptr,
-        0,
+        staged_if_built<LT, K, ST>(),
+        kStagedThreads,
         &launch_init<LT, K, ST>,
         &launch_moments<LT, ST>,
         &launch_pull_f<LT, ST>,
@@ -541,6 +554,7 @@ const KernelSet *make_kernel_set() {
         &batch_occupancy<LT, K, ST>,
         &launch_step_direct<LT, K, ST, 1, true>,
         theta_if_built<LT, K, ST>(),
+        staged_check_if_built<LT, ST>(),
     };
     return &ks;
 }

@@ -1,0 +1,250 @@
+// lbm_staged.cuh -- step variant 1: persistent CTAs that stage the source rows of
+// each tile into shared memory with bulk asynchronous copies (cp.async.bulk, the
+// non-tensor TMA path) completing on mbarriers, in a ring of S stages.
+//
+// A tile is R consecutive x-rows (row index y + ny z) of nx cells.  For each tile
+// and velocity i the source row (y - c_iy, z - c_iz) of plane i is copied whole
+// (nx values, contiguous and 16-byte aligned), so the x shift and its periodic
+// wrap become shared-memory indexing.  One elected thread issues the Q*R copies
+// of a tile S-1 tiles ahead; all threads wait on the stage's mbarrier, compute
+// their cells from shared memory and store coalesced rows to the other buffer.
+//
+// Every wait is bounded by a clock budget: on expiry the CTA records
+// kStagedTimeout in the status word, drains (again bounded) the copies it has in
+// flight, and returns.  The host reports it as LBM_ERR_TIMEOUT.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdlib.h>
+
+#include "lbm_core.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+constexpr unsigned int kStagedTimeout = 1u;
+constexpr long long kWaitBudgetCycles = 2000000000LL;  // ~1 s at the maximum SM clock
+constexpr int kStagedThreads = 256;
+
+__device__ __forceinline__ unsigned int smem_addr(const void *p) {
+    return static_cast<unsigned int>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned int bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned int parity) {
+    unsigned int ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a stage's phase; false when the clock budget ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned int parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitBudgetCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst_smem, const void *src_gmem, unsigned int bytes,
+                                              unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Stage layout in dynamic shared memory: S mbarriers, then S stages of Q*R rows of nx values.
+template <class LT, class ST>
+__device__ __forceinline__ void issue_tile(const typename ST::S *__restrict__ src, typename ST::S *stage,
+                                           unsigned long long *bar, int tile, int R, int rows, int nx, int ny,
+                                           int nz, long long P, unsigned int extra_tx) {
+    using S = typename ST::S;
+    const int r0 = tile * R;
+    const int nr = min(R, rows - r0);
+    const unsigned int row_bytes = unsigned(nx) * sizeof(S);
+    mbar_arrive_expect_tx(bar, unsigned(LT::Q * nr) * row_bytes + extra_tx);
+    for (int r = 0; r < nr; ++r) {
+        const int row = r0 + r;
+        const int y = row % ny, z = row / ny;
+#pragma unroll
+        for (int i = 0; i < LT::Q; ++i) {
+            int ys = y - vel<LT>(i, 1), zs = z - vel<LT>(i, 2);
+            ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);  // dims >= max|c| (host-checked)
+            zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+            bulk_copy_g2s(stage + (size_t(i) * R + r) * nx, src + i * P + (long long)(zs * ny + ys) * nx, row_bytes,
+                          bar);
+        }
+    }
+}
+
+template <class LT, int K, class ST>
+__global__ void __launch_bounds__(kStagedThreads) step_staged_kernel(const typename ST::S *__restrict__ src,
+                                                                     typename ST::S *__restrict__ dst, int nx, int ny,
+                                                                     int nz, long long P, int R, int S_stages,
+                                                                     typename ST::T relax, typename ST::T rho0,
+                                                                     unsigned int *__restrict__ status,
+                                                                     unsigned int extra_tx) {
+    using S = typename ST::S;
+    using T = typename ST::T;
+    constexpr int Q = LT::Q, M = LT::MAXC;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem_raw);
+    S *stages = reinterpret_cast<S *>(smem_raw + 128);
+    const size_t stage_elems = size_t(Q) * R * nx;
+    const int rows = ny * nz;
+    const int tiles = (rows + R - 1) / R;
+    const int cells = R * nx;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S_stages; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // prologue: the first S tiles of this CTA
+    int issued = 0;  // tiles issued so far (tile index = blockIdx.x + k * gridDim.x)
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S_stages; ++s) {
+            const int tile = blockIdx.x + s * gridDim.x;
+            if (tile >= tiles) break;
+            // extra_tx (0 in normal use) makes the first phase wait for bytes that never come:
+            // the test hook of the bounded wait
+            issue_tile<LT, ST>(src, stages + s * stage_elems, &bars[s], tile, R, rows, nx, ny, nz, P,
+                               s == 0 ? extra_tx : 0u);
+        }
+    }
+    issued = S_stages;
+
+    bool failed = false;
+    int k = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++k) {
+        const int s = k % S_stages;
+        const unsigned int parity = (k / S_stages) & 1;
+        const bool ok = mbar_wait_bounded(&bars[s], parity);
+        if (__syncthreads_or(!ok)) {  // one CTA-wide decision, so no thread is left at a barrier
+            failed = true;
+            break;
+        }
+        const S *st = stages + s * stage_elems;
+        const int r0 = tile * R;
+        for (int c = threadIdx.x; c < cells; c += blockDim.x) {
+            const int r = c / nx;
+            const int x = c - r * nx;
+            const int row = r0 + r;
+            if (row >= rows) break;
+            int xs[2 * M + 1];
+#pragma unroll
+            for (int q = -M; q <= M; ++q) {
+                int v = x - q;
+                xs[q + M] = v < 0 ? v + nx : (v >= nx ? v - nx : v);
+            }
+            T g[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] = decode<ST, LT>(st[(size_t(i) * R + r) * nx + xs[vel<LT>(i, 0) + M]], i);
+            collide<LT, K, T>(g, relax, rho0);
+            S *out = dst + (long long)row * nx + x;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) out[(long long)i * P] = encode<ST, LT>(g[i], i);
+        }
+        __syncthreads();  // every thread is done reading stage s
+        if (threadIdx.x == 0) {
+            const int next = blockIdx.x + (k + S_stages) * gridDim.x;
+            if (next < tiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_tile<LT, ST>(src, stages + s * stage_elems, &bars[s], next, R, rows, nx, ny, nz, P, 0u);
+            }
+        }
+    }
+    if (failed) {
+        if (threadIdx.x == 0 && status) atomicOr(status, kStagedTimeout);
+        // drain the copies this CTA still has in flight before its shared memory goes away
+        const int n_issued = min(issued + k, (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
+        for (int kk = k; kk < n_issued; ++kk) {
+            if (!mbar_wait_bounded(&bars[kk % S_stages], (kk / S_stages) & 1)) break;
+        }
+    }
+}
+
+// Rows per tile and stages for a lattice / storage / nx; 0 when the variant does not apply.
+template <class LT, class ST>
+inline void staged_geometry(int nx, int *R, int *S, size_t *smem) {
+    *R = 0;
+    *S = 0;
+    *smem = 0;
+    const size_t row_bytes = size_t(nx) * sizeof(typename ST::S);
+    if (row_bytes % 16 != 0 || nx > 4096) return;
+    int r = (kStagedThreads + nx - 1) / nx;
+    if (r < 1) r = 1;
+    const size_t stage = size_t(LT::Q) * r * row_bytes;
+    int s = int((200u * 1024u) / stage);
+    if (s > 4) s = 4;
+    if (s < 2) return;
+    *R = r;
+    *S = s;
+    *smem = 128 + size_t(s) * stage;
+}
+
+template <class LT, class ST>
+bool staged_applies(int nx) {
+    int R, S;
+    size_t smem;
+    staged_geometry<LT, ST>(nx, &R, &S, &smem);
+    return R > 0;
+}
+
+template <class LT, int K, class ST>
+cudaError_t launch_step_staged(const StepArgs &a, int block, cudaStream_t stream) {
+    using T = typename ST::T;
+    (void)block;
+    int R, S;
+    size_t smem;
+    staged_geometry<LT, ST>(a.nx, &R, &S, &smem);
+    if (R == 0) return cudaErrorInvalidValue;
+    static int configured = 0;  // opt in to large dynamic shared memory once per process and device setup
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(step_staged_kernel<LT, K, ST>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        configured = 1;
+    }
+    // LBM_TEST_STAGED_EXTRA_TX=<bytes>: test hook that makes every CTA's first wait expire (read once)
+    static const unsigned int extra_tx = [] {
+        const char *v = getenv("LBM_TEST_STAGED_EXTRA_TX");
+        return v ? unsigned(strtoul(v, nullptr, 10)) : 0u;
+    }();
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_staged_kernel<LT, K, ST>,
+                                                                  kStagedThreads, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int rows = a.ny * a.nz;
+    const int tiles = (rows + R - 1) / R;
+    int grid = per_sm * sms;
+    if (grid > tiles) grid = tiles;
+    step_staged_kernel<LT, K, ST><<<grid, kStagedThreads, smem, stream>>>(
+        static_cast<const typename ST::S *>(a.src), static_cast<typename ST::S *>(a.dst), a.nx, a.ny, a.nz, a.P, R,
+        S, T(a.relax), T(a.rho0), a.status, extra_tx);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

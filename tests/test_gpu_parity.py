@@ -103,6 +103,11 @@ def _built_variants(name, K, storage, nx):
                 out.append((0, V, block))
             except lbm.LbmError:
                 pass
+    try:  # the staged (bulk-copy) variant, where the row size allows it
+        lbm.lbm_set_kernel(s.handle, 1, 1, 256)
+        out.append((1, 1, 256))
+    except lbm.LbmError:
+        pass
     s.close()
     return out
 
@@ -330,3 +335,22 @@ def test_energy_flux_needs_order_three():
     assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
     lbm.lbm_set_energy_flux(s.handle, 0.0)
     s.close()
+
+
+@pytest.mark.parametrize("name,K,storage,dims", [("D3Q19", 2, "f32", (256, 64, 32)), ("D3Q19", 3, "f16", (40, 26, 14)),
+                                                 ("D3Q39", 4, "f32", (28, 18, 10)), ("D3Q27", 3, "f32", (96, 20, 12))])
+def test_staged_variant_matches_oracle(name, K, storage, dims):
+    """Step variant 1 (rows staged in shared memory by bulk asynchronous copies)."""
+    D = lbm.lbm_lattice_info(name)["D"]
+    rho, u = fields.random_smooth_fields(dims, D, salt=70)
+    f_ref, r_ref, u_ref = oracle_reference(name, K, 0.6, dims, rho, u, 50)
+    s = lbm.Solver(name, dims, 0.6, K, storage)
+    lbm.lbm_set_kernel(s.handle, 1, 1, 256)
+    assert lbm.lbm_get_kernel(s.handle)[0] == 1
+    s.set_fields(rho, u)
+    s.step(50)
+    r, uu = s.moments()
+    s.close()
+    tol = TOL_F32 if storage == "f32" else 2e-3
+    assert rel_u(uu, u_ref) < tol
+    assert rel_f(r, r_ref) < tol
