@@ -92,6 +92,19 @@ template <class LT>
 __host__ __device__ constexpr int vel(int i, int a) {
     return i == 0 ? 0 : ((i & 1) ? LT::c((i - 1) >> 1, a) : -LT::c((i - 1) >> 1, a));
 }
+// Runtime-index form (a small table in constant-folded code is not possible when i is not a
+// compile-time constant): component a of velocity i.
+template <class LT>
+__device__ __forceinline__ int vel_rt(int i, int a) {
+    if (i == 0) return 0;
+    const int p = (i - 1) >> 1;
+    int v = 0;
+#pragma unroll
+    for (int q = 0; q < LT::NP; ++q)
+        if (q == p) v = LT::c(q, a);
+    return (i & 1) ? v : -v;
+}
+
 template <class LT>
 __host__ __device__ constexpr double weight(int i) {
     return i == 0 ? LT::w0 : LT::w((i - 1) >> 1);
