@@ -16,8 +16,9 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
 
-UNITS = ["lbm_api.cu", "lbm_inst_d2q9.cu", "lbm_inst_d3q15.cu", "lbm_inst_d3q19.cu", "lbm_inst_d3q27.cu", "lbm_inst_d3q39.cu",
-         "lbm_batch.cu", "lbm_noalloc.cu"]
+UNITS = ["lbm_api.cu", "lbm_inst_d2q9.cu", "lbm_inst_d3q15.cu", "lbm_inst_d3q19.cu", "lbm_inst_d3q27.cu",
+         "lbm_inst_d3q39.cu", "lbm_inst_d3q39_k2.cu", "lbm_inst_d3q39_k3.cu", "lbm_inst_d3q39_k4.cu",
+         "lbm_inst_d3q39_k5.cu", "lbm_batch.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -66,8 +67,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
                 print(r.stderr)
         return obj
 
+    order = sorted(srcs, key=lambda f: 0 if "d3q39_k" in f else 1)  # longest units start first
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+        done = dict(zip(order, ex.map(compile_one, order)))
+    objs = [done[f] for f in srcs]
     if force or _stale(LIB, objs):
         tmp = LIB + ".tmp.%d" % os.getpid()
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
