@@ -23,6 +23,8 @@
  *     error, lbm_last_error() holds a message for the calling thread.
  *   - Nothing is allocated on the device by the library except a few bytes of
  *     kernel-argument tables: the caller owns the workspace and every buffer.
+ *   - A solver is not thread-safe: calls on one solver must not overlap; distinct
+ *     solvers are independent.  A pool serialises its own calls internally.
  */
 #ifndef LBM_H
 #define LBM_H

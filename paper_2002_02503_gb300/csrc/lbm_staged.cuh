@@ -271,12 +271,19 @@ cudaError_t launch_step_staged(const StepArgs &a, int block, cudaStream_t stream
     size_t smem;
     staged_geometry<LT, ST>(a.nx, &R, &S, &smem, &threads);
     if (R == 0) return cudaErrorInvalidValue;
-    static int configured = 0;  // opt in to large dynamic shared memory once per process and device setup
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(step_staged_kernel<LT, K, ST>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // opt in to large dynamic shared memory once per device (the attribute is per device)
+    static unsigned long long configured = 0;
+    {
+        int cur = 0;
+        cudaError_t e = cudaGetDevice(&cur);
         if (e != cudaSuccess) return e;
-        configured = 1;
+        const unsigned long long bit = cur < 64 ? (1ull << cur) : 0ull;
+        if (!bit || !(configured & bit)) {
+            e = cudaFuncSetAttribute(step_staged_kernel<LT, K, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     227 * 1024);
+            if (e != cudaSuccess) return e;
+            configured |= bit;
+        }
     }
     // LBM_TEST_STAGED_EXTRA_TX=<bytes>: test hook that makes every CTA's first wait expire (read once)
     static const unsigned int extra_tx = [] {
