@@ -21,8 +21,11 @@
  *     device memory of the solver's device.
  *   - Every call returns an lbm_status; none throws, aborts or exits.  On an
  *     error, lbm_last_error() holds a message for the calling thread.
- *   - Nothing is allocated on the device by the library except a few bytes of
- *     kernel-argument tables: the caller owns the workspace and every buffer.
+ *   - The library makes no device-memory allocation: the caller owns the
+ *     workspace, the pool arena and every buffer.  It creates CUDA streams,
+ *     events and graphs for its own scheduling, pinned host memory for a pool's
+ *     slot tables, and holds one fixed 128 KiB device array (see
+ *     lbm_conservation_noalloc).
  *   - A solver is not thread-safe: calls on one solver must not overlap; distinct
  *     solvers are independent.  A pool serialises its own calls internally.
  */
