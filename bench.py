@@ -56,7 +56,40 @@ def parse():
                    help="requests of the serving trace (2000 = the full Poisson workload; 0 = skip)")
     p.add_argument("--serve-rate", type=float, default=50.0)
     p.add_argument("--extra-steps", type=int, default=200)
+    p.add_argument("--precision-report", action="store_true",
+                   help="D3Q19 512^3 Taylor-Green tau=0.52, 500 steps: FP32/FP16/BF16 storage against FP64 storage")
     return p.parse_args()
+
+
+def precision_report(stream):
+    """Relative u and rho errors of the FP32, FP16 and BF16 storage forms after 500 steps of the
+    D3Q19 512^3 Taylor-Green vortex (u0 = 0.05, tau = 0.52, K = 2), measured against the same run
+    with FP64 storage and arithmetic (the FP64 oracle is too slow for this size; the FP64 path
+    matches it within 1e-12 on the parity cases)."""
+    import torch
+
+    from paper_2002_02503_gb300 import fields, lbm
+
+    dims = (512, 512, 512)
+    rho, u = fields.taylor_green_3d(dims, 0.05, 1.0 / 3.0)
+    out = {}
+    ref = None
+    for storage in ("f64", "f32", "f16", "bf16"):
+        s = lbm.Solver("D3Q19", dims, 0.52, 2, storage, stream=stream)
+        s.set_fields(rho, u)
+        s.step(500)
+        r, uu = s.moments()
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        if ref is None:
+            ref = (r, uu)
+            continue
+        out[storage] = {"rel_u": float(np.max(np.abs(uu - ref[1])) / np.max(np.abs(ref[1]))),
+                        "rel_rho": float(np.max(np.abs(r - ref[0]) / ref[0]))}
+        del r, uu
+    return {"workload": "D3Q19 512^3 Taylor-Green u0=0.05 tau=0.52 K=2, 500 steps",
+            "reference": "FP64 storage and arithmetic (same library)", "errors": out}
 
 
 # (lattice, dims, K, storage, tau, u0): the other lattices and storages of the workload family
@@ -380,6 +413,9 @@ def run_ours(a):
         if not a.no_cpu_baseline:
             cpu = oracle_sample(a, a.cpu_seconds)
         extras = {}
+        if a.precision_report:
+            with torch.cuda.stream(stream):
+                extras["precision"] = precision_report(stream)
         if not a.no_extras:
             with torch.cuda.stream(stream):
                 extras["per_lattice"] = [measure_lattice(*cfg, a.extra_steps, stream) for cfg in PER_LATTICE]
