@@ -143,3 +143,30 @@ def test_served_results_same_as_alone():
     assert plain["solves"] == 24
     for i in keep:
         np.testing.assert_allclose(pres[i][1], res[i][1], rtol=0, atol=TOL_F32 * np.abs(res[i][1]).max())
+
+
+@pytest.mark.parametrize("lattice,K,storage,sides", [("D3Q19", 3, "f16", [20, 33]), ("D3Q39", 4, "f32", [9, 14]),
+                                                     ("D3Q27", 2, "bf16", [12, 17])])
+def test_pool_other_classes_match_single_lattice(lattice, K, storage, sides):
+    """Pools of other (lattice, K, storage) classes against the single-lattice solver."""
+    T0 = lbm.lbm_lattice_info(lattice)["T0"]
+    pool = lbm.Pool(lattice, K, storage, 1 << 30, 16)
+    ids = []
+    for side in sides:
+        rho, u = fields.taylor_green_3d((side,) * 3, 0.05, T0)
+        ids.append(pool.submit((side,) * 3, 0.65, rho, u, 25))
+    while not all(pool.poll(i)[0] for i in ids):
+        pool.advance(10)
+        pool.sync()
+    tol = TOL_F32 if storage == "f32" else 2e-3
+    for side, rid in zip(sides, ids):
+        r, u = pool.result(rid, side ** 3)
+        s = lbm.Solver(lattice, (side,) * 3, 0.65, K, storage)
+        rho0, u0 = fields.taylor_green_3d((side,) * 3, 0.05, T0)
+        s.set_fields(rho0, u0)
+        s.step(25)
+        rs, us = s.moments()
+        s.close()
+        assert rel_f(r, rs) < tol
+        assert rel_u(u, us) < tol
+    pool.close()
