@@ -158,7 +158,7 @@ def test_pool_other_classes_match_single_lattice(lattice, K, storage, sides):
     while not all(pool.poll(i)[0] for i in ids):
         pool.advance(10)
         pool.sync()
-    tol = TOL_F32 if storage == "f32" else 2e-3
+    tol = {"f32": TOL_F32, "f16": 2e-3, "bf16": 2e-2}[storage]  # a one-ulp flip of a 16-bit value
     for side, rid in zip(sides, ids):
         r, u = pool.result(rid, side ** 3)
         s = lbm.Solver(lattice, (side,) * 3, 0.65, K, storage)
