@@ -28,8 +28,10 @@ import numpy as np  # noqa: E402
 
 LATTICE_Q = {"D2Q9": 9, "D3Q15": 15, "D3Q19": 19, "D3Q27": 27, "D3Q39": 39}
 LATTICE_T0 = {"D2Q9": 1.0 / 3.0, "D3Q15": 1.0 / 3.0, "D3Q19": 1.0 / 3.0, "D3Q27": 1.0 / 3.0, "D3Q39": 2.0 / 3.0}
-STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}
-DTYPE_NAME = {"f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)", "f64": "f64"}
+STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8, "q16": 2}
+DTYPE_NAME = {"f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)", "f64": "f64",
+              "q16": "f32 (16-bit fixed-point storage)"}
+Q16_RANGE = 0.25  # fixed-point range for the Taylor-Green workloads (u0 = 0.05: |h| up to about 0.16)
 KERNEL_SOURCES = ["lbm_core.cuh", "lbm_kernels.cuh", "lbm_lattice.cuh"]
 
 
@@ -45,6 +47,7 @@ def parse():
     p.add_argument("--tau", type=float, default=0.55)
     p.add_argument("--u0", type=float, default=0.05)
     p.add_argument("--storage", default="f32", choices=list(STORE_BYTES))
+    p.add_argument("--storage-range", type=float, default=Q16_RANGE, help="range of the q16 storage (power of two)")
     p.add_argument("--variant", type=int, default=None, help="force a kernel variant (default: autotune)")
     p.add_argument("--cpt", type=int, default=None, help="force cells per thread (with --variant 0)")
     p.add_argument("--block", type=int, default=None)
@@ -57,12 +60,14 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=50.0)
     p.add_argument("--extra-steps", type=int, default=200)
     p.add_argument("--precision-report", action="store_true",
-                   help="D3Q19 512^3 Taylor-Green tau=0.52, 500 steps: FP32/FP16/BF16 storage against FP64 storage")
+                   help="D3Q19 512^3 Taylor-Green tau=0.52, 500 steps: FP32/FP16/BF16/Q16 storage against FP64 "
+                        "storage")
     return p.parse_args()
 
 
 def precision_report(stream):
-    """Relative u and rho errors of the FP32, FP16 and BF16 storage forms after 500 steps of the
+    """Relative u and rho errors of the FP32, FP16, BF16 and 16-bit fixed-point (range 1/4) storage
+    forms after 500 steps of the
     D3Q19 512^3 Taylor-Green vortex (u0 = 0.05, tau = 0.52, K = 2), measured against the same run
     with FP64 storage and arithmetic (the FP64 oracle is too slow for this size; the FP64 path
     matches it within 1e-12 on the parity cases)."""
@@ -74,8 +79,9 @@ def precision_report(stream):
     rho, u = fields.taylor_green_3d(dims, 0.05, 1.0 / 3.0)
     out = {}
     ref = None
-    for storage in ("f64", "f32", "f16", "bf16"):
-        s = lbm.Solver("D3Q19", dims, 0.52, 2, storage, stream=stream)
+    for storage in ("f64", "f32", "f16", "bf16", "q16"):
+        s = lbm.Solver("D3Q19", dims, 0.52, 2, storage, stream=stream,
+                       storage_range=Q16_RANGE if storage == "q16" else None)
         s.set_fields(rho, u)
         s.step(500)
         r, uu = s.moments()
@@ -100,6 +106,7 @@ PER_LATTICE = [
     ("D3Q19", (512, 512, 512), 2, "f32", 0.52, 0.05),
     ("D3Q19", (512, 512, 512), 2, "f16", 0.52, 0.05),
     ("D3Q19", (512, 512, 512), 2, "bf16", 0.52, 0.05),
+    ("D3Q19", (512, 512, 512), 2, "q16", 0.52, 0.05),
 ]
 
 
@@ -110,7 +117,8 @@ def measure_lattice(lattice, dims, K, storage, tau, u0, steps, stream):
     from paper_2002_02503_gb300 import fields, lbm
 
     rho, u = fields.taylor_green_3d(dims, u0, LATTICE_T0[lattice])
-    s = lbm.Solver(lattice, dims, tau, K, storage, stream=stream)
+    s = lbm.Solver(lattice, dims, tau, K, storage, stream=stream,
+                   storage_range=Q16_RANGE if storage == "q16" else None)
     s.set_fields(rho, u)
     del rho, u
     lbm.lbm_autotune(s.handle, 10)
@@ -146,6 +154,8 @@ def config_of(a, extra=None):
          "u0": a.u0, "storage": a.storage, "parallelism": "replicas",
          "l2": "inputs larger than L2: %.2f GB of distributions per step" % (
              2 * LATTICE_Q[a.lattice] * STORE_BYTES[a.storage] * int(np.prod(a.dims)) / 1e9)}
+    if a.storage == "q16":
+        c["storage_range"] = a.storage_range
     if extra:
         c.update(extra)
     return c
@@ -345,7 +355,8 @@ def run_ours(a):
         torch.cuda.synchronize()
 
     with torch.cuda.stream(stream):
-        s = lbm.Solver(a.lattice, dims, a.tau, a.K, a.storage, stream=stream)
+        s = lbm.Solver(a.lattice, dims, a.tau, a.K, a.storage, stream=stream,
+                       storage_range=a.storage_range if a.storage == "q16" else None)
         s.set_fields(rho, u)
         tuned_us = None
         if a.variant is None:

@@ -48,7 +48,9 @@ typedef enum {
     LBM_ERR_NONFINITE = 5,     /* a reduction met NaN or Inf: the run has gone unstable */
     LBM_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
     LBM_ERR_BUSY = 7,          /* no free slot or memory in a pool right now */
-    LBM_ERR_NOT_FOUND = 8      /* unknown request id */
+    LBM_ERR_NOT_FOUND = 8,     /* unknown request id */
+    LBM_ERR_RANGE = 9          /* a value left the range of the fixed-point storage (or was not
+                                  finite); the stored state is no longer valid */
 } lbm_status;
 
 /* Velocity sets.  D2Q9, D3Q15, D3Q19: isotropy class 2N = 4, T0 = 1/3 (Sec. 2
@@ -57,12 +59,21 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2, LBM_D3Q39 = 3, LBM_D3
 
 /* How distributions are stored in HBM.  The collision always computes in FP32
  * (FP64 for LBM_STORE_F64).  Every form stores the shifted, scaled value
- * h_i = (g_i - w_i rho0) / w_i, rounded to nearest (even) in the storage type. */
+ * h_i = (g_i - w_i rho0) / w_i, rounded to nearest (even) in the storage type.
+ * LBM_STORE_Q16 is 16-bit fixed point: h = q * R / 2^15 with the integer q in
+ * [-32767, 32767] and the range R a power of two (lbm_set_storage_range; default 1).
+ * Its grid step is uniform, where FP16's grows with |h|, so for flows whose |h|
+ * stays below R/2 it rounds 4-16 times finer than FP16 at the same two bytes.  A
+ * value outside +-R (or not finite) is not stored faithfully: the step records it
+ * and the next synchronising call returns LBM_ERR_RANGE.  Q16 runs on the register
+ * pull step (variant 0, every cells_per_thread, BGK and the energy-flux term); pools,
+ * the staged variant and lbm_conservation_noalloc reject it (LBM_ERR_UNSUPPORTED). */
 typedef enum {
     LBM_STORE_F32 = 0,
     LBM_STORE_F16 = 1,
     LBM_STORE_BF16 = 2,
-    LBM_STORE_F64 = 3
+    LBM_STORE_F64 = 3,
+    LBM_STORE_Q16 = 4
 } lbm_storage;
 
 typedef enum { LBM_MEM_HOST = 0, LBM_MEM_DEVICE = 1 } lbm_mem;
@@ -154,6 +165,14 @@ lbm_status lbm_set_collision(lbm_solver *s, lbm_collision model);
  * default) is the paper's Sec. 3 collision.  Applies to the filtered collision;
  * runs one cell per thread.  LBM_ERR_UNSUPPORTED for K = 2. */
 lbm_status lbm_set_energy_flux(lbm_solver *s, double theta);
+
+/* Range R of the fixed-point storage (LBM_STORE_Q16): |h_i| <= R, grid step R / 2^15.
+ * R must be a power of two in [2^-8, 2^8].  The stored codes are not converted, so set
+ * it before lbm_set_fields or lbm_set_distributions (a checkpoint restores with the
+ * range it was taken with).  |h_i| is about |c_i . u| / T0 plus the density excursion
+ * rho - rho0 and the non-equilibrium part, so R = 1/4 holds flows with |c_i . u| up to
+ * about 0.07 on the T0 = 1/3 lattices.  LBM_ERR_UNSUPPORTED for the floating forms. */
+lbm_status lbm_set_storage_range(lbm_solver *s, double range);
 
 /* Autotuner: times every built kernel configuration for this solver on its own
  * buffers (reads the current state, writes only the idle buffer, so the state is

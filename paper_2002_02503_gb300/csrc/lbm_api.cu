@@ -81,6 +81,7 @@ size_t storage_size(lbm_storage st) {
     case LBM_STORE_F16: return 2;
     case LBM_STORE_BF16: return 2;
     case LBM_STORE_F64: return 8;
+    case LBM_STORE_Q16: return 2;
     }
     return 0;
 }
@@ -161,6 +162,7 @@ struct lbm_solver {
     int variant, V, block;
     lbm_collision model;
     double theta;  // energy-flux weight (Eq. pq); 0 = the paper's Sec. 3 collision
+    int qexp;      // fixed-point storage: grid step 2^qexp (range 2^(qexp + 15))
     double graph_theta;
     // Captured graphs of kGraphSteps consecutive steps, one per starting buffer; rebuilt
     // when the kernel configuration changes.  They cut the per-step launch cost, which
@@ -173,7 +175,7 @@ struct lbm_solver {
 namespace {
 
 StepArgs step_args(const lbm_solver *s, int from) {
-    StepArgs a;
+    StepArgs a = {};
     a.src = s->buf[from];
     a.dst = s->buf[from ^ 1];
     a.nx = s->nx;
@@ -185,6 +187,7 @@ StepArgs step_args(const lbm_solver *s, int from) {
     a.status = s->status;
     a.grid_limit = 0;
     a.theta = s->theta;
+    a.qs = qscale_of_exponent(s->qexp);
     return a;
 }
 
@@ -218,8 +221,9 @@ void staging(const lbm_solver *s, int busy, char **ptr, size_t *bytes) {
     }
 }
 
-// The staged step records a bounded-wait expiry in the workspace's status word; the
-// synchronous calls read (and clear) it.
+// The kernels record events in the workspace's status word (kStatus* bits): a
+// bounded-wait expiry of the staged step, a value outside the fixed-point storage's
+// range.  The synchronous calls read (and clear) it.
 lbm_status check_device_status(lbm_solver *s) {
     unsigned int v = 0;
     cudaError_t e = cudaMemcpyAsync(&v, s->status, sizeof(v), cudaMemcpyDeviceToHost, s->stream);
@@ -227,7 +231,9 @@ lbm_status check_device_status(lbm_solver *s) {
     if (e != cudaSuccess) return cuda_fail(e, "status word");
     if (v != 0) {
         cudaMemsetAsync(s->status, 0, sizeof(unsigned int), s->stream);
-        return fail(LBM_ERR_TIMEOUT, "a bounded wait in the staged step expired (status 0x%x)", v);
+        if (v & kStatusTimeout)
+            return fail(LBM_ERR_TIMEOUT, "a bounded wait in the staged step expired (status 0x%x)", v);
+        return fail(LBM_ERR_RANGE, "a value left the fixed-point storage range +-2^%d (status 0x%x)", s->qexp + 15, v);
     }
     return LBM_OK;
 }
@@ -247,6 +253,7 @@ const char *lbm_status_string(lbm_status st) {
     case LBM_ERR_TIMEOUT: return "timeout";
     case LBM_ERR_BUSY: return "busy";
     case LBM_ERR_NOT_FOUND: return "not found";
+    case LBM_ERR_RANGE: return "value outside the storage range";
     }
     return "unknown status";
 }
@@ -327,6 +334,7 @@ lbm_status lbm_create(lbm_lattice lat, const int64_t dims[3], double tau, int K,
     s->t = 0;
     s->ks = ks;
     s->model = LBM_COLLISION_FILTERED_GI;
+    s->qexp = -15;  // fixed-point range 1
     s->variant = 0;
     s->block = 256;
     s->V = 1;
@@ -361,13 +369,15 @@ lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm
     if (!rho || !u) return fail(LBM_ERR_INVALID_ARG, "rho and u are required");
     if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return fail(LBM_ERR_INVALID_ARG, "bad lbm_mem");
     const int D = s->li.D;
-    InitArgs a;
+    InitArgs a = {};
     a.dst = s->buf[0];
     a.nx = s->nx;
     a.ny = s->ny;
     a.nz = s->nz;
     a.P = s->C;
     a.rho0 = s->rho0;
+    a.qs = qscale_of_exponent(s->qexp);
+    a.status = s->status;
     if (mem == LBM_MEM_DEVICE) {
         a.rho = rho;
         a.u = u;
@@ -402,7 +412,7 @@ lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm
     LBM_CUDA(cudaStreamSynchronize(s->stream), "set_fields: synchronize");
     s->cur = 0;
     s->t = 0;
-    return LBM_OK;
+    return check_device_status(s);  // LBM_ERR_RANGE if f^eq does not fit the fixed-point range
 }
 
 static void drop_step_graphs(lbm_solver *s) {
@@ -482,13 +492,14 @@ lbm_status lbm_step(lbm_solver *s, int64_t n) {
 static lbm_status pull_out(lbm_solver *s, double *rho, double *u, double *f, lbm_mem mem) {
     if (lbm_status st = check_device_status(s)) return st;
     const int D = s->li.D, Q = s->li.Q;
-    PullArgs a;
+    PullArgs a = {};
     a.src = s->buf[s->cur];
     a.nx = s->nx;
     a.ny = s->ny;
     a.nz = s->nz;
     a.P = s->C;
     a.rho0 = s->rho0;
+    a.qs = qscale_of_exponent(s->qexp);
     pull_fn fn = f ? s->ks->pull_f : s->ks->moments;
     if (mem == LBM_MEM_DEVICE) {
         a.rho = rho;
@@ -564,6 +575,7 @@ static lbm_status reduce_to_host(lbm_solver *s, reduce_fn fn, ReduceArgs &a, int
     a.partials = s->partials;
     a.out = s->red_out;
     a.blocks = kReduceBlocks;
+    a.qs = qscale_of_exponent(s->qexp);
     LBM_CUDA(fn(a, s->stream), "reduction kernel");
     LBM_CUDA(cudaMemcpyAsync(out, s->red_out, nvals * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
              "copy reduction");
@@ -681,6 +693,21 @@ lbm_status lbm_set_energy_flux(lbm_solver *s, double theta) {
                 s->V = V;
                 break;
             }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_storage_range(lbm_solver *s, double range) {
+    if (lbm_status r = check_solver(s)) return r;
+    if (s->st != LBM_STORE_Q16) return fail(LBM_ERR_UNSUPPORTED, "only the fixed-point storage has a range");
+    int e2 = 0;
+    const double m = frexp(range, &e2);  // range = m 2^e2, m in [1/2, 1)
+    if (!(range > 0.0) || !isfinite(range) || m != 0.5 || e2 - 1 < -8 || e2 - 1 > 8)
+        return fail(LBM_ERR_INVALID_ARG, "range must be a power of two in [2^-8, 2^8] (got %g)", range);
+    const int qexp = (e2 - 1) - 15;
+    if (qexp != s->qexp) {
+        drop_step_graphs(s);  // the grid step is baked into captured launches
+        s->qexp = qexp;
     }
     return LBM_OK;
 }

@@ -216,7 +216,7 @@ int build_table(lbm_pool *p, int b, int *units_total) {
 
 lbm_status pull_to(lbm_pool *p, Request &r, double *rho, double *u, lbm_mem mem) {
     const int cur = r.parity;
-    PullArgs a;
+    PullArgs a = {};
     a.src = r.buf[cur];
     a.nx = r.nx;
     a.ny = r.ny;
@@ -285,6 +285,7 @@ lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, 
     int D, Q, maxc, kmax;
     if (!lattice_query(lat, &D, &Q, &maxc, &kmax)) return set_error(LBM_ERR_INVALID_ARG, "unknown lattice");
     if (storage_bytes(st) == 0) return set_error(LBM_ERR_UNSUPPORTED, "unknown storage");
+    if (st == LBM_STORE_Q16) return set_error(LBM_ERR_UNSUPPORTED, "pools serve the floating storage forms");
     if (K < 2 || K > kmax) return set_error(LBM_ERR_UNSUPPORTED, "truncation order outside [2, 2N-1]");
     if (!arena || reinterpret_cast<uintptr_t>(arena) % kAlign)
         return set_error(LBM_ERR_INVALID_ARG, "arena must be non-NULL and 256-byte aligned");
@@ -372,7 +373,7 @@ lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, doubl
         p->arena.release(r.off, r.bytes);
         return set_cuda_error(e, "pool: event");
     }
-    InitArgs a;
+    InitArgs a = {};
     a.dst = r.buf[0];
     a.nx = r.nx;
     a.ny = r.ny;

@@ -25,6 +25,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "lbm_internal.h"
 #include "lbm_lattice.cuh"
 
 namespace lbm {
@@ -34,39 +35,69 @@ namespace lbm {
 // all velocities then share one magnitude range (the D3Q39 weights span 1/12 to
 // 1/1620), and the collision below works on h directly, so neither decoding nor
 // encoding multiplies by a weight.
+//
+// QScale (lbm_internal.h) carries the step 2^e of the fixed-point form
+// (LBM_STORE_Q16); the floating forms ignore it.  A power-of-two step keeps both
+// directions below exact apart from the one rounding of h to the grid.
+
 struct StoreF32 {
     using S = float;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_F32;
-    __device__ __forceinline__ static T dec(S v) { return v; }
-    __device__ __forceinline__ static S enc(T x) { return x; }
+    __device__ __forceinline__ static T dec(S v, const QScale &) { return v; }
+    __device__ __forceinline__ static S enc(T x, const QScale &, bool &) { return x; }
 };
 struct StoreF64 {
     using S = double;
     using T = double;
     static constexpr lbm_storage id = LBM_STORE_F64;
-    __device__ __forceinline__ static T dec(S v) { return v; }
-    __device__ __forceinline__ static S enc(T x) { return x; }
+    __device__ __forceinline__ static T dec(S v, const QScale &) { return v; }
+    __device__ __forceinline__ static S enc(T x, const QScale &, bool &) { return x; }
 };
 struct StoreF16 {
     using S = __half;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_F16;
-    __device__ __forceinline__ static T dec(S v) { return __half2float(v); }
-    __device__ __forceinline__ static S enc(T x) { return __float2half_rn(x); }
+    __device__ __forceinline__ static T dec(S v, const QScale &) { return __half2float(v); }
+    __device__ __forceinline__ static S enc(T x, const QScale &, bool &) { return __float2half_rn(x); }
 };
 struct StoreBF16 {
     using S = __nv_bfloat16;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_BF16;
-    __device__ __forceinline__ static T dec(S v) { return __bfloat162float(v); }
-    __device__ __forceinline__ static S enc(T x) { return __float2bfloat16_rn(x); }
+    __device__ __forceinline__ static T dec(S v, const QScale &) { return __bfloat162float(v); }
+    __device__ __forceinline__ static S enc(T x, const QScale &, bool &) { return __float2bfloat16_rn(x); }
+};
+// 16-bit fixed point: h = q 2^e with the integer q in [-32767, 32767], held in offset
+// binary (q + 2^15).  Both directions use the FP32 adder's rounding at magnitude 2^23,
+// where the spacing of floats is exactly 1:
+//   encode  v = fma(h, 2^-e, 2^23 + 2^15) rounds h 2^-e to the nearest integer (ties to
+//           even) and leaves q + 2^15 in the low 16 bits of v's encoding; a value outside
+//           the range (or not finite) moves v out of [2^23 + 1, 2^23 + 65535], which the
+//           one unsigned compare below detects (the caller reports it);
+//   decode  the bits 0x4B000000 | (q + 2^15) are the float 2^23 + 2^15 + q, and
+//           fma(that, 2^e, -(2^23 + 2^15) 2^e) = q 2^e exactly.
+struct StoreQ16 {
+    using S = unsigned short;
+    using T = float;
+    static constexpr lbm_storage id = LBM_STORE_Q16;
+    static constexpr float kBias = 8421376.0f;  // 2^23 + 2^15
+    __device__ __forceinline__ static T dec(S v, const QScale &q) {
+        return fmaf(__uint_as_float(0x4B000000u | unsigned(v)), q.mul, q.off);
+    }
+    __device__ __forceinline__ static S enc(T x, const QScale &q, bool &bad) {
+        const unsigned int b = __float_as_uint(fmaf(x, q.inv, kBias));
+        bad |= (b - 0x4B000001u) > 65534u;
+        return static_cast<S>(b);
+    }
 };
 
 // Vector decode / encode of V consecutive values of one velocity plane; the 16-bit
-// forms convert two values per instruction (half2 / bfloat162).
+// floating forms convert two values per instruction (half2 / bfloat162).  encode_vec
+// sets bad when the fixed-point form meets a value outside its range.
 template <class ST, int V>
-__device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typename ST::T (&out)[V]) {
+__device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typename ST::T (&out)[V],
+                                           const QScale &q) {
     if constexpr (ST::id == LBM_STORE_F16 && V % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
@@ -83,12 +114,13 @@ __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typen
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < V; ++j) out[j] = ST::dec(raw[j]);
+        for (int j = 0; j < V; ++j) out[j] = ST::dec(raw[j], q);
     }
 }
 
 template <class ST, int V>
-__device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typename ST::S (&raw)[V]) {
+__device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typename ST::S (&raw)[V],
+                                           const QScale &q, bool &bad) {
     if constexpr (ST::id == LBM_STORE_F16 && V % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
@@ -105,18 +137,18 @@ __device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typena
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < V; ++j) raw[j] = ST::enc(in[j]);
+        for (int j = 0; j < V; ++j) raw[j] = ST::enc(in[j], q, bad);
     }
 }
 
-// Scaled value h of velocity i (the weight index is kept for call sites that need it).
-template <class ST, class LT>
-__device__ __forceinline__ typename ST::T decode(typename ST::S v, int) {
-    return ST::dec(v);
+// Scaled value h of one stored value, and back.
+template <class ST>
+__device__ __forceinline__ typename ST::T decode(typename ST::S v, const QScale &q) {
+    return ST::dec(v, q);
 }
-template <class ST, class LT>
-__device__ __forceinline__ typename ST::S encode(typename ST::T x, int) {
-    return ST::enc(x);
+template <class ST>
+__device__ __forceinline__ typename ST::S encode(typename ST::T x, const QScale &q, bool &bad) {
+    return ST::enc(x, q, bad);
 }
 
 // ------------------------------------------------------------------ moments

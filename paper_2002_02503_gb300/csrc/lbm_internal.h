@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <math.h>
+
 #include <string>
 
 #include "../../include/lbm.h"
@@ -16,6 +18,24 @@ constexpr int kNumV = 4;
 inline int v_index(int V) { return V == 1 ? 0 : V == 2 ? 1 : V == 4 ? 2 : V == 8 ? 3 : -1; }
 inline int v_of_index(int k) { return 1 << k; }
 
+// Grid step of the fixed-point storage (LBM_STORE_Q16) as the three constants the
+// codec uses: mul = 2^e, inv = 2^-e, off = -(2^23 + 2^15) 2^e, all exact in FP32 for
+// |e| <= 30.  The floating storage forms ignore it.
+struct QScale {
+    float mul, inv, off;
+};
+inline QScale qscale_of_exponent(int e) {
+    QScale q;
+    q.mul = ldexpf(1.0f, e);
+    q.inv = ldexpf(1.0f, -e);
+    q.off = -ldexpf(8421376.0f, e);
+    return q;
+}
+
+// Bits of the device status word.
+constexpr unsigned int kStatusTimeout = 1u;  // a bounded wait of the staged step expired
+constexpr unsigned int kStatusRange = 2u;    // a value left the fixed-point storage's range
+
 struct StepArgs {
     const void *src;  // stored distributions at t (post-collision of t-1, un-streamed)
     void *dst;        // stored distributions at t+1
@@ -23,9 +43,10 @@ struct StepArgs {
     long long P;      // cells per velocity plane (nx*ny*nz)
     double relax;     // 1 - 1/tau
     double rho0;
-    unsigned int *status;  // device status word (persistent variant), may be null
+    unsigned int *status;  // device status word (kStatus* bits); may be null for floating storage
     int grid_limit;        // persistent variant: CTAs to launch (0 = one per SM slot)
     double theta;          // weight of the energy-flux part (Eq. pq); 0 = off
+    QScale qs;         // fixed-point grid step (LBM_STORE_Q16 only)
 };
 
 struct InitArgs {
@@ -37,6 +58,8 @@ struct InitArgs {
     int nx, ny, nz;
     long long P;
     double rho0;
+    QScale qs;
+    unsigned int *status;  // receives kStatusRange when a value does not fit the fixed-point range
 };
 
 struct PullArgs {
@@ -49,6 +72,7 @@ struct PullArgs {
     int nx, ny, nz;
     long long P;
     double rho0;
+    QScale qs;
 };
 
 struct ReduceArgs {
@@ -61,6 +85,7 @@ struct ReduceArgs {
     int blocks;
     int k[3];              // mode wave vector
     int component;         // mode velocity component
+    QScale qs;
 };
 
 // One lattice of a batch (device-resident table entry).
@@ -98,14 +123,14 @@ typedef cudaError_t (*reduce_fn)(const ReduceArgs &, cudaStream_t);
 
 struct KernelSet {
     step_fn direct[kNumV];   // variant 0, per V (null where not built)
-    step_fn staged;          // variant 1 (null where not built)
+    step_fn staged;          // variant 1 (null where not built: FP64 and fixed-point storage)
     int staged_block;        // threads per CTA the staged variant is built for
     init_fn init;
     pull_fn moments;
     pull_fn pull_f;
     reduce_fn conservation;  // nvals = 4
     reduce_fn mode;          // nvals = 2
-    batch_fn batch;          // persistent multi-lattice step (V = 1)
+    batch_fn batch;          // persistent multi-lattice step (V = 1); null for fixed-point storage
     int (*batch_occupancy)(int block);
     step_fn bgk;             // BGK comparison operator, register pull with V = 1
     step_fn theta;           // filtered collision with the energy-flux term (K >= 3), V = 1

@@ -84,8 +84,8 @@ template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false
 __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restrict__ src,
                                                    typename ST::S *__restrict__ dst, int nx, int ny, int nz, int ncx,
                                                    long long P, int y, int z, int chunk, bool active,
-                                                   typename ST::T relax, typename ST::T rho0,
-                                                   typename ST::T kq = typename ST::T(0)) {
+                                                   typename ST::T relax, typename ST::T rho0, typename ST::T kq,
+                                                   const QScale &qs, unsigned int *__restrict__ status) {
     using S = typename ST::S;
     using T = typename ST::T;
     constexpr int Q = LT::Q, M = LT::MAXC;
@@ -116,7 +116,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         for (int i = 0; i < Q; ++i) {
             const int cx = vel<LT>(i, 0), cy = vel<LT>(i, 1), cz = vel<LT>(i, 2);
             const S *row = src + (long long)i * P + (long long)(zs[cz + M] * ny + ys[cy + M]) * nx;
-            f[i][0] = decode<ST, LT>(row[xs[cx + M]], i);
+            f[i][0] = decode<ST>(row[xs[cx + M]], qs);
         }
     } else {
 #pragma unroll
@@ -126,7 +126,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         S raw[V];
         load_vec<S, V>(row + x0, raw);
         T v[V];
-        decode_vec<ST, V>(raw, v);
+        decode_vec<ST, V>(raw, v, qs);
         if (cx == 0) {
 #pragma unroll
             for (int j = 0; j < V; ++j) f[i][j] = v[j];
@@ -142,7 +142,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
                     // source lane lane+dl holds chunk+dl of the same row unless at a warp or row edge
                     const int sl = lane + dl;
                     T sh = __shfl_sync(kFull, v[ei], sl < 0 ? 0 : (sl > 31 ? 31 : sl));
-                    if (!ok[dl + kMaxDl]) sh = decode<ST, LT>(row[wrap1(x0 + e, nx)], i);
+                    if (!ok[dl + kMaxDl]) sh = decode<ST>(row[wrap1(x0 + e, nx)], qs);
                     f[i][j] = sh;
                 }
             }
@@ -161,14 +161,19 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         for (int i = 0; i < Q; ++i) f[i][j] = g[i];
     }
 
+    bool bad = false;
     if (active) {
         S *out = dst + (long long)(z * ny + y) * nx + x0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             S raw[V];
-            encode_vec<ST, V>(f[i], raw);
+            encode_vec<ST, V>(f[i], raw, qs, bad);
             store_vec<S, V>(out + (long long)i * P, raw);
         }
+    }
+    if constexpr (ST::id == LBM_STORE_Q16) {
+        // one flag per warp that met a value outside the fixed-point range
+        if (__any_sync(kFull, bad) && lane == 0 && status) atomicOr(status, kStatusRange);
     }
 }
 
@@ -176,7 +181,8 @@ template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false
 __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *__restrict__ src,
                                                           typename ST::S *__restrict__ dst, int nx, int ny,
                                                           int ncx, long long P, typename ST::T relax,
-                                                          typename ST::T rho0, typename ST::T kq) {
+                                                          typename ST::T rho0, typename ST::T kq, QScale qs,
+                                                          unsigned int *__restrict__ status) {
     const int z = blockIdx.y;
     const int total = ncx * ny;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
     const int y = t / ncx;
     const int chunk = t - y * ncx;
     pull_collide_store<LT, K, ST, V, BGK, THETA>(src, dst, nx, ny, gridDim.y, ncx, P, y, z, chunk, active, relax,
-                                                 rho0, kq);
+                                                 rho0, kq, qs, status);
 }
 
 // ------------------------------------------------------------------ batched step
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__rest
         pull_collide_store<LT, K, ST, V>(static_cast<const typename ST::S *>(sl.buf[cur]),
                                          static_cast<typename ST::S *>(sl.buf[cur ^ 1]), sl.nx, sl.ny, sl.nz, sl.ncx,
                                          sl.P, y, z, chunk, active, typename ST::T(sl.relax),
-                                         typename ST::T(sl.rho0));
+                                         typename ST::T(sl.rho0), typename ST::T(0), QScale{}, nullptr);
     }
 }
 
@@ -264,7 +270,7 @@ cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream
     const double kq = a.relax * a.theta / (6.0 * LT::T0 * LT::T0 * LT::T0);
     step_direct_kernel<LT, K, ST, V, BGK, THETA><<<grid, block, 0, stream>>>(
         static_cast<const typename ST::S *>(a.src), static_cast<typename ST::S *>(a.dst), a.nx, a.ny, ncx, a.P,
-        T(a.relax), T(a.rho0), T(kq));
+        T(a.relax), T(a.rho0), T(kq), a.qs, a.status);
     return cudaGetLastError();
 }
 
@@ -275,9 +281,11 @@ cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream
 template <class LT, int K, class ST>
 __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__restrict__ rho,
                             const double *__restrict__ u, long long ustride, long long c0, long long count, int nx,
-                            int ny, int nz, long long P, double rho0) {
+                            int ny, int nz, long long P, double rho0, QScale qs,
+                            unsigned int *__restrict__ status) {
     using S = typename ST::S;
     using T = typename ST::T;
+    bool bad = false;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
          k += (long long)gridDim.x * blockDim.x) {
         const long long cell = c0 + k;
@@ -295,9 +303,10 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
             const int xs = wrapn(x - vel<LT>(i, 0), nx);
             const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
             const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
-            dst[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs] = encode<ST, LT>(T(g[i]), i);
+            dst[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs] = encode<ST>(T(g[i]), qs, bad);
         }
     }
+    if (bad && status) atomicOr(status, kStatusRange);
 }
 
 template <class LT, int K, class ST>
@@ -307,7 +316,7 @@ cudaError_t launch_init(const InitArgs &a, cudaStream_t stream) {
     if (blocks > 65535) blocks = 65535;
     init_kernel<LT, K, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<typename ST::S *>(a.dst), a.rho, a.u,
                                                                   a.ustride, a.c0, a.count, a.nx, a.ny, a.nz, a.P,
-                                                                  a.rho0);
+                                                                  a.rho0, a.qs, a.status);
     return cudaGetLastError();
 }
 
@@ -315,7 +324,7 @@ cudaError_t launch_init(const InitArgs &a, cudaStream_t stream) {
 // Pre-collision f_i(x, t) = g_i(x - c_i) decoded to FP64; rho and u per Eq. mme.
 template <class LT, class ST>
 __device__ __forceinline__ void pull_cell(const typename ST::S *__restrict__ src, long long cell, int nx, int ny,
-                                          int nz, long long P, double (&gt)[LT::Q]) {
+                                          int nz, long long P, const QScale &qs, double (&gt)[LT::Q]) {
     const int x = int(cell % nx);
     const int y = int((cell / nx) % ny);
     const int z = int(cell / ((long long)nx * ny));
@@ -324,18 +333,19 @@ __device__ __forceinline__ void pull_cell(const typename ST::S *__restrict__ src
         const int xs = wrapn(x - vel<LT>(i, 0), nx);
         const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
         const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
-        gt[i] = weight<LT>(i) * double(decode<ST, LT>(src[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs], i));
+        gt[i] = weight<LT>(i) * double(decode<ST>(src[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs], qs));
     }
 }
 
 template <class LT, class ST>
 __global__ void moments_kernel(const typename ST::S *__restrict__ src, double *__restrict__ rho,
                                double *__restrict__ u, double *__restrict__ f, long long ustride, long long fstride,
-                               long long c0, long long count, int nx, int ny, int nz, long long P, double rho0) {
+                               long long c0, long long count, int nx, int ny, int nz, long long P, double rho0,
+                               QScale qs) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
          k += (long long)gridDim.x * blockDim.x) {
         double gt[LT::Q];
-        pull_cell<LT, ST>(src, c0 + k, nx, ny, nz, P, gt);
+        pull_cell<LT, ST>(src, c0 + k, nx, ny, nz, P, qs, gt);
         if (f) {
 #pragma unroll
             for (int i = 0; i < LT::Q; ++i) f[i * fstride + k] = gt[i] + weight<LT>(i) * rho0;
@@ -365,7 +375,7 @@ cudaError_t launch_moments(const PullArgs &a, cudaStream_t stream) {
     if (blocks > 65535) blocks = 65535;
     moments_kernel<LT, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const typename ST::S *>(a.src), a.rho,
                                                                   a.u, nullptr, a.ustride, a.fstride, a.c0, a.count,
-                                                                  a.nx, a.ny, a.nz, a.P, a.rho0);
+                                                                  a.nx, a.ny, a.nz, a.P, a.rho0, a.qs);
     return cudaGetLastError();
 }
 
@@ -376,7 +386,7 @@ cudaError_t launch_pull_f(const PullArgs &a, cudaStream_t stream) {
     if (blocks > 65535) blocks = 65535;
     moments_kernel<LT, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const typename ST::S *>(a.src), nullptr,
                                                                   nullptr, a.f, a.ustride, a.fstride, a.c0, a.count,
-                                                                  a.nx, a.ny, a.nz, a.P, a.rho0);
+                                                                  a.nx, a.ny, a.nz, a.P, a.rho0, a.qs);
     return cudaGetLastError();
 }
 
@@ -422,7 +432,7 @@ __global__ void final_reduce_kernel(const double *__restrict__ partials, int blo
 // plane by plane without pulling: sum_x rho = C rho0 + sum_i sum_y g~_i(y).
 template <class LT, class ST>
 __global__ void __launch_bounds__(kReduceThreads) conservation_kernel(const typename ST::S *__restrict__ src,
-                                                                      long long P, double rho0,
+                                                                      long long P, double rho0, QScale qs,
                                                                       double *__restrict__ partials) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const long long per = (P + gridDim.x - 1) / gridDim.x;
@@ -436,7 +446,7 @@ __global__ void __launch_bounds__(kReduceThreads) conservation_kernel(const type
     long long n = 0;
     for (long long k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
 #pragma unroll
-        for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST, LT>(src[(long long)i * P + k], i));
+        for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST>(src[(long long)i * P + k], qs));
         ++n;
     }
     v[0] = double(n) * rho0;
@@ -458,7 +468,7 @@ __global__ void __launch_bounds__(kReduceThreads) conservation_kernel(const type
 template <class LT, class ST>
 cudaError_t launch_conservation(const ReduceArgs &a, cudaStream_t stream) {
     conservation_kernel<LT, ST><<<a.blocks, kReduceThreads, 0, stream>>>(static_cast<const typename ST::S *>(a.src),
-                                                                         a.P, a.rho0, a.partials);
+                                                                         a.P, a.rho0, a.qs, a.partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     final_reduce_kernel<4><<<1, 4 * 32, 0, stream>>>(a.partials, a.blocks, a.out);
@@ -469,14 +479,15 @@ cudaError_t launch_conservation(const ReduceArgs &a, cudaStream_t stream) {
 template <class LT, class ST>
 __global__ void __launch_bounds__(kReduceThreads) mode_kernel(const typename ST::S *__restrict__ src, int nx, int ny,
                                                               int nz, long long P, double rho0, int kx, int ky,
-                                                              int kz, int comp, double *__restrict__ partials) {
+                                                              int kz, int comp, QScale qs,
+                                                              double *__restrict__ partials) {
     double v[2] = {0.0, 0.0};
     const long long per = (P + gridDim.x - 1) / gridDim.x;
     const long long b0 = blockIdx.x * per;
     const long long b1 = b0 + per < P ? b0 + per : P;
     for (long long cell = b0 + threadIdx.x; cell < b1; cell += blockDim.x) {
         double gt[LT::Q];
-        pull_cell<LT, ST>(src, cell, nx, ny, nz, P, gt);
+        pull_cell<LT, ST>(src, cell, nx, ny, nz, P, qs, gt);
         double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int i = 0; i < LT::Q; ++i) {
@@ -503,7 +514,7 @@ template <class LT, class ST>
 cudaError_t launch_mode(const ReduceArgs &a, cudaStream_t stream) {
     mode_kernel<LT, ST><<<a.blocks, kReduceThreads, 0, stream>>>(static_cast<const typename ST::S *>(a.src), a.nx,
                                                                  a.ny, a.nz, a.P, a.rho0, a.k[0], a.k[1], a.k[2],
-                                                                 a.component, a.partials);
+                                                                 a.component, a.qs, a.partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     final_reduce_kernel<2><<<1, 2 * 32, 0, stream>>>(a.partials, a.blocks, a.out);
@@ -520,16 +531,35 @@ constexpr step_fn direct_if_built() {
     else return &launch_step_direct<LT, K, ST, V>;
 }
 
+// FP64 and fixed-point storage run on the register pull only; the fixed-point form
+// has no batched step either (a pool serves one floating storage class).
+template <class ST>
+constexpr bool register_pull_only() {
+    return sizeof(typename ST::S) == 8 || ST::id == LBM_STORE_Q16;
+}
+
 template <class LT, int K, class ST>
 constexpr step_fn staged_if_built() {
-    if constexpr (sizeof(typename ST::S) == 8) return nullptr;  // FP64 storage: register pull only
+    if constexpr (register_pull_only<ST>()) return nullptr;
     else return &launch_step_staged<LT, K, ST>;
 }
 
 template <class LT, class ST>
 constexpr bool (*staged_check_if_built())(int) {
-    if constexpr (sizeof(typename ST::S) == 8) return nullptr;
+    if constexpr (register_pull_only<ST>()) return nullptr;
     else return &staged_applies<LT, ST>;
+}
+
+template <class LT, int K, class ST>
+constexpr batch_fn batch_if_built() {
+    if constexpr (ST::id == LBM_STORE_Q16) return nullptr;
+    else return &launch_batch<LT, K, ST>;
+}
+
+template <class LT, int K, class ST>
+constexpr int (*batch_occupancy_if_built())(int) {
+    if constexpr (ST::id == LBM_STORE_Q16) return nullptr;
+    else return &batch_occupancy<LT, K, ST>;
 }
 
 template <class LT, int K, class ST>
@@ -550,8 +580,8 @@ const KernelSet *make_kernel_set() {
         &launch_pull_f<LT, ST>,
         &launch_conservation<LT, ST>,
         &launch_mode<LT, ST>,
-        &launch_batch<LT, K, ST>,
-        &batch_occupancy<LT, K, ST>,
+        batch_if_built<LT, K, ST>(),
+        batch_occupancy_if_built<LT, K, ST>(),
         &launch_step_direct<LT, K, ST, 1, true>,
         theta_if_built<LT, K, ST>(),
         staged_check_if_built<LT, ST>(),
@@ -566,6 +596,7 @@ const KernelSet *kernel_set_for_storage(lbm_storage st) {
     case LBM_STORE_F16: return make_kernel_set<LT, K, StoreF16>();
     case LBM_STORE_BF16: return make_kernel_set<LT, K, StoreBF16>();
     case LBM_STORE_F64: return make_kernel_set<LT, K, StoreF64>();
+    case LBM_STORE_Q16: return make_kernel_set<LT, K, StoreQ16>();
     }
     return nullptr;
 }

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kNoallocThreads) plane_sums_kernel(const typen
     long long n = 0;
     for (long long k = threadIdx.x; k < plane_cells; k += blockDim.x) {
 #pragma unroll
-        for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST, LT>(src[(long long)i * P + base + k], i));
+        for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST>(src[(long long)i * P + base + k], QScale{}));
         ++n;
     }
     double v[4] = {double(n) * rho0, 0.0, 0.0, 0.0};
@@ -122,6 +122,8 @@ extern "C" lbm_status lbm_conservation_noalloc(lbm_lattice lattice, lbm_storage 
                                                void *cuda_stream) {
     if (!dims || !distributions || !out) return set_error(LBM_ERR_INVALID_ARG, "dims, distributions and out are required");
     if (out_mem != LBM_MEM_HOST && out_mem != LBM_MEM_DEVICE) return set_error(LBM_ERR_INVALID_ARG, "bad lbm_mem");
+    if (storage == LBM_STORE_Q16)
+        return set_error(LBM_ERR_UNSUPPORTED, "the fixed-point storage needs its range: use lbm_conservation");
     if (storage != LBM_STORE_F32 && storage != LBM_STORE_F16 && storage != LBM_STORE_BF16 && storage != LBM_STORE_F64)
         return set_error(LBM_ERR_UNSUPPORTED, "unknown storage");
     if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || dims[0] * dims[1] > (int64_t(1) << 31))

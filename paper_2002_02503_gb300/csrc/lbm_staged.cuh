@@ -23,7 +23,7 @@
 
 namespace lbm {
 
-constexpr unsigned int kStagedTimeout = 1u;
+constexpr unsigned int kStagedTimeout = kStatusTimeout;
 constexpr long long kWaitBudgetCycles = 2000000000LL;  // ~1 s at the maximum SM clock
 constexpr int kStagedThreads = 32 + 512;  // one producer warp + sixteen consumer warps
 
@@ -216,11 +216,12 @@ __global__ void __launch_bounds__(kStagedThreads) step_staged_kernel(const typen
             const S *base = st + size_t(cr[j]) * nx;
             T g[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) g[i] = decode<ST, LT>(base[size_t(i) * R * nx + xs[vel<LT>(i, 0) + M]], i);
+            for (int i = 0; i < Q; ++i) g[i] = decode<ST>(base[size_t(i) * R * nx + xs[vel<LT>(i, 0) + M]], QScale{});
             collide<LT, K, T>(g, relax, rho0);
             S *out = dst + (long long)row * nx + x;
+            bool bad = false;  // floating storage only: no range to leave
 #pragma unroll
-            for (int i = 0; i < Q; ++i) out[(long long)i * P] = encode<ST, LT>(g[i], i);
+            for (int i = 0; i < Q; ++i) out[(long long)i * P] = encode<ST>(g[i], QScale{}, bad);
         }
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[s])) : "memory");

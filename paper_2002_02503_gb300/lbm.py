@@ -15,9 +15,10 @@ LIB_PATH = os.path.join(HERE, "liblbm_gb300.so")
 
 LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
 LBM_ERR_CUDA, LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_BUSY, LBM_ERR_NOT_FOUND = 4, 5, 6, 7, 8
+LBM_ERR_RANGE = 9
 LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2, "D3Q39": 3, "D3Q15": 4}
-STORAGES = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3}
-STORAGE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}
+STORAGES = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3, "q16": 4}
+STORAGE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8, "q16": 2}
 MEM_HOST, MEM_DEVICE = 0, 1
 
 # (name, restype, argtypes) of every exported entry point of include/lbm.h
@@ -44,6 +45,7 @@ SIGNATURES = [
     ("lbm_get_kernel", _c.c_int, [_P, _IP, _IP, _IP]),
     ("lbm_set_collision", _c.c_int, [_P, _c.c_int]),
     ("lbm_set_energy_flux", _c.c_int, [_P, _c.c_double]),
+    ("lbm_set_storage_range", _c.c_int, [_P, _c.c_double]),
     ("lbm_autotune", _c.c_int, [_P, _c.c_int, _DP]),
     ("lbm_conservation_noalloc", _c.c_int, [_c.c_int, _c.c_int, _I64P, _c.c_double, _P, _P, _c.c_int, _P]),
     ("lbm_destroy", _c.c_int, [_P]),
@@ -74,7 +76,7 @@ class LbmError(RuntimeError):
 def _status_name(status):
     names = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_UNSUPPORTED", 3: "LBM_ERR_OUT_OF_MEMORY",
              4: "LBM_ERR_CUDA", 5: "LBM_ERR_NONFINITE", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_BUSY",
-             8: "LBM_ERR_NOT_FOUND"}
+             8: "LBM_ERR_NOT_FOUND", 9: "LBM_ERR_RANGE"}
     return names.get(status, "LBM_STATUS_%d" % status)
 
 
@@ -230,6 +232,10 @@ def lbm_set_energy_flux(h, theta):
     _check(lib().lbm_set_energy_flux(h, float(theta)))
 
 
+def lbm_set_storage_range(h, R):
+    _check(lib().lbm_set_storage_range(h, float(R)))
+
+
 def lbm_autotune(h, iters=10):
     us = ctypes.c_double()
     _check(lib().lbm_autotune(h, int(iters), ctypes.byref(us)))
@@ -256,9 +262,11 @@ def lbm_destroy(h):
 class Solver:
     """Owns a solver handle plus its device workspace (a torch uint8 tensor).
 
-    ``stream`` is a ``torch.cuda.Stream`` (default: the current stream)."""
+    ``stream`` is a ``torch.cuda.Stream`` (default: the current stream).  ``storage_range``
+    sets the range of the fixed-point storage ("q16"; a power of two, default 1)."""
 
-    def __init__(self, lattice, dims, tau, K, storage="f32", rho0=1.0, stream=None, device=None):
+    def __init__(self, lattice, dims, tau, K, storage="f32", rho0=1.0, stream=None, device=None,
+                 storage_range=None):
         import torch
 
         self.lattice = lattice
@@ -274,6 +282,8 @@ class Solver:
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         self.handle = lbm_create(lattice, self.dims, tau, K, storage, rho0, self.workspace.data_ptr(), nbytes,
                                  self.stream.cuda_stream)
+        if storage_range is not None:
+            lbm_set_storage_range(self.handle, storage_range)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

@@ -101,3 +101,21 @@ def test_null_solver_is_rejected(L):
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_step(None, 1)
     assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+
+
+def test_fixed_point_storage_host_checks(L):
+    """The fixed-point form: two bytes per value, a range only it has, and the pool and the
+    allocation-free reduction turn it away before any device work."""
+    n16 = lbm.lbm_workspace_bytes("D3Q19", (64, 64, 64), "f16")
+    assert lbm.lbm_workspace_bytes("D3Q19", (64, 64, 64), "q16") == n16
+    assert lbm.lib().lbm_set_storage_range(None, 1.0) == lbm.LBM_ERR_INVALID_ARG
+    assert lbm.lib().lbm_status_string(lbm.LBM_ERR_RANGE) == b"value outside the storage range"
+    h = ctypes.c_void_p()
+    st = lbm.lib().lbm_pool_create(lbm.LATTICES["D3Q19"], 3, lbm.STORAGES["q16"], None, 1 << 20, 4, None, None,
+                                   ctypes.byref(h))
+    assert st == lbm.LBM_ERR_UNSUPPORTED and h.value is None
+    out = (ctypes.c_double * 4)()
+    d = (ctypes.c_int64 * 3)(8, 8, 8)
+    st = lbm.lib().lbm_conservation_noalloc(lbm.LATTICES["D3Q19"], lbm.STORAGES["q16"], d, 1.0,
+                                            ctypes.c_void_p(256), out, lbm.MEM_HOST, None)
+    assert st == lbm.LBM_ERR_UNSUPPORTED

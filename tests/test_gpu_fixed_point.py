@@ -1,0 +1,222 @@
+"""The 16-bit fixed-point storage form (LBM_STORE_Q16) through the C-ABI.
+
+h = q 2^e with q in [-32767, 32767] stored as q + 2^15 and the range R = 2^(e + 15) a power
+of two.  Checked here: the decoder is exact (integer codes in, FP64 values out, compared
+bit for bit), the encoder rounds to nearest with ties to even, a value beyond the range is
+reported as LBM_ERR_RANGE (a state whose next step leaves the range, as the oracle's own step
+shows) while the same state in a wider range is not, and results match the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_02503_gb300 import fields, lbm
+
+from _lbmtest import DIMS, TOL_U16, oracle_reference, perm_lib_to_oracle, rel_f, rel_u, to_lib_order
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    lbm.lib()
+    yield
+    torch.cuda.synchronize()
+
+
+def _pull(info, dims, stored):
+    """Pre-collision f_i(x) = g_i(x - c_i) of stored planes g (library order)."""
+    nx, ny, nz = dims
+    out = np.empty_like(stored)
+    for i in range(info["Q"]):
+        cx, cy, cz = info["c"][i]
+        out[i] = np.roll(stored[i].reshape(nz, ny, nx), (cz, cy, cx), axis=(0, 1, 2)).reshape(-1)
+    return out
+
+
+@pytest.mark.parametrize("R", [2.0 ** -8, 0.25, 1.0, 2.0 ** 8])
+def test_decode_is_exact(R):
+    name, dims = "D3Q19", (20, 9, 7)
+    info = lbm.lbm_lattice_info(name)
+    C = int(np.prod(dims))
+    g = np.random.default_rng(31).integers(1, 65536, size=(info["Q"], C), dtype=np.uint16)
+    s = lbm.Solver(name, dims, 0.6, 3, "q16", rho0=1.0, storage_range=R)
+    lbm.lbm_set_distributions(s.handle, g, 0)
+    f = s.f()
+    s.close()
+    step = R / 32768.0
+    h = (g.astype(np.float64) - 32768.0) * step  # exact: |q| < 2^15 and step a power of two
+    w = info["w"][:, None]
+    want = _pull(info, dims, w * h + w * 1.0)  # the library's FP64 decode: w h + w rho0
+    np.testing.assert_array_equal(f, want)
+
+
+def test_encode_rounds_to_nearest_even():
+    """At u = 0 the truncated equilibrium is h_i = rho - rho0 exactly, so rho - rho0 = (k + frac) 2^e
+    must store code 2^15 + round_half_even(k + frac) for every velocity."""
+    name, dims, R = "D3Q19", (16, 8, 6), 1.0
+    info = lbm.lbm_lattice_info(name)
+    C = int(np.prod(dims))
+    step = R / 32768.0
+    rg = np.random.default_rng(32)
+    k = rg.integers(-30000, 30000, size=C).astype(np.float64)
+    frac = rg.choice([0.0, 0.25, 0.5, 0.75, -0.5], size=C)
+    q = k + frac
+    rho = 1.0 + q * step
+    u = np.zeros((3, C))
+    s = lbm.Solver(name, dims, 0.6, 3, "q16", storage_range=R)
+    s.set_fields(rho, u)
+    raw = np.empty(info["Q"] * C, dtype=np.uint16)
+    lbm.lbm_get_distributions(s.handle, raw)
+    s.close()
+    code = 32768 + np.rint(q)  # numpy rounds halves to even
+    nx, ny, nz = dims
+    want = np.empty((info["Q"], C))
+    for i in range(info["Q"]):  # stored g_i(y) = f_i(y + c_i)
+        cx, cy, cz = info["c"][i]
+        want[i] = np.roll(code.reshape(nz, ny, nx), (-cz, -cy, -cx), axis=(0, 1, 2)).reshape(-1)
+    np.testing.assert_array_equal(raw.reshape(info["Q"], C).astype(np.float64), want)
+
+
+def _implosion(info, dims, R, code):
+    """Every moving velocity carries h = code 2^e toward one cell x0; everything else is h = 0."""
+    nx, ny, nz = dims
+    C = nx * ny * nz
+    stored = np.full((info["Q"], C), 32768, dtype=np.uint16)
+    x0 = (3, 4, 5)
+    for i in range(1, info["Q"]):
+        c = info["c"][i]
+        x, y, z = ((x0[0] - c[0]) % nx, (x0[1] - c[1]) % ny, (x0[2] - c[2]) % nz)
+        stored[i, x + nx * (y + ny * z)] = 32768 + code
+    return stored, x0[0] + nx * (x0[1] + ny * x0[2])
+
+
+def test_value_beyond_the_range_is_reported():
+    name, dims, K, tau = "D3Q19", (8, 8, 8), 3, 0.55
+    info = lbm.lbm_lattice_info(name)
+    R = 0.25
+    stored, cell = _implosion(info, dims, R, 32767)  # h = R (1 - 2^-15) on the incoming links
+    h0 = (stored.astype(np.float64) - 32768) * (R / 32768)
+    # the oracle's step of the same state: the rest population of x0 leaves the range
+    w = info["w"][:, None]
+    f0 = _pull(info, dims, w * h0 + w)
+    f0o = np.empty_like(f0)
+    f0o[perm_lib_to_oracle(name)] = f0
+    f1 = to_lib_order(name, oracle.run(name, K, tau, dims, f0o, 1))
+    h_rest = (f1[0, cell] - info["w"][0]) / info["w"][0]
+    assert h_rest > R, h_rest
+
+    s = lbm.Solver(name, dims, tau, K, "q16", storage_range=R)
+    lbm.lbm_set_distributions(s.handle, stored, 0)
+    s.step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        s.moments()
+    assert e.value.status == lbm.LBM_ERR_RANGE
+    s.close()
+
+    # the same physical state in twice the range: no report, and the step matches the oracle
+    stored2, _ = _implosion(info, dims, 2 * R, 16384)
+    s = lbm.Solver(name, dims, tau, K, "q16", storage_range=2 * R)
+    lbm.lbm_set_distributions(s.handle, stored2, 0)
+    s.step(1)
+    f = s.f()
+    s.close()
+    assert np.max(np.abs(f - f1) / np.abs(f1)) < 2 * R / 32768
+
+
+def test_set_fields_beyond_the_range_is_reported():
+    dims = (16, 16, 16)
+    rho, u = fields.taylor_green_3d(dims, 0.05, 1.0 / 3.0)  # |h| up to about 0.16
+    s = lbm.Solver("D3Q19", dims, 0.6, 3, "q16", storage_range=2.0 ** -4)
+    with pytest.raises(lbm.LbmError) as e:
+        s.set_fields(rho, u)
+    assert e.value.status == lbm.LBM_ERR_RANGE
+    lbm.lbm_set_storage_range(s.handle, 0.25)
+    s.set_fields(rho, u)  # fits now
+    s.close()
+
+
+def test_range_must_be_a_power_of_two_and_floating_forms_have_none():
+    s = lbm.Solver("D3Q19", DIMS["D3Q19"], 0.6, 3, "q16")
+    for bad in (0.3, 0.0, -1.0, 2.0 ** -9, 2.0 ** 9, float("nan")):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_storage_range(s.handle, bad)
+        assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+    s.close()
+    s = lbm.Solver("D3Q19", DIMS["D3Q19"], 0.6, 3, "f16")
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_storage_range(s.handle, 1.0)
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+    s.close()
+
+
+CASES = [("D2Q9", 3), ("D3Q15", 3), ("D3Q19", 2), ("D3Q19", 3), ("D3Q27", 3), ("D3Q39", 4), ("D3Q39", 5)]
+
+
+@pytest.mark.parametrize("name,K", CASES)
+def test_smooth_fields_match_oracle(name, K):
+    """Smooth seeded fields (u0 = 0.05), 100 steps, range 1/2: within the 16-bit bound on u."""
+    dims = DIMS[name]
+    D = lbm.lbm_lattice_info(name)["D"]
+    rho, u = fields.random_smooth_fields(dims, D, config_index=0, salt=K)
+    f_ref, r_ref, u_ref = oracle_reference(name, K, 0.55, dims, rho, u, 100)
+    s = lbm.Solver(name, dims, 0.55, K, "q16", storage_range=0.5)
+    s.set_fields(rho, u)
+    s.step(100)
+    r, uu = s.moments()
+    f = s.f()
+    s.close()
+    eu = rel_u(uu, u_ref)
+    print("%s K=%d q16 rel u %.3e rel f %.3e" % (name, K, eu, rel_f(f, to_lib_order(name, f_ref))))
+    assert eu < TOL_U16
+    assert rel_f(f, to_lib_order(name, f_ref)) < TOL_U16
+
+
+@pytest.mark.parametrize("V", [1, 2, 4, 8])
+def test_every_cells_per_thread_gives_the_same_codes(V):
+    """The register-pull variants differ only in how they load; with one FP32 arithmetic per cell
+    they must store identical codes."""
+    name, K, dims = "D3Q19", 3, (64, 20, 12)
+    rho, u = fields.random_smooth_fields(dims, 3, config_index=0, salt=41)
+    out = []
+    for v in (1, V):
+        s = lbm.Solver(name, dims, 0.6, K, "q16", storage_range=0.5)
+        lbm.lbm_set_kernel(s.handle, 0, v, 128)
+        s.set_fields(rho, u)
+        s.step(40)
+        raw = np.empty(s.raw_bytes() // 2, dtype=np.uint16)
+        lbm.lbm_get_distributions(s.handle, raw)
+        s.close()
+        out.append(raw)
+    assert np.count_nonzero(out[0] != out[1]) <= 1e-4 * out[0].size
+    assert np.max(np.abs(out[0].astype(np.int64) - out[1].astype(np.int64))) <= 1
+
+
+def test_bgk_and_energy_flux_run_on_fixed_point():
+    name, K, dims = "D3Q19", 3, DIMS["D3Q19"]
+    rho, u = fields.random_smooth_fields(dims, 3, config_index=0, salt=42)
+    for model, theta in (("bgk", 0.0), ("filtered", 0.7)):
+        _, r_ref, u_ref = oracle_reference_model(name, K, 0.6, dims, rho, u, 50, model, theta)
+        s = lbm.Solver(name, dims, 0.6, K, "q16", storage_range=0.5)
+        lbm.lbm_set_collision(s.handle, model)
+        lbm.lbm_set_energy_flux(s.handle, theta)
+        s.set_fields(rho, u)
+        s.step(50)
+        r, uu = s.moments()
+        s.close()
+        assert rel_u(uu, u_ref) < TOL_U16, model
+
+
+def oracle_reference_model(name, K, tau, dims, rho, u, steps, model, theta):
+    f0 = oracle.init_eq(name, K, dims, rho, u)
+    f = oracle.run(name, K, tau, dims, f0, steps, model=model, theta=theta)
+    r, uu = oracle.moments(name, dims, f)
+    return f, r, uu
+
+
+def test_pool_rejects_fixed_point():
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Pool("D3Q19", 3, "q16", 1 << 20, 4)
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
