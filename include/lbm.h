@@ -61,10 +61,11 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2, LBM_D3Q39 = 3, LBM_D3
  * (FP64 for LBM_STORE_F64).  Every form stores the shifted, scaled value
  * h_i = (g_i - w_i rho0) / w_i, rounded to nearest (even) in the storage type.
  * LBM_STORE_Q16 is 16-bit fixed point: h = q * R / 2^15 with the integer q in
- * [-32767, 32767] and the range R a power of two (lbm_set_storage_range; default 1).
+ * [-32768, 32767] (stored as q + 2^15) and the range R a power of two
+ * (lbm_set_storage_range; default 1).
  * Its grid step is uniform, where FP16's grows with |h|, so for flows whose |h|
  * stays below R/2 it rounds 4-16 times finer than FP16 at the same two bytes.  A
- * value outside +-R (or not finite) is not stored faithfully: the step records it
+ * value outside [-R, R) (or not finite) is not stored faithfully: the step records it
  * and the next synchronising call returns LBM_ERR_RANGE.  Q16 runs on the register
  * pull step (variant 0, every cells_per_thread, BGK and the energy-flux term); pools,
  * the staged variant and lbm_conservation_noalloc reject it (LBM_ERR_UNSUPPORTED). */
@@ -166,7 +167,7 @@ lbm_status lbm_set_collision(lbm_solver *s, lbm_collision model);
  * runs one cell per thread.  LBM_ERR_UNSUPPORTED for K = 2. */
 lbm_status lbm_set_energy_flux(lbm_solver *s, double theta);
 
-/* Range R of the fixed-point storage (LBM_STORE_Q16): |h_i| <= R, grid step R / 2^15.
+/* Range R of the fixed-point storage (LBM_STORE_Q16): -R <= h_i < R, grid step R / 2^15.
  * R must be a power of two in [2^-8, 2^8].  The stored codes are not converted, so set
  * it before lbm_set_fields or lbm_set_distributions (a checkpoint restores with the
  * range it was taken with).  |h_i| is about |c_i . u| / T0 plus the density excursion

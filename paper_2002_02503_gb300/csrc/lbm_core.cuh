@@ -45,36 +45,38 @@ struct StoreF32 {
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_F32;
     __device__ __forceinline__ static T dec(S v, const QScale &) { return v; }
-    __device__ __forceinline__ static S enc(T x, const QScale &, bool &) { return x; }
+    __device__ __forceinline__ static S enc(T x, const QScale &, unsigned int &) { return x; }
 };
 struct StoreF64 {
     using S = double;
     using T = double;
     static constexpr lbm_storage id = LBM_STORE_F64;
     __device__ __forceinline__ static T dec(S v, const QScale &) { return v; }
-    __device__ __forceinline__ static S enc(T x, const QScale &, bool &) { return x; }
+    __device__ __forceinline__ static S enc(T x, const QScale &, unsigned int &) { return x; }
 };
 struct StoreF16 {
     using S = __half;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_F16;
     __device__ __forceinline__ static T dec(S v, const QScale &) { return __half2float(v); }
-    __device__ __forceinline__ static S enc(T x, const QScale &, bool &) { return __float2half_rn(x); }
+    __device__ __forceinline__ static S enc(T x, const QScale &, unsigned int &) { return __float2half_rn(x); }
 };
 struct StoreBF16 {
     using S = __nv_bfloat16;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_BF16;
     __device__ __forceinline__ static T dec(S v, const QScale &) { return __bfloat162float(v); }
-    __device__ __forceinline__ static S enc(T x, const QScale &, bool &) { return __float2bfloat16_rn(x); }
+    __device__ __forceinline__ static S enc(T x, const QScale &, unsigned int &) { return __float2bfloat16_rn(x); }
 };
-// 16-bit fixed point: h = q 2^e with the integer q in [-32767, 32767], held in offset
+// 16-bit fixed point: h = q 2^e with the integer q in [-32768, 32767], held in offset
 // binary (q + 2^15).  Both directions use the FP32 adder's rounding at magnitude 2^23,
 // where the spacing of floats is exactly 1:
 //   encode  v = fma(h, 2^-e, 2^23 + 2^15) rounds h 2^-e to the nearest integer (ties to
-//           even) and leaves q + 2^15 in the low 16 bits of v's encoding; a value outside
-//           the range (or not finite) moves v out of [2^23 + 1, 2^23 + 65535], which the
-//           one unsigned compare below detects (the caller reports it);
+//           even); for q in range v lies in [2^23, 2^23 + 65535], whose encodings are
+//           exactly 0x4B00xxxx with q + 2^15 in the low 16 bits.  Any other v (out of
+//           range, negative, not finite) has different upper 16 bits, so OR-ing
+//           (bits ^ 0x4B000000) into an accumulator and testing its upper half once per
+//           cell (range_exceeded) detects it at one logic operation per value;
 //   decode  the bits 0x4B000000 | (q + 2^15) are the float 2^23 + 2^15 + q, and
 //           fma(that, 2^e, -(2^23 + 2^15) 2^e) = q 2^e exactly.
 struct StoreQ16 {
@@ -82,19 +84,25 @@ struct StoreQ16 {
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_Q16;
     static constexpr float kBias = 8421376.0f;  // 2^23 + 2^15
+    static constexpr unsigned int kExp = 0x4B000000u;
     __device__ __forceinline__ static T dec(S v, const QScale &q) {
-        return fmaf(__uint_as_float(0x4B000000u | unsigned(v)), q.mul, q.off);
+        return fmaf(__uint_as_float(kExp | unsigned(v)), q.mul, q.off);
     }
-    __device__ __forceinline__ static S enc(T x, const QScale &q, bool &bad) {
+    __device__ __forceinline__ static unsigned int enc_bits(T x, const QScale &q, unsigned int &acc) {
         const unsigned int b = __float_as_uint(fmaf(x, q.inv, kBias));
-        bad |= (b - 0x4B000001u) > 65534u;
-        return static_cast<S>(b);
+        acc |= b ^ kExp;
+        return b;
+    }
+    __device__ __forceinline__ static S enc(T x, const QScale &q, unsigned int &acc) {
+        return static_cast<S>(enc_bits(x, q, acc));
     }
 };
+// True when an encode since acc = 0 met a value outside the fixed-point range.
+__device__ __forceinline__ bool range_exceeded(unsigned int acc) { return (acc >> 16) != 0u; }
 
 // Vector decode / encode of V consecutive values of one velocity plane; the 16-bit
 // floating forms convert two values per instruction (half2 / bfloat162).  encode_vec
-// sets bad when the fixed-point form meets a value outside its range.
+// accumulates the fixed-point form's range check into acc (range_exceeded).
 template <class ST, int V>
 __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typename ST::T (&out)[V],
                                            const QScale &q) {
@@ -112,6 +120,14 @@ __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typen
             out[j] = f.x;
             out[j + 1] = f.y;
         }
+    } else if constexpr (ST::id == LBM_STORE_Q16 && V % 2 == 0) {
+        // two codes per 32-bit word: one byte permute builds each float's bits
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            const unsigned int w = unsigned(raw[j]) | (unsigned(raw[j + 1]) << 16);
+            out[j] = fmaf(__uint_as_float(__byte_perm(w, StoreQ16::kExp, 0x7610)), q.mul, q.off);
+            out[j + 1] = fmaf(__uint_as_float(__byte_perm(w, StoreQ16::kExp, 0x7632)), q.mul, q.off);
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < V; ++j) out[j] = ST::dec(raw[j], q);
@@ -120,7 +136,7 @@ __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typen
 
 template <class ST, int V>
 __device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typename ST::S (&raw)[V],
-                                           const QScale &q, bool &bad) {
+                                           const QScale &q, unsigned int &acc) {
     if constexpr (ST::id == LBM_STORE_F16 && V % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
@@ -135,9 +151,18 @@ __device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typena
             raw[j] = __low2bfloat16(h);
             raw[j + 1] = __high2bfloat16(h);
         }
+    } else if constexpr (ST::id == LBM_STORE_Q16 && V % 2 == 0) {
+        // the low halves of two encodings packed into one 32-bit word
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            const unsigned int w = __byte_perm(StoreQ16::enc_bits(in[j], q, acc),
+                                               StoreQ16::enc_bits(in[j + 1], q, acc), 0x5410);
+            raw[j] = static_cast<unsigned short>(w);
+            raw[j + 1] = static_cast<unsigned short>(w >> 16);
+        }
     } else {
 #pragma unroll
-        for (int j = 0; j < V; ++j) raw[j] = ST::enc(in[j], q, bad);
+        for (int j = 0; j < V; ++j) raw[j] = ST::enc(in[j], q, acc);
     }
 }
 
@@ -147,8 +172,8 @@ __device__ __forceinline__ typename ST::T decode(typename ST::S v, const QScale 
     return ST::dec(v, q);
 }
 template <class ST>
-__device__ __forceinline__ typename ST::S encode(typename ST::T x, const QScale &q, bool &bad) {
-    return ST::enc(x, q, bad);
+__device__ __forceinline__ typename ST::S encode(typename ST::T x, const QScale &q, unsigned int &acc) {
+    return ST::enc(x, q, acc);
 }
 
 // ------------------------------------------------------------------ moments

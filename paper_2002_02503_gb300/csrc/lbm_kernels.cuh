@@ -161,19 +161,19 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         for (int i = 0; i < Q; ++i) f[i][j] = g[i];
     }
 
-    bool bad = false;
+    unsigned int acc = 0u;
     if (active) {
         S *out = dst + (long long)(z * ny + y) * nx + x0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             S raw[V];
-            encode_vec<ST, V>(f[i], raw, qs, bad);
+            encode_vec<ST, V>(f[i], raw, qs, acc);
             store_vec<S, V>(out + (long long)i * P, raw);
         }
     }
     if constexpr (ST::id == LBM_STORE_Q16) {
         // one flag per warp that met a value outside the fixed-point range
-        if (__any_sync(kFull, bad) && lane == 0 && status) atomicOr(status, kStatusRange);
+        if (__any_sync(kFull, range_exceeded(acc)) && lane == 0 && status) atomicOr(status, kStatusRange);
     }
 }
 
@@ -285,7 +285,7 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
                             unsigned int *__restrict__ status) {
     using S = typename ST::S;
     using T = typename ST::T;
-    bool bad = false;
+    unsigned int acc = 0u;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
          k += (long long)gridDim.x * blockDim.x) {
         const long long cell = c0 + k;
@@ -303,10 +303,12 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
             const int xs = wrapn(x - vel<LT>(i, 0), nx);
             const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
             const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
-            dst[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs] = encode<ST>(T(g[i]), qs, bad);
+            dst[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs] = encode<ST>(T(g[i]), qs, acc);
         }
     }
-    if (bad && status) atomicOr(status, kStatusRange);
+    if constexpr (ST::id == LBM_STORE_Q16) {
+        if (range_exceeded(acc) && status) atomicOr(status, kStatusRange);
+    }
 }
 
 template <class LT, int K, class ST>

@@ -219,9 +219,9 @@ __global__ void __launch_bounds__(kStagedThreads) step_staged_kernel(const typen
             for (int i = 0; i < Q; ++i) g[i] = decode<ST>(base[size_t(i) * R * nx + xs[vel<LT>(i, 0) + M]], QScale{});
             collide<LT, K, T>(g, relax, rho0);
             S *out = dst + (long long)row * nx + x;
-            bool bad = false;  // floating storage only: no range to leave
+            unsigned int acc = 0u;  // floating storage only: no range to leave
 #pragma unroll
-            for (int i = 0; i < Q; ++i) out[(long long)i * P] = encode<ST>(g[i], QScale{}, bad);
+            for (int i = 0; i < Q; ++i) out[(long long)i * P] = encode<ST>(g[i], QScale{}, acc);
         }
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[s])) : "memory");

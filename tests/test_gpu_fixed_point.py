@@ -1,6 +1,6 @@
 """The 16-bit fixed-point storage form (LBM_STORE_Q16) through the C-ABI.
 
-h = q 2^e with q in [-32767, 32767] stored as q + 2^15 and the range R = 2^(e + 15) a power
+h = q 2^e with q in [-32768, 32767] stored as q + 2^15 and the range R = 2^(e + 15) a power
 of two.  Checked here: the decoder is exact (integer codes in, FP64 values out, compared
 bit for bit), the encoder rounds to nearest with ties to even, a value beyond the range is
 reported as LBM_ERR_RANGE (a state whose next step leaves the range, as the oracle's own step
@@ -41,7 +41,8 @@ def test_decode_is_exact(R):
     name, dims = "D3Q19", (20, 9, 7)
     info = lbm.lbm_lattice_info(name)
     C = int(np.prod(dims))
-    g = np.random.default_rng(31).integers(1, 65536, size=(info["Q"], C), dtype=np.uint16)
+    g = np.random.default_rng(31).integers(0, 65536, size=(info["Q"], C), dtype=np.uint16)
+    g[:, 0], g[:, 1] = 0, 65535  # both ends of the code range
     s = lbm.Solver(name, dims, 0.6, 3, "q16", rho0=1.0, storage_range=R)
     lbm.lbm_set_distributions(s.handle, g, 0)
     f = s.f()
@@ -63,6 +64,7 @@ def test_encode_rounds_to_nearest_even():
     rg = np.random.default_rng(32)
     k = rg.integers(-30000, 30000, size=C).astype(np.float64)
     frac = rg.choice([0.0, 0.25, 0.5, 0.75, -0.5], size=C)
+    k[:2], frac[:2] = (-32768.0, 32767.0), 0.0  # both ends of the range are representable
     q = k + frac
     rho = 1.0 + q * step
     u = np.zeros((3, C))
@@ -135,6 +137,16 @@ def test_set_fields_beyond_the_range_is_reported():
     assert e.value.status == lbm.LBM_ERR_RANGE
     lbm.lbm_set_storage_range(s.handle, 0.25)
     s.set_fields(rho, u)  # fits now
+    s.close()
+    # the range is [-R, R): at u = 0, h = rho - rho0 for every velocity
+    s = lbm.Solver("D3Q19", dims, 0.6, 3, "q16", storage_range=0.25)
+    C = 16 ** 3
+    zero = np.zeros((3, C))
+    s.set_fields(np.full(C, 1.0 - 0.25), zero)
+    s.set_fields(np.full(C, 1.0 + 0.25 * (1 - 2.0 ** -15)), zero)
+    with pytest.raises(lbm.LbmError) as e:
+        s.set_fields(np.full(C, 1.0 + 0.25), zero)
+    assert e.value.status == lbm.LBM_ERR_RANGE
     s.close()
 
 
