@@ -121,12 +121,17 @@ __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typen
             out[j + 1] = f.y;
         }
     } else if constexpr (ST::id == LBM_STORE_Q16 && V % 2 == 0) {
-        // two codes per 32-bit word: one byte permute builds each float's bits
+        // two codes per 32-bit word: one byte permute builds each float's bits, one paired
+        // FMA scales both
+        const float2 mul = make_float2(q.mul, q.mul), off = make_float2(q.off, q.off);
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
             const unsigned int w = unsigned(raw[j]) | (unsigned(raw[j + 1]) << 16);
-            out[j] = fmaf(__uint_as_float(__byte_perm(w, StoreQ16::kExp, 0x7610)), q.mul, q.off);
-            out[j + 1] = fmaf(__uint_as_float(__byte_perm(w, StoreQ16::kExp, 0x7632)), q.mul, q.off);
+            const float2 v = make_float2(__uint_as_float(__byte_perm(w, StoreQ16::kExp, 0x7610)),
+                                         __uint_as_float(__byte_perm(w, StoreQ16::kExp, 0x7632)));
+            const float2 h = __ffma2_rn(v, mul, off);
+            out[j] = h.x;
+            out[j + 1] = h.y;
         }
     } else {
 #pragma unroll
@@ -152,11 +157,14 @@ __device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typena
             raw[j + 1] = __high2bfloat16(h);
         }
     } else if constexpr (ST::id == LBM_STORE_Q16 && V % 2 == 0) {
-        // the low halves of two encodings packed into one 32-bit word
+        // one paired FMA encodes two values; the low halves of both encodings pack into one word
+        const float2 inv = make_float2(q.inv, q.inv), bias = make_float2(StoreQ16::kBias, StoreQ16::kBias);
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
-            const unsigned int w = __byte_perm(StoreQ16::enc_bits(in[j], q, acc),
-                                               StoreQ16::enc_bits(in[j + 1], q, acc), 0x5410);
+            const float2 v = __ffma2_rn(make_float2(in[j], in[j + 1]), inv, bias);
+            const unsigned int b0 = __float_as_uint(v.x), b1 = __float_as_uint(v.y);
+            acc |= (b0 ^ StoreQ16::kExp) | (b1 ^ StoreQ16::kExp);
+            const unsigned int w = __byte_perm(b0, b1, 0x5410);
             raw[j] = static_cast<unsigned short>(w);
             raw[j + 1] = static_cast<unsigned short>(w >> 16);
         }
@@ -175,6 +183,48 @@ template <class ST>
 __device__ __forceinline__ typename ST::S encode(typename ST::T x, const QScale &q, unsigned int &acc) {
     return ST::enc(x, q, acc);
 }
+
+// ------------------------------------------------------------------ paired FP32
+// F2 holds one FP32 value of each of two cells, and its arithmetic maps to the paired
+// FP32 instructions of sm_100+ (two lanes per instruction, each rounded as the scalar
+// operation).  The collision below is a template over its arithmetic type, so with
+// T = F2 one pass of its code updates two cells.  A product stays unevaluated (F2P)
+// until it meets an addition, so a*b + c issues one paired fused multiply-add, as the
+// compiler's contraction does for scalars; a product used otherwise is rounded once.
+struct F2P;
+struct F2 {
+    float2 v;
+    F2() = default;
+    __device__ __forceinline__ F2(float2 x) : v(x) {}
+    __device__ __forceinline__ explicit F2(double c) : v(make_float2(float(c), float(c))) {}
+    __device__ __forceinline__ F2(const F2P &p);
+};
+struct F2P {
+    float2 a, b;
+};
+__device__ __forceinline__ float2 neg2(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ F2::F2(const F2P &p) : v(__fmul2_rn(p.a, p.b)) {}
+__device__ __forceinline__ F2P operator*(F2 x, F2 y) { return {x.v, y.v}; }
+__device__ __forceinline__ F2P operator*(const F2P &p, F2 y) { return {F2(p).v, y.v}; }
+__device__ __forceinline__ F2P operator*(F2 x, const F2P &p) { return {x.v, F2(p).v}; }
+__device__ __forceinline__ F2P operator*(const F2P &p, const F2P &q) { return {F2(p).v, F2(q).v}; }
+__device__ __forceinline__ F2 operator-(F2 x) { return F2(neg2(x.v)); }
+__device__ __forceinline__ F2P operator-(const F2P &p) { return {neg2(p.a), p.b}; }
+__device__ __forceinline__ F2 operator+(F2 x, F2 y) { return F2(__fadd2_rn(x.v, y.v)); }
+__device__ __forceinline__ F2 operator-(F2 x, F2 y) { return F2(__fadd2_rn(x.v, neg2(y.v))); }
+__device__ __forceinline__ F2 operator+(const F2P &p, F2 c) { return F2(__ffma2_rn(p.a, p.b, c.v)); }
+__device__ __forceinline__ F2 operator+(F2 c, const F2P &p) { return F2(__ffma2_rn(p.a, p.b, c.v)); }
+__device__ __forceinline__ F2 operator-(const F2P &p, F2 c) { return F2(__ffma2_rn(p.a, p.b, neg2(c.v))); }
+__device__ __forceinline__ F2 operator-(F2 c, const F2P &p) { return F2(__ffma2_rn(neg2(p.a), p.b, c.v)); }
+__device__ __forceinline__ F2 operator+(const F2P &p, const F2P &q) { return F2(__ffma2_rn(p.a, p.b, F2(q).v)); }
+__device__ __forceinline__ F2 operator-(const F2P &p, const F2P &q) {
+    return F2(__ffma2_rn(p.a, p.b, neg2(F2(q).v)));
+}
+__device__ __forceinline__ F2 operator/(F2 x, F2 y) { return F2(make_float2(x.v.x / y.v.x, x.v.y / y.v.y)); }
+__device__ __forceinline__ F2 &operator+=(F2 &x, F2 y) { return x = x + y; }
+__device__ __forceinline__ F2 &operator-=(F2 &x, F2 y) { return x = x - y; }
+__device__ __forceinline__ F2 &operator+=(F2 &x, const F2P &p) { return x = x + p; }
+__device__ __forceinline__ F2 &operator-=(F2 &x, const F2P &p) { return x = x - p; }
 
 // ------------------------------------------------------------------ moments
 // Accumulators start at -0.0: x + (-0.0) == x for every x, so the compiler drops

