@@ -251,8 +251,18 @@ lbm_status lbm_pool_sync(lbm_pool *p);
 /* Free arena bytes, resident requests, and requests done but not collected. */
 lbm_status lbm_pool_stats(const lbm_pool *p, size_t *free_bytes, int *resident, int *done);
 
-/* Autotuner for the batch kernel: times each built block size on the current
- * resident set (state unchanged) and keeps the fastest.  best_us: time per step. */
+/* Kernel configuration of the batched step.  cells_per_thread: the most cells a thread
+ * updates, 1 or 2 (the default); a request whose nx is odd always runs 1, so a request's
+ * arithmetic depends on this setting and its own dims only, never on the other residents.
+ * Two cells per thread run the collision on the paired FP32 instructions.  block_threads:
+ * 128 or 256 (the default).  Zero keeps the current value.  Waits for the launched chunks.
+ * LBM_ERR_UNSUPPORTED for other values. */
+lbm_status lbm_pool_set_kernel(lbm_pool *p, int cells_per_thread, int block_threads);
+lbm_status lbm_pool_get_kernel(const lbm_pool *p, int *cells_per_thread, int *block_threads);
+
+/* Autotuner for the batch kernel: times each built configuration (cells per thread 1 or 2
+ * x block 128 or 256) on the current resident set (state unchanged) and keeps the fastest.
+ * best_us: time per step. */
 lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us);
 
 /* Release the pool (not the arena).  Synchronises both streams. */

@@ -105,6 +105,7 @@ struct lbm_pool {
     cudaStream_t compute, io, capture;
     bool own_io;
     int block, grid;
+    int cpt;  // most cells per thread a slot may run (1 or 2; a slot with odd nx runs 1)
     // double-buffered slot tables
     BatchSlot *d_table[2];
     int *d_header[2];
@@ -147,7 +148,7 @@ lbm_status get_graph(lbm_pool *p, long long chunk, int b, cudaGraphExec_t *out) 
     if (e != cudaSuccess) return set_cuda_error(e, "pool: begin capture");
     cudaError_t le = cudaSuccess;
     for (long long s = 0; s < chunk && le == cudaSuccess; ++s)
-        le = p->ks->batch(p->d_table[b], p->d_header[b], int(s), p->grid, p->block, p->capture);
+        le = p->ks->batch(p->d_table[b], p->d_header[b], int(s), p->grid, p->block, p->cpt, p->capture);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(p->capture, &g);
     if (le != cudaSuccess) {
@@ -169,14 +170,15 @@ void drop_graphs(lbm_pool *p) {
     p->graphs.clear();
 }
 
-lbm_status set_geometry(lbm_pool *p, int block) {
-    int occ = p->ks->batch_occupancy(block);
+lbm_status set_geometry(lbm_pool *p, int block, int cpt) {
+    int occ = p->ks->batch_occupancy(block, cpt);
     if (occ <= 0) return set_error(LBM_ERR_CUDA, "pool: batch kernel occupancy query failed");
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return set_cuda_error(e, "pool: device query");
     p->block = block;
+    p->cpt = cpt;
     p->grid = occ * sms;
     drop_graphs(p);
     return LBM_OK;
@@ -195,15 +197,16 @@ int build_table(lbm_pool *p, int b, int *units_total) {
         s.nx = r.nx;
         s.ny = r.ny;
         s.nz = r.nz;
-        s.ncx = r.nx;  // V = 1
+        const int V = (p->cpt == 2 && r.nx % 2 == 0) ? 2 : 1;
+        s.ncx = r.nx / V;
         s.P = r.C;
         s.relax = r.relax;
         s.rho0 = r.rho0;
         s.parity = r.parity;
         s.steps_left = int(std::min<int64_t>(left, 1 << 30));
         s.unit0 = units;
-        s.units = int((r.C + p->block - 1) / p->block);
-        fastdiv_init(unsigned(r.nx), &s.mx, &s.sx);
+        s.units = int((r.C / V + p->block - 1) / p->block);
+        fastdiv_init(unsigned(s.ncx), &s.mx, &s.sx);
         fastdiv_init(unsigned(r.ny), &s.my, &s.sy);
         units += s.units;
         ++n;
@@ -332,7 +335,7 @@ lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, 
         lbm_pool_destroy(p);
         return set_cuda_error(e, "pool: host setup");
     }
-    lbm_status rs = set_geometry(p, 256);
+    lbm_status rs = set_geometry(p, 256, 2);
     if (rs != LBM_OK) {
         lbm_pool_destroy(p);
         return rs;
@@ -548,19 +551,20 @@ lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int best_block = p->block;
-    for (int block : {128, 256}) {
-        rs = set_geometry(p, block);
+    int best_block = p->block, best_cpt = p->cpt;
+    for (int cfg = 0; cfg < 4; ++cfg) {
+        const int cpt = 1 + (cfg >> 1), block = (cfg & 1) ? 256 : 128;
+        rs = set_geometry(p, block, cpt);
         if (rs != LBM_OK) break;
-        build_table(p, b, &units);  // units depend on the block size
+        build_table(p, b, &units);  // units depend on the block size and the cells per thread
         e = cudaMemcpyAsync(p->d_table[b], p->h_table[b], sizeof(BatchSlot) * n, cudaMemcpyHostToDevice, p->compute);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], 2 * sizeof(int), cudaMemcpyHostToDevice, p->compute);
         for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grid, p->block, p->compute);
+            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grid, p->block, p->cpt, p->compute);
         if (e == cudaSuccess) e = cudaEventRecord(e0, p->compute);
         for (int it = 0; it < iters && e == cudaSuccess; ++it)
-            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grid, p->block, p->compute);
+            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grid, p->block, p->cpt, p->compute);
         if (e == cudaSuccess) e = cudaEventRecord(e1, p->compute);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -572,14 +576,35 @@ lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us) {
         if (ms < best) {
             best = ms;
             best_block = block;
+            best_cpt = cpt;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rs != LBM_OK) return rs;
-    rs = set_geometry(p, best_block);
+    rs = set_geometry(p, best_block, best_cpt);
     if (rs != LBM_OK) return rs;
     if (best_us) *best_us = 1000.0 * best / iters;
+    return LBM_OK;
+}
+
+lbm_status lbm_pool_set_kernel(lbm_pool *p, int cells_per_thread, int block_threads) {
+    if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    std::lock_guard<std::mutex> lock(p->mu);
+    const int cpt = cells_per_thread == 0 ? p->cpt : cells_per_thread;
+    const int block = block_threads == 0 ? p->block : block_threads;
+    if (cpt != 1 && cpt != 2) return set_error(LBM_ERR_UNSUPPORTED, "pool: cells_per_thread must be 1 or 2");
+    if (block != 128 && block != 256) return set_error(LBM_ERR_UNSUPPORTED, "pool: block_threads must be 128 or 256");
+    // the launched chunks hold graphs built for the current geometry: let them finish first
+    lbm_status rs = ensure_completed(p, p->chunks, true);
+    if (rs != LBM_OK) return rs;
+    return set_geometry(p, block, cpt);
+}
+
+lbm_status lbm_pool_get_kernel(const lbm_pool *p, int *cells_per_thread, int *block_threads) {
+    if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    if (cells_per_thread) *cells_per_thread = p->cpt;
+    if (block_threads) *block_threads = p->block;
     return LBM_OK;
 }
 

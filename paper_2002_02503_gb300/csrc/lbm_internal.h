@@ -92,7 +92,7 @@ struct ReduceArgs {
 struct BatchSlot {
     void *buf[2];      // the two distribution buffers of this lattice
     int nx, ny, nz;
-    int ncx;           // nx / V
+    int ncx;           // nx / V, V = cells per thread of this slot (1 or 2)
     long long P;       // cells per velocity plane
     double relax;      // 1 - 1/tau
     double rho0;
@@ -100,7 +100,7 @@ struct BatchSlot {
     int steps_left;    // steps still to run at the start of the chunk
     int unit0;         // first work unit of this slot (table sorted by unit0)
     int units;         // work units of this slot
-    unsigned int mx, sx, my, sy;  // division by nx and ny as multiply-high + shift (fastdiv_init)
+    unsigned int mx, sx, my, sy;  // division by ncx and ny as multiply-high + shift (fastdiv_init)
 };
 
 // Division by a runtime constant d (1 <= d < 2^31) as q = (umulhi(n, m) + n) >> s for
@@ -116,7 +116,7 @@ inline void fastdiv_init(unsigned int d, unsigned int *m, unsigned int *s) {
 
 typedef cudaError_t (*step_fn)(const StepArgs &, int block_threads, cudaStream_t);
 typedef cudaError_t (*batch_fn)(const BatchSlot *slots, const int *header, int step_index, int grid, int block,
-                                cudaStream_t);
+                                int cells_per_thread, cudaStream_t);
 typedef cudaError_t (*init_fn)(const InitArgs &, cudaStream_t);
 typedef cudaError_t (*pull_fn)(const PullArgs &, cudaStream_t);
 typedef cudaError_t (*reduce_fn)(const ReduceArgs &, cudaStream_t);
@@ -130,8 +130,8 @@ struct KernelSet {
     pull_fn pull_f;
     reduce_fn conservation;  // nvals = 4
     reduce_fn mode;          // nvals = 2
-    batch_fn batch;          // persistent multi-lattice step (V = 1); null for fixed-point storage
-    int (*batch_occupancy)(int block);
+    batch_fn batch;          // persistent multi-lattice step (1 or at most 2 cells per thread); null for fixed point
+    int (*batch_occupancy)(int block, int cells_per_thread);
     step_fn bgk;             // BGK comparison operator, register pull with V = 1
     step_fn theta;           // filtered collision with the energy-flux term (K >= 3), V = 1
     bool (*staged_applies)(int nx);  // variant 1 needs nx * sizeof(storage) % 16 == 0 and a fitting tile

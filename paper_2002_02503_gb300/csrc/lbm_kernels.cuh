@@ -216,7 +216,10 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
 
 // ------------------------------------------------------------------ batched step
 // Persistent kernel over the work units of every slot in a table (one unit =
-// blockDim.x consecutive cells of one lattice, one cell per thread).  One launch
+// blockDim.x consecutive threads of one lattice).  A slot runs V = nx / ncx cells per
+// thread: 2 where the pool allows it and nx is even (the collision then runs on the
+// paired FP32 instructions), else 1; a CTA serves one unit, so the choice is uniform
+// across it and depends only on the slot, never on the other residents.  One launch
 // advances every slot with step_index < steps_left by one step; the slot's buffers
 // alternate with its parity.  The table lives in device memory, so a captured graph
 // of launches stays valid while the host rewrites the table between chunks.
@@ -224,7 +227,7 @@ __device__ __forceinline__ int fastdiv(int n, unsigned int m, unsigned int s) {
     return int((__umulhi((unsigned int)n, m) + (unsigned int)n) >> s);
 }
 
-template <class LT, int K, class ST, int V>
+template <class LT, int K, class ST, int VMAX>
 __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__restrict__ slots,
                                                          const int *__restrict__ header, int step_index) {
     const int total_units = header[0];
@@ -249,30 +252,37 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__rest
         int t = (unit - sl.unit0) * blockDim.x + threadIdx.x;
         const bool active = t < total;
         if (!active) t = total - 1;
-        const int row = fastdiv(t, sl.mx, sl.sx);  // ncx = nx for V = 1
+        const int row = fastdiv(t, sl.mx, sl.sx);  // t / ncx
         const int chunk = t - row * sl.ncx;
         const int z = fastdiv(row, sl.my, sl.sy);
         const int y = row - z * sl.ny;
-        pull_collide_store<LT, K, ST, V>(static_cast<const typename ST::S *>(sl.buf[cur]),
-                                         static_cast<typename ST::S *>(sl.buf[cur ^ 1]), sl.nx, sl.ny, sl.nz, sl.ncx,
-                                         sl.P, y, z, chunk, active, typename ST::T(sl.relax),
-                                         typename ST::T(sl.rho0), typename ST::T(0), QScale{}, nullptr);
+        const auto *src = static_cast<const typename ST::S *>(sl.buf[cur]);
+        auto *dst = static_cast<typename ST::S *>(sl.buf[cur ^ 1]);
+        const typename ST::T relax(sl.relax), rho0(sl.rho0), kq(0);
+        if (VMAX == 2 && sl.ncx != sl.nx)
+            pull_collide_store<LT, K, ST, VMAX>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk, active, relax,
+                                                rho0, kq, QScale{}, nullptr);
+        else
+            pull_collide_store<LT, K, ST, 1>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk, active, relax,
+                                             rho0, kq, QScale{}, nullptr);
     }
 }
 
 template <class LT, int K, class ST>
-cudaError_t launch_batch(const BatchSlot *slots, const int *header, int step_index, int grid, int block,
+cudaError_t launch_batch(const BatchSlot *slots, const int *header, int step_index, int grid, int block, int cpt,
                          cudaStream_t stream) {
-    batch_step_kernel<LT, K, ST, 1><<<grid, block, 0, stream>>>(slots, header, step_index);
+    if (cpt == 2) batch_step_kernel<LT, K, ST, 2><<<grid, block, 0, stream>>>(slots, header, step_index);
+    else batch_step_kernel<LT, K, ST, 1><<<grid, block, 0, stream>>>(slots, header, step_index);
     return cudaGetLastError();
 }
 
 template <class LT, int K, class ST>
-int batch_occupancy(int block) {
+int batch_occupancy(int block, int cpt) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 1>, block, 0) != cudaSuccess)
-        return 0;
-    return n;
+    cudaError_t e = cpt == 2
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 2>, block, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 1>, block, 0);
+    return e == cudaSuccess ? n : 0;
 }
 
 template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false>
@@ -579,7 +589,7 @@ constexpr batch_fn batch_if_built() {
 }
 
 template <class LT, int K, class ST>
-constexpr int (*batch_occupancy_if_built())(int) {
+constexpr int (*batch_occupancy_if_built())(int, int) {
     if constexpr (ST::id == LBM_STORE_Q16) return nullptr;
     else return &batch_occupancy<LT, K, ST>;
 }

@@ -58,6 +58,8 @@ SIGNATURES = [
     ("lbm_pool_result", _c.c_int, [_P, _c.c_int64, _P, _P, _c.c_int]),
     ("lbm_pool_sync", _c.c_int, [_P]),
     ("lbm_pool_stats", _c.c_int, [_P, _c.POINTER(_c.c_size_t), _IP, _IP]),
+    ("lbm_pool_set_kernel", _c.c_int, [_P, _c.c_int, _c.c_int]),
+    ("lbm_pool_get_kernel", _c.c_int, [_P, _IP, _IP]),
     ("lbm_pool_autotune", _c.c_int, [_P, _c.c_int, _DP]),
     ("lbm_pool_destroy", _c.c_int, [_P]),
     ("lbm_status_string", _c.c_char_p, [_c.c_int]),
@@ -384,6 +386,16 @@ def lbm_pool_stats(h):
     res, dn = ctypes.c_int(), ctypes.c_int()
     _check(lib().lbm_pool_stats(h, ctypes.byref(fb), ctypes.byref(res), ctypes.byref(dn)))
     return {"free_bytes": fb.value, "resident": res.value, "done": dn.value}
+
+
+def lbm_pool_set_kernel(h, cells_per_thread=0, block_threads=0):
+    _check(lib().lbm_pool_set_kernel(h, int(cells_per_thread), int(block_threads)))
+
+
+def lbm_pool_get_kernel(h):
+    cpt, block = ctypes.c_int(), ctypes.c_int()
+    _check(lib().lbm_pool_get_kernel(h, ctypes.byref(cpt), ctypes.byref(block)))
+    return cpt.value, block.value
 
 
 def lbm_pool_autotune(h, iters=5):

@@ -18,9 +18,12 @@ def _tg(side, u0):
     return fields.taylor_green_3d((side,) * 3, u0, 1.0 / 3.0)
 
 
-def _run_pool(reqs, chunk=7, arena=2 << 30, submit_after=None):
-    """reqs: list of (side, tau, u0, steps).  submit_after[k] = chunk index at which request k joins."""
+def _run_pool(reqs, chunk=7, arena=2 << 30, submit_after=None, kernel=None):
+    """reqs: list of (side, tau, u0, steps).  submit_after[k] = chunk index at which request k joins.
+    kernel: (cells per thread, block) of the batched step, or None for the default."""
     pool = lbm.Pool("D3Q19", 3, "f32", arena, 64)
+    if kernel is not None:
+        lbm.lbm_pool_set_kernel(pool.handle, *kernel)
     submit_after = submit_after or [0] * len(reqs)
     ids = {}
     out = {}
@@ -109,8 +112,9 @@ def test_admission_by_memory_and_zero_steps():
 
 
 def test_pool_autotune_keeps_results():
+    """Tuning launches write only the idle buffers: after autotuning, the results equal bit for bit
+    those of a pool set to the configuration the tuner chose."""
     reqs = [(24, 0.7, 0.05, 20), (31, 0.6, 0.04, 20)]
-    base = _run_pool(reqs)
     pool = lbm.Pool("D3Q19", 3, "f32", 1 << 30, 64)
     ids = []
     for side, tau, u0, steps in reqs:
@@ -118,6 +122,9 @@ def test_pool_autotune_keeps_results():
         ids.append(pool.submit((side,) * 3, tau, rho, u, steps))
     us = lbm.lbm_pool_autotune(pool.handle, 2)
     assert us > 0
+    chosen = lbm.lbm_pool_get_kernel(pool.handle)
+    assert chosen[0] in (1, 2) and chosen[1] in (128, 256)
+    base = _run_pool(reqs, kernel=chosen)
     while not all(pool.poll(i)[0] for i in ids):
         pool.advance(7)
         pool.sync()
@@ -169,4 +176,27 @@ def test_pool_other_classes_match_single_lattice(lattice, K, storage, sides):
         s.close()
         assert rel_f(r, rs) < tol
         assert rel_u(u, us) < tol
+    pool.close()
+
+
+def test_cells_per_thread_of_the_batched_step():
+    """Two cells per thread (even nx only; odd nx keeps one) against one cell per thread: the same
+    fields within the FP32 tolerance, and a request's result does not depend on the residents."""
+    reqs = [(24, 0.7, 0.05, 30), (25, 0.6, 0.04, 30), (40, 0.55, 0.06, 17)]
+    one = _run_pool(reqs, kernel=(1, 256))
+    two = _run_pool(reqs, kernel=(2, 128))
+    for k, (side, tau, u0, steps) in enumerate(reqs):
+        assert rel_f(two[k][0], one[k][0]) < TOL_F32
+        assert rel_u(two[k][1], one[k][1]) < TOL_F32
+        r, u = _single(side, tau, u0, steps)
+        assert rel_u(two[k][1], u) < TOL_F32
+    np.testing.assert_array_equal(two[1][1], one[1][1])  # odd nx: one cell per thread either way
+    alone = _run_pool([reqs[0]], kernel=(2, 128))[0]
+    np.testing.assert_array_equal(alone[1], two[0][1])
+    pool = lbm.Pool("D3Q19", 3, "f32", 1 << 24, 4)
+    for bad in [(3, 0), (0, 96)]:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_pool_set_kernel(pool.handle, *bad)
+        assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+    assert lbm.lbm_pool_get_kernel(pool.handle) == (2, 256)
     pool.close()
