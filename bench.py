@@ -430,8 +430,15 @@ def run_ours(a):
         if not a.no_extras:
             with torch.cuda.stream(stream):
                 extras["per_lattice"] = [measure_lattice(*cfg, a.extra_steps, stream) for cfg in PER_LATTICE]
+            from paper_2002_02503_gb300 import serve
+
+            peak, _ = measured_peak()
+            extras["batched"] = []
+            for storage in ("f32", "f16"):
+                r = serve.batched_rate(40, a.extra_steps, storage)
+                r["frac_of_measured_hbm"] = r["MLUPS"] * 1e6 * r["bytes_per_update"] / 1e9 / peak
+                extras["batched"].append(r)
             if a.serve > 0:
-                from paper_2002_02503_gb300 import serve
 
                 trace = serve.make_trace(a.serve, rate=a.serve_rate)
                 pool_stats, _ = serve.serve_pool(trace)

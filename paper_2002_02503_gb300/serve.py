@@ -155,3 +155,46 @@ def serve_plain(trace, K=3, storage="f32", keep=None):
             results[r["i"]] = (ro, uo)
     t_total = time.perf_counter() - t0
     return _summary(lat, t_total, cells), results
+
+
+def batched_rate(n=40, steps=200, storage="f32", K=3, chunk=50, salt=5, autotune=True, kernel=None):
+    """Throughput of the batched step alone: n resident D3Q19 Taylor-Green lattices drawn like
+    the trace (sides log-uniform 32-128, tau, u0), every one with more steps left than are run,
+    advanced `steps` steps in chunks of `chunk`; timed with CUDA events on the pool's compute
+    stream after one untimed chunk (and the autotuner, unless a kernel (cells per thread,
+    block) is given).  Returns MLUPS, bytes per update and the kernel configuration."""
+    import torch
+
+    trace = make_trace(n, salt=salt)
+    cells = sum(r["side"] ** 3 for r in trace)
+    Q = lbm.lbm_lattice_info("D3Q19")["Q"]
+    arena = sum(lbm.lbm_pool_request_bytes("D3Q19", (r["side"],) * 3, storage) for r in trace) + (64 << 20)
+    pool = lbm.Pool("D3Q19", K, storage, arena, max(n, 1))
+    try:
+        for r in trace:
+            rho, u = request_fields(r)
+            if pool.submit((r["side"],) * 3, r["tau"], rho, u, 10 * (steps + chunk)) is None:
+                raise RuntimeError("pool refused a request of the batched workload")
+        if kernel is not None:
+            lbm.lbm_pool_set_kernel(pool.handle, *kernel)
+        pool.advance(chunk)
+        if autotune and kernel is None:
+            lbm.lbm_pool_autotune(pool.handle, 5)
+        pool.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(pool.compute)
+        done = 0
+        while done < steps:
+            m = min(chunk, steps - done)
+            pool.advance(m)
+            done += m
+        e1.record(pool.compute)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        cpt, block = lbm.lbm_pool_get_kernel(pool.handle)
+    finally:
+        pool.close()
+    return {"workload": "%d resident D3Q19 lattices (sides log-uniform 32-128, %d cells), %s, K=%d, %d steps"
+                        % (n, cells, storage, K, steps),
+            "MLUPS": cells * steps / (ms / 1e3) / 1e6, "bytes_per_update": 2 * Q * lbm.STORAGE_BYTES[storage],
+            "ms_per_step": ms / steps, "kernel": {"cells_per_thread": cpt, "block": block}}
