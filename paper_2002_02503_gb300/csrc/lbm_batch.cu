@@ -197,15 +197,17 @@ int build_table(lbm_pool *p, int b, int *units_total) {
         s.nx = r.nx;
         s.ny = r.ny;
         s.nz = r.nz;
-        const int V = (p->cpt == 2 && r.nx % 2 == 0) ? 2 : 1;
-        s.ncx = r.nx / V;
+        // two cells per thread: x-neighbours (row vectors) for even nx, flat neighbours otherwise
+        s.mode = p->cpt == 1 ? 0 : (r.nx % 2 == 0 ? 1 : 2);
+        s.ncx = s.mode == 1 ? r.nx / 2 : r.nx;
+        s.threads = int(s.mode == 0 ? r.C : (r.C + 1) / 2);
         s.P = r.C;
         s.relax = r.relax;
         s.rho0 = r.rho0;
         s.parity = r.parity;
         s.steps_left = int(std::min<int64_t>(left, 1 << 30));
         s.unit0 = units;
-        s.units = int((r.C / V + p->block - 1) / p->block);
+        s.units = int((s.threads + p->block - 1) / p->block);
         fastdiv_init(unsigned(s.ncx), &s.mx, &s.sx);
         fastdiv_init(unsigned(r.ny), &s.my, &s.sy);
         units += s.units;

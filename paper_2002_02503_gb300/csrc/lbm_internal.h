@@ -92,7 +92,10 @@ struct ReduceArgs {
 struct BatchSlot {
     void *buf[2];      // the two distribution buffers of this lattice
     int nx, ny, nz;
-    int ncx;           // nx / V, V = cells per thread of this slot (1 or 2)
+    int mode;          // 0: one cell per thread; 1: two x-neighbours per thread (row vectors, even nx);
+                       // 2: two consecutive cells of the flat index per thread (any nx)
+    int ncx;           // nx / V in modes 0 and 1 (V = 1, 2); nx in mode 2
+    int threads;       // threads the slot's step needs (C, C / 2, ceil(C / 2))
     long long P;       // cells per velocity plane
     double relax;      // 1 - 1/tau
     double rho0;
@@ -100,7 +103,7 @@ struct BatchSlot {
     int steps_left;    // steps still to run at the start of the chunk
     int unit0;         // first work unit of this slot (table sorted by unit0)
     int units;         // work units of this slot
-    unsigned int mx, sx, my, sy;  // division by ncx and ny as multiply-high + shift (fastdiv_init)
+    unsigned int mx, sx, my, sy;  // division by ncx (modes 0, 1) or nx (mode 2) and by ny (fastdiv_init)
 };
 
 // Division by a runtime constant d (1 <= d < 2^31) as q = (umulhi(n, m) + n) >> s for

@@ -180,8 +180,9 @@ def test_pool_other_classes_match_single_lattice(lattice, K, storage, sides):
 
 
 def test_cells_per_thread_of_the_batched_step():
-    """Two cells per thread (even nx only; odd nx keeps one) against one cell per thread: the same
-    fields within the FP32 tolerance, and a request's result does not depend on the residents."""
+    """Two cells per thread (x-neighbours for even nx, flat-index neighbours for odd nx) against one
+    cell per thread: the same fields within the FP32 tolerance, and a request's result does not
+    depend on the residents."""
     reqs = [(24, 0.7, 0.05, 30), (25, 0.6, 0.04, 30), (40, 0.55, 0.06, 17)]
     one = _run_pool(reqs, kernel=(1, 256))
     two = _run_pool(reqs, kernel=(2, 128))
@@ -190,9 +191,9 @@ def test_cells_per_thread_of_the_batched_step():
         assert rel_u(two[k][1], one[k][1]) < TOL_F32
         r, u = _single(side, tau, u0, steps)
         assert rel_u(two[k][1], u) < TOL_F32
-    np.testing.assert_array_equal(two[1][1], one[1][1])  # odd nx: one cell per thread either way
-    alone = _run_pool([reqs[0]], kernel=(2, 128))[0]
-    np.testing.assert_array_equal(alone[1], two[0][1])
+    for k in (0, 1):  # an even and an odd nx, alone against the mix
+        alone = _run_pool([reqs[k]], kernel=(2, 128))[0]
+        np.testing.assert_array_equal(alone[1], two[k][1])
     pool = lbm.Pool("D3Q19", 3, "f32", 1 << 24, 4)
     for bad in [(3, 0), (0, 96)]:
         with pytest.raises(lbm.LbmError) as e:
