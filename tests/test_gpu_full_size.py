@@ -1,0 +1,104 @@
+"""Parity at the full sizes of the benchmark and experiment configurations, in the launch
+configuration bench.py times (the autotuner's choice), against the FP64 oracle on sampled cells.
+
+One cell after n steps depends only on the cells within n max|c| of it, so the oracle computes
+it exactly on a periodic box of side 2 n max|c| + 1 centred on the cell, initialised from the
+same analytic fields: no wrap of the box reaches the centre within n steps.  The GPU runs the
+whole lattice; its pre-collision f_i(x, n) at the sampled cells (and at cells on the lattice's
+periodic faces and corners) must match the box's centre."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_02503_gb300 import fields, lbm
+
+from _lbmtest import TOL_F32, TOL_U16, perm_lib_to_oracle
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    lbm.lib()
+    yield
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def _samples(dims, n=20, seed=0):
+    g = np.random.default_rng(seed)
+    pts = [tuple(int(g.integers(0, d)) for d in dims) for _ in range(n)]
+    nx, ny, nz = dims
+    pts += [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (0, ny - 1, nz // 2), (nx - 1, 0, 0)]
+    return pts
+
+
+def _box(a, dims, x, y, z, R):
+    """Periodic box of side 2R + 1 of the [..., C] field a, centred on (x, y, z); flattened x fastest."""
+    nx, ny, nz = dims
+    a = a.reshape(a.shape[:-1] + (nz, ny, nx))
+    ix = (x + np.arange(-R, R + 1)) % nx
+    iy = (y + np.arange(-R, R + 1)) % ny
+    iz = (z + np.arange(-R, R + 1)) % nz
+    b = a[..., iz[:, None, None], iy[None, :, None], ix[None, None, :]]
+    return b.reshape(a.shape[:-3] + (-1,))
+
+
+def _check(name, K, tau, dims, rho, u, storage, tol, storage_range=None):
+    import torch
+
+    info = lbm.lbm_lattice_info(name)
+    Q, C = info["Q"], int(np.prod(dims))
+    s = lbm.Solver(name, dims, tau, K, storage, storage_range=storage_range)
+    s.set_fields(rho, u)
+    lbm.lbm_autotune(s.handle, 3)  # the benchmark's launch configuration
+    s.step(STEPS)
+    f = torch.empty((Q, C), dtype=torch.float64, device="cuda")
+    lbm.lbm_get_f(s.handle, f)
+    s.close()
+    pts = _samples(dims)
+    nx, ny = dims[0], dims[1]
+    idx = torch.tensor([x + nx * (y + ny * z) for x, y, z in pts], device="cuda")
+    got = f[:, idx].cpu().numpy()
+    del f
+    torch.cuda.empty_cache()
+    R = STEPS * info["c"].max()
+    side = 2 * R + 1
+    perm = perm_lib_to_oracle(name)
+    worst = 0.0
+    for k, (x, y, z) in enumerate(pts):
+        rb, ub = _box(rho, dims, x, y, z, R), _box(u, dims, x, y, z, R)
+        fb = oracle.run(name, K, tau, (side,) * 3, oracle.init_eq(name, K, (side,) * 3, rb, ub), STEPS)
+        centre = R + side * (R + side * R)
+        want = fb[perm, centre]
+        worst = max(worst, float(np.max(np.abs(got[:, k] - want) / np.abs(want))))
+    print("%s %s K=%d %s: max rel f error over %d cells after %d steps %.3e" % (
+        name, "x".join(map(str, dims)), K, storage, len(pts), STEPS, worst))
+    assert worst < tol
+
+
+def test_d3q19_256_taylor_green_bench_config():
+    dims = (256, 256, 256)
+    rho, u = fields.taylor_green_3d(dims, 0.05, 1.0 / 3.0)
+    _check("D3Q19", 2, 0.55, dims, rho, u, "f32", TOL_F32)
+
+
+@pytest.mark.parametrize("name,K", [("D3Q27", 3), ("D3Q39", 4)])
+def test_192_shear_wave_on_background_flow(name, K):
+    """The Galilean-invariance configuration at its highest background speed, U_x = 0.2."""
+    dims = (192, 192, 192)
+    rho, u = fields.shear_wave(dims, 0.01, 3, 1, 0, background=(0.2, 0.0, 0.0))
+    _check(name, K, 0.6, dims, rho, u, "f32", TOL_F32)
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", TOL_F32), ("f16", TOL_U16), ("bf16", 5e-3), ("q16", TOL_U16)])
+def test_d3q19_512_taylor_green_storage_forms(storage, tol):
+    """The storage-precision configuration (512^3, tau = 0.52), every storage form."""
+    dims = (512, 512, 512)
+    rho, u = fields.taylor_green_3d(dims, 0.05, 1.0 / 3.0)
+    _check("D3Q19", 2, 0.52, dims, rho, u, storage, tol, storage_range=0.25 if storage == "q16" else None)
