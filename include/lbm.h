@@ -67,8 +67,9 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2, LBM_D3Q39 = 3, LBM_D3
  * stays below R/2 it rounds 4-16 times finer than FP16 at the same two bytes.  A
  * value outside [-R, R) (or not finite) is not stored faithfully: the step records it
  * and the next synchronising call returns LBM_ERR_RANGE.  Q16 runs on the register
- * pull step (variant 0, every cells_per_thread, BGK and the energy-flux term); pools,
- * the staged variant and lbm_conservation_noalloc reject it (LBM_ERR_UNSUPPORTED). */
+ * pull step (variant 0, every cells_per_thread, BGK and the energy-flux term) and in
+ * pools (lbm_pool_set_storage_range); the staged variant and lbm_conservation_noalloc
+ * reject it (LBM_ERR_UNSUPPORTED). */
 typedef enum {
     LBM_STORE_F32 = 0,
     LBM_STORE_F16 = 1,
@@ -216,7 +217,8 @@ lbm_status lbm_destroy(lbm_solver *s);
  * ------------------------------------------------------------------------ */
 typedef struct lbm_pool lbm_pool;
 
-/* Device bytes one request of these dims occupies in a pool's arena. */
+/* Device bytes one request of these dims occupies in a pool's arena: its two
+ * distribution buffers and a 256-byte status word. */
 size_t lbm_pool_request_bytes(lbm_lattice lattice, const int64_t dims[3], lbm_storage storage);
 
 /* arena: caller-owned device memory (256-byte aligned) that the pool carves
@@ -229,7 +231,8 @@ lbm_status lbm_pool_create(lbm_lattice lattice, int truncation_order, lbm_storag
 /* Admit one solve: f = f^eq(rho, u) (Eq. hermite) on a periodic lattice of dims,
  * to be advanced `steps` steps.  rho: double[C], u: double[D][C], in memory `mem`.
  * The inputs are consumed before the call returns.  LBM_ERR_BUSY when the arena
- * or the slot count has no room now (retry after results are collected). */
+ * or the slot count has no room now (retry after results are collected);
+ * LBM_ERR_RANGE when f^eq does not fit a fixed-point pool's range (not admitted). */
 lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, double rho0, const double *rho,
                            const double *u, lbm_mem mem, int64_t steps, int64_t *id);
 
@@ -242,7 +245,10 @@ lbm_status lbm_pool_advance(lbm_pool *p, int64_t chunk_steps, int *active);
 lbm_status lbm_pool_poll(lbm_pool *p, int64_t id, int *done, int64_t *steps_done);
 
 /* For a done request: rho and u after its steps (Eq. mme, pre-collision state),
- * then the request's memory returns to the arena.  Synchronises the io stream. */
+ * then the request's memory returns to the arena.  Synchronises the io stream.
+ * LBM_ERR_RANGE (fixed-point pools): a value of this request left the storage range
+ * during its steps; the outputs are not valid and the request is released all the same.
+ * Other requests are unaffected. */
 lbm_status lbm_pool_result(lbm_pool *p, int64_t id, double *rho, double *u, lbm_mem mem);
 
 /* Wait for every launched chunk. */
@@ -250,6 +256,12 @@ lbm_status lbm_pool_sync(lbm_pool *p);
 
 /* Free arena bytes, resident requests, and requests done but not collected. */
 lbm_status lbm_pool_stats(const lbm_pool *p, size_t *free_bytes, int *resident, int *done);
+
+/* Range R of a fixed-point pool (LBM_STORE_Q16), as lbm_set_storage_range: a power of two
+ * in [2^-8, 2^8], default 1, the same for every request.  Only while no request is
+ * resident (LBM_ERR_BUSY otherwise).  A request whose f^eq does not fit is refused by
+ * lbm_pool_submit with LBM_ERR_RANGE.  LBM_ERR_UNSUPPORTED for the floating forms. */
+lbm_status lbm_pool_set_storage_range(lbm_pool *p, double range);
 
 /* Kernel configuration of the batched step.  cells_per_thread: the most cells a thread
  * updates, 1 or 2 (the default); a request whose nx is odd always runs 1, so a request's

@@ -86,6 +86,7 @@ struct Request {
     int parity;                        // buffer holding the state after the launched steps
     size_t off, bytes;
     void *buf[2];
+    unsigned int *status;              // device status word (kStatusRange), after the two buffers
     bool waited_init;                  // compute stream already waits on its init event
     cudaEvent_t init_event;
     long long finish_chunk;            // chunk counter of its last step (-1 while running)
@@ -105,7 +106,8 @@ struct lbm_pool {
     cudaStream_t compute, io, capture;
     bool own_io;
     int block, grid;
-    int cpt;  // most cells per thread a slot may run (1 or 2; a slot with odd nx runs 1)
+    int cpt;  // most cells per thread a slot may run (1 or 2)
+    int qexp; // fixed-point storage: grid step 2^qexp
     // double-buffered slot tables
     BatchSlot *d_table[2];
     int *d_header[2];
@@ -135,7 +137,12 @@ lbm_status ensure_completed(lbm_pool *p, long long upto_exclusive, bool wait) {
     return LBM_OK;
 }
 
-size_t request_bytes(int Q, size_t ssize, long long C) { return 2 * align_up(size_t(C) * Q * ssize); }
+// A request's arena block: its two distribution buffers, then its status word.
+size_t buffer_bytes(int Q, size_t ssize, long long C) { return align_up(size_t(C) * Q * ssize); }
+size_t request_bytes(int Q, size_t ssize, long long C) { return 2 * buffer_bytes(Q, ssize, C) + kAlign; }
+
+// Reads (and clears) a request's status word on the io stream; LBM_ERR_RANGE if set.
+lbm_status request_status(lbm_pool *p, unsigned int *status);
 
 lbm_status get_graph(lbm_pool *p, long long chunk, int b, cudaGraphExec_t *out) {
     auto key = std::make_pair(chunk, b);
@@ -208,6 +215,8 @@ int build_table(lbm_pool *p, int b, int *units_total) {
         s.steps_left = int(std::min<int64_t>(left, 1 << 30));
         s.unit0 = units;
         s.units = int((s.threads + p->block - 1) / p->block);
+        s.qs = qscale_of_exponent(p->qexp);
+        s.status = r.status;
         fastdiv_init(unsigned(s.ncx), &s.mx, &s.sx);
         fastdiv_init(unsigned(r.ny), &s.my, &s.sy);
         units += s.units;
@@ -228,6 +237,7 @@ lbm_status pull_to(lbm_pool *p, Request &r, double *rho, double *u, lbm_mem mem)
     a.nz = r.nz;
     a.P = r.C;
     a.rho0 = r.rho0;
+    a.qs = qscale_of_exponent(p->qexp);
     a.f = nullptr;
     cudaError_t e;
     if (mem == LBM_MEM_DEVICE) {
@@ -241,7 +251,7 @@ lbm_status pull_to(lbm_pool *p, Request &r, double *rho, double *u, lbm_mem mem)
         if (e != cudaSuccess) return set_cuda_error(e, "pool: moments");
     } else {
         double *stage = static_cast<double *>(r.buf[cur ^ 1]);
-        const size_t cap = align_up(size_t(r.C) * p->Q * p->ssize);
+        const size_t cap = buffer_bytes(p->Q, p->ssize, r.C);
         const int per_cell = (rho ? 1 : 0) + (u ? p->D : 0);
         if (per_cell == 0) return LBM_OK;
         const long long per = (long long)(cap / (sizeof(double) * per_cell));
@@ -272,6 +282,18 @@ lbm_status pull_to(lbm_pool *p, Request &r, double *rho, double *u, lbm_mem mem)
     return LBM_OK;
 }
 
+lbm_status request_status(lbm_pool *p, unsigned int *status) {
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, status, sizeof(v), cudaMemcpyDeviceToHost, p->io);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->io);
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: status word");
+    if (v & kStatusRange) {
+        cudaMemsetAsync(status, 0, sizeof(unsigned int), p->io);
+        return set_error(LBM_ERR_RANGE, "pool: a value of this request left the fixed-point storage range");
+    }
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -290,7 +312,6 @@ lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, 
     int D, Q, maxc, kmax;
     if (!lattice_query(lat, &D, &Q, &maxc, &kmax)) return set_error(LBM_ERR_INVALID_ARG, "unknown lattice");
     if (storage_bytes(st) == 0) return set_error(LBM_ERR_UNSUPPORTED, "unknown storage");
-    if (st == LBM_STORE_Q16) return set_error(LBM_ERR_UNSUPPORTED, "pools serve the floating storage forms");
     if (K < 2 || K > kmax) return set_error(LBM_ERR_UNSUPPORTED, "truncation order outside [2, 2N-1]");
     if (!arena || reinterpret_cast<uintptr_t>(arena) % kAlign)
         return set_error(LBM_ERR_INVALID_ARG, "arena must be non-NULL and 256-byte aligned");
@@ -304,6 +325,7 @@ lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, 
     p->lat = lat;
     p->K = K;
     p->st = st;
+    p->qexp = -15;  // fixed-point range 1
     p->D = D;
     p->Q = Q;
     p->maxc = maxc;
@@ -369,14 +391,22 @@ lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, doubl
     r.parity = 0;
     r.bytes = request_bytes(p->Q, p->ssize, r.C);
     if (!p->arena.alloc(r.bytes, &r.off)) return set_error(LBM_ERR_BUSY, "pool: arena has no room for this request");
+    const size_t half = buffer_bytes(p->Q, p->ssize, r.C);
     r.buf[0] = p->arena.base + r.off;
-    r.buf[1] = p->arena.base + r.off + r.bytes / 2;
+    r.buf[1] = p->arena.base + r.off + half;
+    r.status = reinterpret_cast<unsigned int *>(p->arena.base + r.off + 2 * half);
     r.waited_init = false;
     r.finish_chunk = steps == 0 ? p->chunks - 1 : -1;
     cudaError_t e = cudaEventCreateWithFlags(&r.init_event, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         p->arena.release(r.off, r.bytes);
         return set_cuda_error(e, "pool: event");
+    }
+    e = cudaMemsetAsync(r.status, 0, sizeof(unsigned int), p->io);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(r.init_event);
+        p->arena.release(r.off, r.bytes);
+        return set_cuda_error(e, "pool: clear status word");
     }
     InitArgs a = {};
     a.dst = r.buf[0];
@@ -385,6 +415,8 @@ lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, doubl
     a.nz = r.nz;
     a.P = r.C;
     a.rho0 = rho0;
+    a.qs = qscale_of_exponent(p->qexp);
+    a.status = r.status;
     if (mem == LBM_MEM_DEVICE) {
         a.rho = rho;
         a.u = u;
@@ -394,7 +426,7 @@ lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, doubl
         e = p->ks->init(a, p->io);
     } else {
         double *stage = static_cast<double *>(r.buf[1]);
-        const long long per = (long long)((r.bytes / 2) / (sizeof(double) * (1 + p->D)));
+        const long long per = (long long)(half / (sizeof(double) * (1 + p->D)));
         for (long long c0 = 0; c0 < r.C && e == cudaSuccess; c0 += per) {
             const long long n = std::min(per, r.C - c0);
             e = cudaMemcpyAsync(stage, rho + c0, n * sizeof(double), cudaMemcpyHostToDevice, p->io);
@@ -415,6 +447,11 @@ lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, doubl
         cudaEventDestroy(r.init_event);
         p->arena.release(r.off, r.bytes);
         return set_cuda_error(e, "pool: upload");
+    }
+    if (lbm_status rs = request_status(p, r.status)) {  // f^eq does not fit the fixed-point range
+        cudaEventDestroy(r.init_event);
+        p->arena.release(r.off, r.bytes);
+        return rs;
     }
     r.id = p->next_id++;
     p->reqs[r.id] = r;
@@ -502,11 +539,12 @@ lbm_status lbm_pool_result(lbm_pool *p, int64_t id, double *rho, double *u, lbm_
     }
     lbm_status rs = pull_to(p, r, rho, u, mem);
     if (rs != LBM_OK) return rs;
+    const lbm_status st = request_status(p, r.status);  // LBM_ERR_RANGE: the outputs are not valid
     cudaEventDestroy(r.init_event);
     p->arena.release(r.off, r.bytes);
     p->order.erase(std::find(p->order.begin(), p->order.end(), id));
     p->reqs.erase(it);
-    return LBM_OK;
+    return st;
 }
 
 lbm_status lbm_pool_sync(lbm_pool *p) {
@@ -587,6 +625,19 @@ lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us) {
     rs = set_geometry(p, best_block, best_cpt);
     if (rs != LBM_OK) return rs;
     if (best_us) *best_us = 1000.0 * best / iters;
+    return LBM_OK;
+}
+
+lbm_status lbm_pool_set_storage_range(lbm_pool *p, double range) {
+    if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    std::lock_guard<std::mutex> lock(p->mu);
+    if (p->st != LBM_STORE_Q16) return set_error(LBM_ERR_UNSUPPORTED, "only the fixed-point storage has a range");
+    int e2 = 0;
+    const double m = frexp(range, &e2);  // range = m 2^e2, m in [1/2, 1)
+    if (!(range > 0.0) || !isfinite(range) || m != 0.5 || e2 - 1 < -8 || e2 - 1 > 8)
+        return set_error(LBM_ERR_INVALID_ARG, "range must be a power of two in [2^-8, 2^8]");
+    if (!p->reqs.empty()) return set_error(LBM_ERR_BUSY, "pool: the range can change only while no request is resident");
+    p->qexp = (e2 - 1) - 15;
     return LBM_OK;
 }
 

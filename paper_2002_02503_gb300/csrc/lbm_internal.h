@@ -104,6 +104,8 @@ struct BatchSlot {
     int unit0;         // first work unit of this slot (table sorted by unit0)
     int units;         // work units of this slot
     unsigned int mx, sx, my, sy;  // division by ncx (modes 0, 1) or nx (mode 2) and by ny (fastdiv_init)
+    QScale qs;                    // fixed-point grid step (LBM_STORE_Q16 only)
+    unsigned int *status;         // this request's status word (kStatusRange)
 };
 
 // Division by a runtime constant d (1 <= d < 2^31) as q = (umulhi(n, m) + n) >> s for
@@ -133,7 +135,7 @@ struct KernelSet {
     pull_fn pull_f;
     reduce_fn conservation;  // nvals = 4
     reduce_fn mode;          // nvals = 2
-    batch_fn batch;          // persistent multi-lattice step (1 or at most 2 cells per thread); null for fixed point
+    batch_fn batch;          // persistent multi-lattice step (1 or at most 2 cells per thread)
     int (*batch_occupancy)(int block, int cells_per_thread);
     step_fn bgk;             // BGK comparison operator, register pull with V = 1
     step_fn theta;           // filtered collision with the energy-flux term (K >= 3), V = 1

@@ -244,7 +244,8 @@ template <class LT, int K, class ST>
 __device__ __forceinline__ void pull_collide_store_pair(const typename ST::S *__restrict__ src,
                                                         typename ST::S *__restrict__ dst, int nx, int ny, int nz,
                                                         long long P, int x0, int y0, int z0, bool second,
-                                                        typename ST::T relax, typename ST::T rho0) {
+                                                        typename ST::T relax, typename ST::T rho0,
+                                                        const QScale &qs, unsigned int *__restrict__ status) {
     using T = typename ST::T;
     constexpr int Q = LT::Q;
     int x1 = x0 + 1, y1 = y0, z1 = z0;  // the next cell in flat order (the same cell when !second)
@@ -257,7 +258,6 @@ __device__ __forceinline__ void pull_collide_store_pair(const typename ST::S *__
             ++z1;
         }
     }
-    const QScale qs{};
     T f0[Q], f1[Q];
     pull_cell_scaled<LT, ST>(src, nx, ny, nz, P, x0, y0, z0, qs, f0);
     pull_cell_scaled<LT, ST>(src, nx, ny, nz, P, x1, y1, z1, qs, f1);
@@ -276,11 +276,14 @@ __device__ __forceinline__ void pull_collide_store_pair(const typename ST::S *__
         collide<LT, K, T>(f1, relax, rho0);
     }
     const long long c0 = x0 + (long long)nx * (y0 + (long long)ny * z0);
-    unsigned int acc = 0u;  // the batched step serves the floating storage forms only
+    unsigned int acc = 0u;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         dst[(long long)i * P + c0] = encode<ST>(f0[i], qs, acc);
         if (second) dst[(long long)i * P + c0 + 1] = encode<ST>(f1[i], qs, acc);
+    }
+    if constexpr (ST::id == LBM_STORE_Q16) {
+        if (range_exceeded(acc) && status) atomicOr(status, kStatusRange);
     }
 }
 
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__rest
             const int row = fastdiv(c0, sl.mx, sl.sx);  // c0 / nx
             const int z = fastdiv(row, sl.my, sl.sy);
             pull_collide_store_pair<LT, K, ST>(src, dst, sl.nx, sl.ny, sl.nz, sl.P, c0 - row * sl.nx, row - z * sl.ny,
-                                               z, (long long)c0 + 1 < sl.P, relax, rho0);
+                                               z, (long long)c0 + 1 < sl.P, relax, rho0, sl.qs, sl.status);
             continue;
         }
         const bool active = t < total;
@@ -341,10 +344,10 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__rest
         const int y = row - z * sl.ny;
         if (VMAX == 2 && sl.mode == 1)
             pull_collide_store<LT, K, ST, VMAX>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk, active, relax,
-                                                rho0, kq, QScale{}, nullptr);
+                                                rho0, kq, sl.qs, sl.status);
         else
             pull_collide_store<LT, K, ST, 1>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk, active, relax,
-                                             rho0, kq, QScale{}, nullptr);
+                                             rho0, kq, sl.qs, sl.status);
     }
 }
 
@@ -643,8 +646,7 @@ constexpr step_fn direct_if_built() {
     else return &launch_step_direct<LT, K, ST, V>;
 }
 
-// FP64 and fixed-point storage run on the register pull only; the fixed-point form
-// has no batched step either (a pool serves one floating storage class).
+// FP64 and fixed-point storage run on the register pull only (no staged variant).
 template <class ST>
 constexpr bool register_pull_only() {
     return sizeof(typename ST::S) == 8 || ST::id == LBM_STORE_Q16;
@@ -662,17 +664,6 @@ constexpr bool (*staged_check_if_built())(int) {
     else return &staged_applies<LT, ST>;
 }
 
-template <class LT, int K, class ST>
-constexpr batch_fn batch_if_built() {
-    if constexpr (ST::id == LBM_STORE_Q16) return nullptr;
-    else return &launch_batch<LT, K, ST>;
-}
-
-template <class LT, int K, class ST>
-constexpr int (*batch_occupancy_if_built())(int, int) {
-    if constexpr (ST::id == LBM_STORE_Q16) return nullptr;
-    else return &batch_occupancy<LT, K, ST>;
-}
 
 template <class LT, int K, class ST>
 constexpr step_fn theta_if_built() {
@@ -692,8 +683,8 @@ const KernelSet *make_kernel_set() {
         &launch_pull_f<LT, ST>,
         &launch_conservation<LT, ST>,
         &launch_mode<LT, ST>,
-        batch_if_built<LT, K, ST>(),
-        batch_occupancy_if_built<LT, K, ST>(),
+        &launch_batch<LT, K, ST>,
+        &batch_occupancy<LT, K, ST>,
         &launch_step_direct<LT, K, ST, 1, true>,
         theta_if_built<LT, K, ST>(),
         staged_check_if_built<LT, ST>(),

@@ -58,6 +58,7 @@ SIGNATURES = [
     ("lbm_pool_result", _c.c_int, [_P, _c.c_int64, _P, _P, _c.c_int]),
     ("lbm_pool_sync", _c.c_int, [_P]),
     ("lbm_pool_stats", _c.c_int, [_P, _c.POINTER(_c.c_size_t), _IP, _IP]),
+    ("lbm_pool_set_storage_range", _c.c_int, [_P, _c.c_double]),
     ("lbm_pool_set_kernel", _c.c_int, [_P, _c.c_int, _c.c_int]),
     ("lbm_pool_get_kernel", _c.c_int, [_P, _IP, _IP]),
     ("lbm_pool_autotune", _c.c_int, [_P, _c.c_int, _DP]),
@@ -388,6 +389,10 @@ def lbm_pool_stats(h):
     return {"free_bytes": fb.value, "resident": res.value, "done": dn.value}
 
 
+def lbm_pool_set_storage_range(h, R):
+    _check(lib().lbm_pool_set_storage_range(h, float(R)))
+
+
 def lbm_pool_set_kernel(h, cells_per_thread=0, block_threads=0):
     _check(lib().lbm_pool_set_kernel(h, int(cells_per_thread), int(block_threads)))
 
@@ -411,7 +416,7 @@ def lbm_pool_destroy(h):
 class Pool:
     """Owns a pool handle plus its device arena (a torch uint8 tensor) and two streams."""
 
-    def __init__(self, lattice, K, storage, arena_bytes, max_slots=256, device=None):
+    def __init__(self, lattice, K, storage, arena_bytes, max_slots=256, device=None, storage_range=None):
         import torch
 
         self.lattice = lattice
@@ -423,6 +428,8 @@ class Pool:
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=dev)
         self.handle = lbm_pool_create(lattice, K, storage, self.arena.data_ptr(), int(arena_bytes), max_slots,
                                       self.compute.cuda_stream, self.io.cuda_stream)
+        if storage_range is not None:
+            lbm_pool_set_storage_range(self.handle, storage_range)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

@@ -106,8 +106,8 @@ def test_null_solver_is_rejected(L):
 
 
 def test_fixed_point_storage_host_checks(L):
-    """The fixed-point form: two bytes per value, a range only it has, and the pool and the
-    allocation-free reduction turn it away before any device work."""
+    """The fixed-point form: two bytes per value, a range only it has, and the allocation-free
+    reduction turns it away before any device work."""
     n16 = lbm.lbm_workspace_bytes("D3Q19", (64, 64, 64), "f16")
     assert lbm.lbm_workspace_bytes("D3Q19", (64, 64, 64), "q16") == n16
     assert lbm.lib().lbm_set_storage_range(None, 1.0) == lbm.LBM_ERR_INVALID_ARG
@@ -115,7 +115,8 @@ def test_fixed_point_storage_host_checks(L):
     h = ctypes.c_void_p()
     st = lbm.lib().lbm_pool_create(lbm.LATTICES["D3Q19"], 3, lbm.STORAGES["q16"], None, 1 << 20, 4, None, None,
                                    ctypes.byref(h))
-    assert st == lbm.LBM_ERR_UNSUPPORTED and h.value is None
+    assert st == lbm.LBM_ERR_INVALID_ARG and h.value is None  # pools take it; the NULL arena is refused
+    assert lbm.lib().lbm_pool_set_storage_range(None, 1.0) == lbm.LBM_ERR_INVALID_ARG
     out = (ctypes.c_double * 4)()
     d = (ctypes.c_int64 * 3)(8, 8, 8)
     st = lbm.lib().lbm_conservation_noalloc(lbm.LATTICES["D3Q19"], lbm.STORAGES["q16"], d, 1.0,

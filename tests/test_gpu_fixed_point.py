@@ -4,7 +4,8 @@ h = q 2^e with q in [-32768, 32767] stored as q + 2^15 and the range R = 2^(e + 
 of two.  Checked here: the decoder is exact (integer codes in, FP64 values out, compared
 bit for bit), the encoder rounds to nearest with ties to even, a value beyond the range is
 reported as LBM_ERR_RANGE (a state whose next step leaves the range, as the oracle's own step
-shows) while the same state in a wider range is not, and results match the FP64 oracle."""
+shows) while the same state in a wider range is not, and results match the FP64 oracle; the same
+for pools of the fixed-point form."""
 import numpy as np
 import pytest
 
@@ -235,7 +236,93 @@ def oracle_reference_model(name, K, tau, dims, rho, u, steps, model, theta):
     return f, r, uu
 
 
-def test_pool_rejects_fixed_point():
+def _converging_pair(n, a):
+    """u_x = +a at x = 3 and -a at x = 4, rest at rho = 1: at tau = 0.51 max|h| grows from 0.238 to
+    0.258 at the third step for a = 0.074 (the oracle's own run), across the range 1/4."""
+    C = n ** 3
+    x = np.arange(C) % n
+    u = np.zeros((3, C))
+    u[0] = a * np.where(x == 3, 1.0, np.where(x == 4, -1.0, 0.0))
+    return np.ones(C), u
+
+
+def test_dynamic_range_exit_is_reported_by_the_solver():
+    rho, u = _converging_pair(8, 0.074)
+    f = oracle.init_eq("D3Q19", 2, (8, 8, 8), rho, u)
+    w = oracle.lattice("D3Q19")["w"][:, None]
+    hmax = [np.abs((f - w) / w).max()]
+    for _ in range(3):
+        f = oracle.run("D3Q19", 2, 0.51, (8, 8, 8), f, 1)
+        hmax.append(np.abs((f - w) / w).max())
+    assert hmax[0] < 0.25 * 0.97 and hmax[3] > 0.25 * 1.02, hmax
+    s = lbm.Solver("D3Q19", (8, 8, 8), 0.51, 2, "q16", storage_range=0.25)
+    s.set_fields(rho, u)  # fits at t = 0
+    s.step(3)
     with pytest.raises(lbm.LbmError) as e:
-        lbm.Pool("D3Q19", 3, "q16", 1 << 20, 4)
-    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+        s.moments()
+    assert e.value.status == lbm.LBM_ERR_RANGE
+    s.close()
+
+
+def test_pool_fixed_point():
+    """A fixed-point pool: results match the single-lattice fixed-point solver and the oracle within
+    the 16-bit bound, a request's result is the same alone and in a mix, and a request that leaves
+    the range is reported on its own result while the others are unaffected."""
+    def run(reqs, R=0.25):
+        pool = lbm.Pool("D3Q19", 2, "q16", 1 << 30, 16, storage_range=R)
+        ids = [pool.submit(d, tau, rho, u, n) for d, tau, rho, u, n in reqs]
+        assert all(i is not None for i in ids)
+        while not all(pool.poll(i)[0] for i in ids):
+            pool.advance(7)
+            pool.sync()
+        out = []
+        for (d, _, _, _, _), i in zip(reqs, ids):
+            try:
+                out.append(pool.result(i, int(np.prod(d))))
+            except lbm.LbmError as e:
+                out.append(e.status)
+        pool.close()
+        return out
+
+    good = []
+    for side, u0 in ((24, 0.04), (27, 0.03)):
+        d = (side,) * 3
+        rho, u = fields.taylor_green_3d(d, u0, 1.0 / 3.0)
+        good.append((d, 0.6, rho, u, 40))
+    rho_b, u_b = _converging_pair(8, 0.074)
+    bad = ((8, 8, 8), 0.51, rho_b, u_b, 10)
+    mixed = run([good[0], bad, good[1]])
+    assert mixed[1] == lbm.LBM_ERR_RANGE
+    alone = run([good[0]])
+    np.testing.assert_array_equal(alone[0][1], mixed[0][1])
+    for k, (d, tau, rho, u, n) in zip((0, 2), good):
+        _, r_ref, u_ref = oracle_reference("D3Q19", 2, tau, d, rho, u, n)
+        assert rel_u(mixed[k][1], u_ref) < TOL_U16
+        assert rel_f(mixed[k][0], r_ref) < TOL_U16
+        s = lbm.Solver("D3Q19", d, tau, 2, "q16", storage_range=0.25)
+        s.set_fields(rho, u)
+        s.step(n)
+        r1, u1 = s.moments()
+        s.close()
+        assert rel_u(mixed[k][1], u1) < TOL_U16
+    # in twice the range the same request runs through
+    wide = run([bad], R=0.5)
+    assert not isinstance(wide[0], int)
+    # f^eq beyond the range is refused at admission; the pool's range changes only when empty
+    pool = lbm.Pool("D3Q19", 2, "q16", 1 << 28, 4, storage_range=2.0 ** -4)
+    d = (16, 16, 16)
+    rho, u = fields.taylor_green_3d(d, 0.05, 1.0 / 3.0)
+    with pytest.raises(lbm.LbmError) as e:
+        pool.submit(d, 0.6, rho, u, 5)
+    assert e.value.status == lbm.LBM_ERR_RANGE
+    assert pool.stats()["resident"] == 0
+    lbm.lbm_pool_set_storage_range(pool.handle, 0.25)
+    rid = pool.submit(d, 0.6, rho, u, 5)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_pool_set_storage_range(pool.handle, 0.5)
+    assert e.value.status == lbm.LBM_ERR_BUSY
+    while not pool.poll(rid)[0]:
+        pool.advance(5)
+        pool.sync()
+    pool.result(rid, 16 ** 3)
+    pool.close()
