@@ -448,6 +448,7 @@ def run_ours(a):
                 burst = [dict(r, arrival=0.0) for r in trace]
                 burst_pool, _ = serve.serve_pool(burst)
                 burst_plain, _ = serve.serve_plain(burst)
+                extras["serving_accuracy"] = serve.served_accuracy()
                 extras["serving"] = {
                     "workload": "%d D3Q19 Taylor-Green solves, side log-uniform 32-128, tau U[0.52,1], "
                                 "u0 U[0.01,0.08], 100-2000 steps, Poisson %g/s, FP32, K=3" % (a.serve, a.serve_rate),

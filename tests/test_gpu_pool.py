@@ -201,3 +201,13 @@ def test_cells_per_thread_of_the_batched_step():
         assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
     assert lbm.lbm_pool_get_kernel(pool.handle) == (2, 256)
     pool.close()
+
+
+def test_served_accuracy_by_storage_form():
+    """Requests drawn like the serving trace, served by pools of each storage form, against the FP32
+    single-lattice solver: the FP32 pool within the FP32 tolerance, the fixed-point pool (range 1/2)
+    within the 16-bit bound on every request; FP16 and BF16 are reported."""
+    acc = serve.served_accuracy(n=8, salt=11)
+    print(acc)
+    assert acc["f32"]["max_rel_u"] < TOL_F32
+    assert acc["q16 (range 0.5)"]["max_rel_u"] < 1e-3
