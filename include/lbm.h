@@ -21,6 +21,8 @@
  *     device memory of the solver's device.
  *   - Every call returns an lbm_status; none throws, aborts or exits.  On an
  *     error, lbm_last_error() holds a message for the calling thread.
+ *   - The calls that do host-visible work mark it with NVTX ranges named after the
+ *     call (for timeline profilers; no cost beyond a branch without one).
  *   - The library makes no device-memory allocation: the caller owns the
  *     workspace, the pool arena and every buffer.  It creates CUDA streams,
  *     events and graphs for its own scheduling, pinned host memory for a pool's
@@ -250,6 +252,12 @@ lbm_status lbm_pool_poll(lbm_pool *p, int64_t id, int *done, int64_t *steps_done
  * during its steps; the outputs are not valid and the request is released all the same.
  * Other requests are unaffected. */
 lbm_status lbm_pool_result(lbm_pool *p, int64_t id, double *rho, double *u, lbm_mem mem);
+
+/* Withdraw a request, done or not (a client that has gone away, a solve that is no longer
+ * wanted): no further steps are scheduled for it, and once the chunks in flight and its upload
+ * have finished (the call waits for them) its memory returns to the arena.  The other requests
+ * run on unaffected.  LBM_ERR_NOT_FOUND for an unknown (or already collected) id. */
+lbm_status lbm_pool_cancel(lbm_pool *p, int64_t id);
 
 /* Wait for every launched chunk. */
 lbm_status lbm_pool_sync(lbm_pool *p);

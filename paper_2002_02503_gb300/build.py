@@ -74,7 +74,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if force or _stale(LIB, objs):
         tmp = LIB + ".tmp.%d" % os.getpid()
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
-            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+            "-ldl", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]  # -ldl: the NVTX loader (lbm_trace.h)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -18,6 +18,7 @@
 
 #include "lbm_internal.h"
 #include "lbm_lattice.cuh"
+#include "lbm_trace.h"
 
 using namespace lbm;
 
@@ -288,6 +289,7 @@ size_t lbm_workspace_bytes(lbm_lattice lat, const int64_t dims[3], lbm_storage s
 
 lbm_status lbm_create(lbm_lattice lat, const int64_t dims[3], double tau, int K, lbm_storage st, double rho0,
                       void *ws, size_t ws_bytes, void *stream, lbm_solver **out) {
+    LBM_NVTX_RANGE("lbm_create");
     if (!out) return fail(LBM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     LatInfo li;
@@ -365,6 +367,7 @@ lbm_status lbm_destroy(lbm_solver *s) {
 }
 
 lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm_mem mem) {
+    LBM_NVTX_RANGE("lbm_set_fields");
     if (lbm_status r = check_solver(s)) return r;
     if (!rho || !u) return fail(LBM_ERR_INVALID_ARG, "rho and u are required");
     if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return fail(LBM_ERR_INVALID_ARG, "bad lbm_mem");
@@ -466,6 +469,7 @@ static cudaError_t step_graph(lbm_solver *s, step_fn fn, int from, cudaGraphExec
 }
 
 lbm_status lbm_step(lbm_solver *s, int64_t n) {
+    LBM_NVTX_RANGE("lbm_step");
     if (lbm_status r = check_solver(s)) return r;
     if (n < 0) return fail(LBM_ERR_INVALID_ARG, "n must be >= 0");
     step_fn fn = step_for(s, s->variant, s->V);
@@ -490,6 +494,7 @@ lbm_status lbm_step(lbm_solver *s, int64_t n) {
 }
 
 static lbm_status pull_out(lbm_solver *s, double *rho, double *u, double *f, lbm_mem mem) {
+    LBM_NVTX_RANGE(f ? "lbm_get_f" : "lbm_get_moments");
     if (lbm_status st = check_device_status(s)) return st;
     const int D = s->li.D, Q = s->li.Q;
     PullArgs a = {};
@@ -565,6 +570,7 @@ lbm_status lbm_get_f(lbm_solver *s, double *f, lbm_mem mem) {
 }
 
 static lbm_status reduce_to_host(lbm_solver *s, reduce_fn fn, ReduceArgs &a, int nvals, double *out) {
+    LBM_NVTX_RANGE(nvals == 4 ? "lbm_conservation" : "lbm_mode_amplitude");
     if (lbm_status st = check_device_status(s)) return st;
     a.src = s->buf[s->cur];
     a.nx = s->nx;
@@ -608,6 +614,7 @@ lbm_status lbm_mode_amplitude(lbm_solver *s, const int64_t k[3], int component, 
 }
 
 lbm_status lbm_get_distributions(lbm_solver *s, void *dst, size_t bytes, lbm_mem mem, int64_t *t) {
+    LBM_NVTX_RANGE("lbm_get_distributions");
     if (lbm_status r = check_solver(s)) return r;
     if (!dst) return fail(LBM_ERR_INVALID_ARG, "dst is NULL");
     if (bytes != s->buf_bytes) return fail(LBM_ERR_INVALID_ARG, "bytes must be %zu", s->buf_bytes);
@@ -620,6 +627,7 @@ lbm_status lbm_get_distributions(lbm_solver *s, void *dst, size_t bytes, lbm_mem
 }
 
 lbm_status lbm_set_distributions(lbm_solver *s, const void *src, size_t bytes, lbm_mem mem, int64_t t) {
+    LBM_NVTX_RANGE("lbm_set_distributions");
     if (lbm_status r = check_solver(s)) return r;
     if (!src) return fail(LBM_ERR_INVALID_ARG, "src is NULL");
     if (bytes != s->buf_bytes) return fail(LBM_ERR_INVALID_ARG, "bytes must be %zu", s->buf_bytes);
@@ -721,6 +729,7 @@ lbm_status lbm_get_kernel(const lbm_solver *s, int *variant, int *V, int *block)
 }
 
 lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us) {
+    LBM_NVTX_RANGE("lbm_autotune");
     if (lbm_status r = check_solver(s)) return r;
     if (iters < 1) iters = 1;
     cudaEvent_t e0, e1;

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "lbm_internal.h"
+#include "lbm_trace.h"
 
 using namespace lbm;
 
@@ -370,6 +371,7 @@ lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, 
 
 lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, double rho0, const double *rho,
                            const double *u, lbm_mem mem, int64_t steps, int64_t *id) {
+    LBM_NVTX_RANGE("lbm_pool_submit");
     if (!p || !dims || !rho || !u || !id) return set_error(LBM_ERR_INVALID_ARG, "pool, dims, rho, u, id required");
     std::lock_guard<std::mutex> lock(p->mu);
     std::string dp = dims_check(p->lat, dims);
@@ -461,6 +463,7 @@ lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, doubl
 }
 
 lbm_status lbm_pool_advance(lbm_pool *p, int64_t chunk, int *active) {
+    LBM_NVTX_RANGE("lbm_pool_advance");
     if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
     if (chunk < 1 || chunk > 100000) return set_error(LBM_ERR_INVALID_ARG, "chunk_steps out of range");
     std::lock_guard<std::mutex> lock(p->mu);
@@ -521,6 +524,7 @@ lbm_status lbm_pool_poll(lbm_pool *p, int64_t id, int *done, int64_t *steps_done
 }
 
 lbm_status lbm_pool_result(lbm_pool *p, int64_t id, double *rho, double *u, lbm_mem mem) {
+    LBM_NVTX_RANGE("lbm_pool_result");
     if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
     if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return set_error(LBM_ERR_INVALID_ARG, "bad lbm_mem");
     std::lock_guard<std::mutex> lock(p->mu);
@@ -547,6 +551,25 @@ lbm_status lbm_pool_result(lbm_pool *p, int64_t id, double *rho, double *u, lbm_
     return st;
 }
 
+lbm_status lbm_pool_cancel(lbm_pool *p, int64_t id) {
+    if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    LBM_NVTX_RANGE("lbm_pool_cancel");
+    std::lock_guard<std::mutex> lock(p->mu);
+    auto it = p->reqs.find(id);
+    if (it == p->reqs.end()) return set_error(LBM_ERR_NOT_FOUND, "unknown request id");
+    Request &r = it->second;
+    // the launched chunks may still step it, and its upload may still be writing: let both finish
+    lbm_status rs = ensure_completed(p, p->chunks, true);
+    if (rs != LBM_OK) return rs;
+    cudaError_t e = cudaEventSynchronize(r.init_event);
+    if (e != cudaSuccess) return set_cuda_error(e, "pool: cancel");
+    cudaEventDestroy(r.init_event);
+    p->arena.release(r.off, r.bytes);
+    p->order.erase(std::find(p->order.begin(), p->order.end(), id));
+    p->reqs.erase(it);
+    return LBM_OK;
+}
+
 lbm_status lbm_pool_sync(lbm_pool *p) {
     if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
     std::lock_guard<std::mutex> lock(p->mu);
@@ -567,6 +590,7 @@ lbm_status lbm_pool_stats(const lbm_pool *p, size_t *free_bytes, int *resident, 
 }
 
 lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us) {
+    LBM_NVTX_RANGE("lbm_pool_autotune");
     if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
     if (iters < 1) iters = 1;
     std::lock_guard<std::mutex> lock(p->mu);

@@ -56,6 +56,7 @@ SIGNATURES = [
     ("lbm_pool_advance", _c.c_int, [_P, _c.c_int64, _IP]),
     ("lbm_pool_poll", _c.c_int, [_P, _c.c_int64, _IP, _c.POINTER(_c.c_int64)]),
     ("lbm_pool_result", _c.c_int, [_P, _c.c_int64, _P, _P, _c.c_int]),
+    ("lbm_pool_cancel", _c.c_int, [_P, _c.c_int64]),
     ("lbm_pool_sync", _c.c_int, [_P]),
     ("lbm_pool_stats", _c.c_int, [_P, _c.POINTER(_c.c_size_t), _IP, _IP]),
     ("lbm_pool_set_storage_range", _c.c_int, [_P, _c.c_double]),
@@ -387,6 +388,10 @@ def lbm_pool_stats(h):
     res, dn = ctypes.c_int(), ctypes.c_int()
     _check(lib().lbm_pool_stats(h, ctypes.byref(fb), ctypes.byref(res), ctypes.byref(dn)))
     return {"free_bytes": fb.value, "resident": res.value, "done": dn.value}
+
+
+def lbm_pool_cancel(h, rid):
+    _check(lib().lbm_pool_cancel(h, int(rid)))
 
 
 def lbm_pool_set_storage_range(h, R):

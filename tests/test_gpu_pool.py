@@ -216,3 +216,39 @@ def test_served_accuracy_by_storage_form():
     assert acc["f32"]["max_du_over_u0"] < TOL_F32
     for form in ("f16", "q16 (range 0.5)"):
         assert acc[form]["max_du_over_u0"] < 1e-2, form
+
+
+def test_cancelled_request_leaves_the_others_unchanged():
+    """Host-side fault injection: a request withdrawn mid-run (and one withdrawn before its first
+    step) frees its memory, and the requests that stay give bit for bit the results they give when
+    the withdrawn ones never existed."""
+    reqs = [(28, 0.7, 0.05, 60), (21, 0.6, 0.04, 60), (35, 0.8, 0.06, 45)]
+    base = _run_pool([reqs[0], reqs[2]], kernel=(2, 128))
+    pool = lbm.Pool("D3Q19", 3, "f32", 1 << 30, 16)
+    lbm.lbm_pool_set_kernel(pool.handle, 2, 128)
+    free0 = pool.stats()["free_bytes"]
+    ids = []
+    for side, tau, u0, steps in reqs:
+        rho, u = _tg(side, u0)
+        ids.append(pool.submit((side,) * 3, tau, rho, u, steps))
+    rho, u = _tg(16, 0.03)
+    never = pool.submit((16,) * 3, 0.7, rho, u, 100)
+    lbm.lbm_pool_cancel(pool.handle, never)  # before any step
+    pool.advance(14)
+    pool.advance(14)
+    lbm.lbm_pool_cancel(pool.handle, ids[1])  # with chunks in flight
+    with pytest.raises(lbm.LbmError) as e:
+        pool.poll(ids[1])
+    assert e.value.status == lbm.LBM_ERR_NOT_FOUND
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_pool_cancel(pool.handle, ids[1])
+    assert e.value.status == lbm.LBM_ERR_NOT_FOUND
+    while not (pool.poll(ids[0])[0] and pool.poll(ids[2])[0]):
+        pool.advance(14)
+        pool.sync()
+    r0 = pool.result(ids[0], 28 ** 3)
+    r2 = pool.result(ids[2], 35 ** 3)
+    assert pool.stats()["resident"] == 0 and pool.stats()["free_bytes"] == free0
+    pool.close()
+    np.testing.assert_array_equal(r0[1], base[0][1])
+    np.testing.assert_array_equal(r2[1], base[1][1])
