@@ -214,160 +214,6 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
                                                  rho0, kq, qs, status);
 }
 
-// ------------------------------------------------------------------ flat cell pairs
-// Pre-collision values of one cell pulled with direct shifted loads (any nx).
-template <class LT, class ST>
-__device__ __forceinline__ void pull_cell_scaled(const typename ST::S *__restrict__ src, int nx, int ny, int nz,
-                                                 long long P, int x, int y, int z, const QScale &qs,
-                                                 typename ST::T (&f)[LT::Q]) {
-    constexpr int M = LT::MAXC;
-    int xs[2 * M + 1], ys[2 * M + 1], zs[2 * M + 1];
-#pragma unroll
-    for (int k = -M; k <= M; ++k) {
-        xs[k + M] = wrap1(x - k, nx);  // dims >= max|c| is checked on the host
-        ys[k + M] = wrap1(y - k, ny);
-        zs[k + M] = wrap1(z - k, nz);
-    }
-#pragma unroll
-    for (int i = 0; i < LT::Q; ++i) {
-        const long long at = (long long)i * P + (long long)(zs[vel<LT>(i, 2) + M] * ny + ys[vel<LT>(i, 1) + M]) * nx +
-                             xs[vel<LT>(i, 0) + M];
-        f[i] = decode<ST>(src[at], qs);
-    }
-}
-
-// Two consecutive cells of the flat index, c0 = x0 + nx (y0 + ny z0) and c0 + 1 (when
-// `second`), for any nx: each is pulled with direct loads, and the pair runs one pass of
-// the collision on the paired FP32 instructions (two scalar passes in FP64).  No warp
-// collectives: a thread with nothing to do may skip the call.
-template <class LT, int K, class ST>
-__device__ __forceinline__ void pull_collide_store_pair(const typename ST::S *__restrict__ src,
-                                                        typename ST::S *__restrict__ dst, int nx, int ny, int nz,
-                                                        long long P, int x0, int y0, int z0, bool second,
-                                                        typename ST::T relax, typename ST::T rho0,
-                                                        const QScale &qs, unsigned int *__restrict__ status) {
-    using T = typename ST::T;
-    constexpr int Q = LT::Q;
-    int x1 = x0 + 1, y1 = y0, z1 = z0;  // the next cell in flat order (the same cell when !second)
-    if (!second) {
-        x1 = x0;
-    } else if (x1 == nx) {
-        x1 = 0;
-        if (++y1 == ny) {
-            y1 = 0;
-            ++z1;
-        }
-    }
-    T f0[Q], f1[Q];
-    pull_cell_scaled<LT, ST>(src, nx, ny, nz, P, x0, y0, z0, qs, f0);
-    pull_cell_scaled<LT, ST>(src, nx, ny, nz, P, x1, y1, z1, qs, f1);
-    if constexpr (sizeof(T) == 4) {
-        F2 g[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = F2(make_float2(f0[i], f1[i]));
-        collide<LT, K, F2>(g, F2(relax), F2(rho0), F2(0.0));
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            f0[i] = g[i].v.x;
-            f1[i] = g[i].v.y;
-        }
-    } else {
-        collide<LT, K, T>(f0, relax, rho0);
-        collide<LT, K, T>(f1, relax, rho0);
-    }
-    const long long c0 = x0 + (long long)nx * (y0 + (long long)ny * z0);
-    unsigned int acc = 0u;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        dst[(long long)i * P + c0] = encode<ST>(f0[i], qs, acc);
-        if (second) dst[(long long)i * P + c0 + 1] = encode<ST>(f1[i], qs, acc);
-    }
-    if constexpr (ST::id == LBM_STORE_Q16) {
-        if (range_exceeded(acc) && status) atomicOr(status, kStatusRange);
-    }
-}
-
-// ------------------------------------------------------------------ batched step
-// Persistent kernel over the work units of every slot in a table (one unit =
-// blockDim.x consecutive threads of one lattice).  A slot runs in the mode its table
-// entry names: one cell per thread, or two -- x-neighbours with row vector loads for even
-// nx, consecutive cells of the flat index for odd nx -- whose collision runs on the paired
-// FP32 instructions.  A CTA serves one unit, so the mode is uniform across it and depends
-// only on the slot, never on the other residents.  One launch
-// advances every slot with step_index < steps_left by one step; the slot's buffers
-// alternate with its parity.  The table lives in device memory, so a captured graph
-// of launches stays valid while the host rewrites the table between chunks.
-__device__ __forceinline__ int fastdiv(int n, unsigned int m, unsigned int s) {
-    return int((__umulhi((unsigned int)n, m) + (unsigned int)n) >> s);
-}
-
-template <class LT, int K, class ST, int VMAX>
-__global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__restrict__ slots,
-                                                         const int *__restrict__ header, int step_index) {
-    const int total_units = header[0];
-    const int nslots = header[1];
-    // grid-stride over units (neighbouring CTAs work on neighbouring rows at the same time);
-    // units only increase, so each thread walks the slot index forward without a barrier
-    int slot = 0;
-    for (int unit = blockIdx.x; unit < total_units; unit += gridDim.x) {
-        if (slot + 1 < nslots && slots[slot + 1].unit0 <= unit) {
-            int lo = slot + 1, hi = nslots - 1;  // last slot with unit0 <= unit
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (slots[mid].unit0 <= unit) lo = mid;
-                else hi = mid - 1;
-            }
-            slot = lo;
-        }
-        const BatchSlot &sl = slots[slot];
-        if (step_index >= sl.steps_left) continue;  // uniform across the CTA
-        const int cur = (sl.parity + step_index) & 1;
-        const int total = sl.threads;
-        int t = (unit - sl.unit0) * blockDim.x + threadIdx.x;
-        const auto *src = static_cast<const typename ST::S *>(sl.buf[cur]);
-        auto *dst = static_cast<typename ST::S *>(sl.buf[cur ^ 1]);
-        const typename ST::T relax(sl.relax), rho0(sl.rho0), kq(0);
-        if (VMAX == 2 && sl.mode == 2) {
-            if (t >= total) continue;  // no warp collectives on this path
-            const int c0 = 2 * t;
-            const int row = fastdiv(c0, sl.mx, sl.sx);  // c0 / nx
-            const int z = fastdiv(row, sl.my, sl.sy);
-            pull_collide_store_pair<LT, K, ST>(src, dst, sl.nx, sl.ny, sl.nz, sl.P, c0 - row * sl.nx, row - z * sl.ny,
-                                               z, (long long)c0 + 1 < sl.P, relax, rho0, sl.qs, sl.status);
-            continue;
-        }
-        const bool active = t < total;
-        if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
-        const int row = fastdiv(t, sl.mx, sl.sx);  // t / ncx
-        const int chunk = t - row * sl.ncx;
-        const int z = fastdiv(row, sl.my, sl.sy);
-        const int y = row - z * sl.ny;
-        if (VMAX == 2 && sl.mode == 1)
-            pull_collide_store<LT, K, ST, VMAX>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk, active, relax,
-                                                rho0, kq, sl.qs, sl.status);
-        else
-            pull_collide_store<LT, K, ST, 1>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk, active, relax,
-                                             rho0, kq, sl.qs, sl.status);
-    }
-}
-
-template <class LT, int K, class ST>
-cudaError_t launch_batch(const BatchSlot *slots, const int *header, int step_index, int grid, int block, int cpt,
-                         cudaStream_t stream) {
-    if (cpt == 2) batch_step_kernel<LT, K, ST, 2><<<grid, block, 0, stream>>>(slots, header, step_index);
-    else batch_step_kernel<LT, K, ST, 1><<<grid, block, 0, stream>>>(slots, header, step_index);
-    return cudaGetLastError();
-}
-
-template <class LT, int K, class ST>
-int batch_occupancy(int block, int cpt) {
-    int n = 0;
-    cudaError_t e = cpt == 2
-                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 2>, block, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 1>, block, 0);
-    return e == cudaSuccess ? n : 0;
-}
-
 template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false>
 cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream) {
     using T = typename ST::T;
@@ -635,6 +481,12 @@ cudaError_t launch_mode(const ReduceArgs &a, cudaStream_t stream) {
     final_reduce_kernel<2><<<1, 2 * 32, 0, stream>>>(a.partials, a.blocks, a.out);
     return cudaGetLastError();
 }
+
+}  // namespace lbm
+
+#include "lbm_batch_kernels.cuh"
+
+namespace lbm {
 
 // ------------------------------------------------------------------ kernel sets
 template <class LT, int K, class ST, int V>
