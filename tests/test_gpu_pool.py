@@ -252,3 +252,45 @@ def test_cancelled_request_leaves_the_others_unchanged():
     pool.close()
     np.testing.assert_array_equal(r0[1], base[0][1])
     np.testing.assert_array_equal(r2[1], base[1][1])
+
+
+def test_many_small_requests_under_memory_pressure():
+    """300 requests of sides 3-20 (odd and even, so both cell-pair modes), random tau and 0-40
+    steps, through an arena that holds about a third of them at once: requests are admitted as
+    others' results free memory, and every result matches its own single-lattice run."""
+    g = np.random.default_rng(99)
+    reqs = [(int(g.integers(3, 21)), float(g.uniform(0.52, 1.0)), float(g.uniform(0.01, 0.08)),
+             int(g.integers(0, 41))) for _ in range(300)]
+    per = [lbm.lbm_pool_request_bytes("D3Q19", (sd,) * 3, "f32") for sd, _, _, _ in reqs]
+    pool = lbm.Pool("D3Q19", 3, "f32", sum(per) // 3 + (1 << 20), 512)
+    free0 = pool.stats()["free_bytes"]
+    todo = list(range(len(reqs)))
+    ids, out = {}, {}
+    rounds = 0
+    while len(out) < len(reqs):
+        while todo:
+            sd, tau, u0, n = reqs[todo[0]]
+            rho, u = _tg(sd, u0)
+            rid = pool.submit((sd,) * 3, tau, rho, u, n)
+            if rid is None:
+                break
+            ids[todo.pop(0)] = rid
+        pool.advance(13)
+        pool.sync()
+        for k, rid in list(ids.items()):
+            if pool.poll(rid)[0]:
+                out[k] = pool.result(rid, reqs[k][0] ** 3)
+                del ids[k]
+        rounds += 1
+        assert rounds < 1000
+    assert pool.stats()["free_bytes"] == free0
+    pool.close()
+    for k, (sd, tau, u0, n) in enumerate(reqs):
+        s = lbm.Solver("D3Q19", (sd,) * 3, tau, 3, "f32")
+        rho, u = _tg(sd, u0)
+        s.set_fields(rho, u)
+        s.step(n)
+        r, uu = s.moments()
+        s.close()
+        assert rel_f(out[k][0], r) < TOL_F32, k
+        assert np.max(np.abs(out[k][1] - uu)) < TOL_F32 * u0, k
