@@ -177,6 +177,7 @@ lbm_status lbm_set_energy_flux(lbm_solver *s, double theta);
  * rho - rho0 and the non-equilibrium part, so R = 1/4 holds flows with |c_i . u| up to
  * about 0.07 on the T0 = 1/3 lattices.  LBM_ERR_UNSUPPORTED for the floating forms. */
 lbm_status lbm_set_storage_range(lbm_solver *s, double range);
+lbm_status lbm_get_storage_range(const lbm_solver *s, double *range);
 
 /* Autotuner: times every built kernel configuration for this solver on its own
  * buffers (reads the current state, writes only the idle buffer, so the state is
@@ -270,6 +271,7 @@ lbm_status lbm_pool_stats(const lbm_pool *p, size_t *free_bytes, int *resident, 
  * resident (LBM_ERR_BUSY otherwise).  A request whose f^eq does not fit is refused by
  * lbm_pool_submit with LBM_ERR_RANGE.  LBM_ERR_UNSUPPORTED for the floating forms. */
 lbm_status lbm_pool_set_storage_range(lbm_pool *p, double range);
+lbm_status lbm_pool_get_storage_range(const lbm_pool *p, double *range);
 
 /* Kernel configuration of the batched step.  cells_per_thread: the most cells a thread
  * updates, 1 or 2 (the default); a request whose nx is odd always runs 1, so a request's

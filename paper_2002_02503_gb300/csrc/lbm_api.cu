@@ -720,6 +720,13 @@ lbm_status lbm_set_storage_range(lbm_solver *s, double range) {
     return LBM_OK;
 }
 
+lbm_status lbm_get_storage_range(const lbm_solver *s, double *range) {
+    if (!s || !range) return fail(LBM_ERR_INVALID_ARG, "solver and range are required");
+    if (s->st != LBM_STORE_Q16) return fail(LBM_ERR_UNSUPPORTED, "only the fixed-point storage has a range");
+    *range = ldexp(1.0, s->qexp + 15);
+    return LBM_OK;
+}
+
 lbm_status lbm_get_kernel(const lbm_solver *s, int *variant, int *V, int *block) {
     if (!s) return fail(LBM_ERR_INVALID_ARG, "solver is NULL");
     if (variant) *variant = s->variant;

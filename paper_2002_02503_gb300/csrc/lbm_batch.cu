@@ -665,6 +665,13 @@ lbm_status lbm_pool_set_storage_range(lbm_pool *p, double range) {
     return LBM_OK;
 }
 
+lbm_status lbm_pool_get_storage_range(const lbm_pool *p, double *range) {
+    if (!p || !range) return set_error(LBM_ERR_INVALID_ARG, "pool and range are required");
+    if (p->st != LBM_STORE_Q16) return set_error(LBM_ERR_UNSUPPORTED, "only the fixed-point storage has a range");
+    *range = ldexp(1.0, p->qexp + 15);
+    return LBM_OK;
+}
+
 lbm_status lbm_pool_set_kernel(lbm_pool *p, int cells_per_thread, int block_threads) {
     if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
     std::lock_guard<std::mutex> lock(p->mu);

@@ -46,6 +46,7 @@ SIGNATURES = [
     ("lbm_set_collision", _c.c_int, [_P, _c.c_int]),
     ("lbm_set_energy_flux", _c.c_int, [_P, _c.c_double]),
     ("lbm_set_storage_range", _c.c_int, [_P, _c.c_double]),
+    ("lbm_get_storage_range", _c.c_int, [_P, _DP]),
     ("lbm_autotune", _c.c_int, [_P, _c.c_int, _DP]),
     ("lbm_conservation_noalloc", _c.c_int, [_c.c_int, _c.c_int, _I64P, _c.c_double, _P, _P, _c.c_int, _P]),
     ("lbm_destroy", _c.c_int, [_P]),
@@ -60,6 +61,7 @@ SIGNATURES = [
     ("lbm_pool_sync", _c.c_int, [_P]),
     ("lbm_pool_stats", _c.c_int, [_P, _c.POINTER(_c.c_size_t), _IP, _IP]),
     ("lbm_pool_set_storage_range", _c.c_int, [_P, _c.c_double]),
+    ("lbm_pool_get_storage_range", _c.c_int, [_P, _DP]),
     ("lbm_pool_set_kernel", _c.c_int, [_P, _c.c_int, _c.c_int]),
     ("lbm_pool_get_kernel", _c.c_int, [_P, _IP, _IP]),
     ("lbm_pool_autotune", _c.c_int, [_P, _c.c_int, _DP]),
@@ -240,6 +242,12 @@ def lbm_set_storage_range(h, R):
     _check(lib().lbm_set_storage_range(h, float(R)))
 
 
+def lbm_get_storage_range(h):
+    r = ctypes.c_double()
+    _check(lib().lbm_get_storage_range(h, ctypes.byref(r)))
+    return r.value
+
+
 def lbm_autotune(h, iters=10):
     us = ctypes.c_double()
     _check(lib().lbm_autotune(h, int(iters), ctypes.byref(us)))
@@ -396,6 +404,12 @@ def lbm_pool_cancel(h, rid):
 
 def lbm_pool_set_storage_range(h, R):
     _check(lib().lbm_pool_set_storage_range(h, float(R)))
+
+
+def lbm_pool_get_storage_range(h):
+    r = ctypes.c_double()
+    _check(lib().lbm_pool_get_storage_range(h, ctypes.byref(r)))
+    return r.value
 
 
 def lbm_pool_set_kernel(h, cells_per_thread=0, block_threads=0):
