@@ -202,9 +202,16 @@ def oracle_sample(a, seconds):
     t0 = time.perf_counter()
     oracle.run(a.lattice, a.K, a.tau, dims, f, steps, nthreads)
     dt = time.perf_counter() - t0
+    # the same sub-lattice on one core, for a few steps
+    steps1 = int(max(1, min(steps, 0.25 * seconds / max(one * nthreads, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(a.lattice, a.K, a.tau, dims, f, steps1, 1)
+    dt1 = time.perf_counter() - t0
     return {"value": C * steps / dt / 1e6, "unit": "MLUPS", "cores": nthreads, "kind": "oracle",
             "sample": "%s K=%d tau=%g Taylor-Green sub-lattice %dx%dx%d, %d steps, %.1f s" % (
-                a.lattice, a.K, a.tau, dims[0], dims[1], dims[2], steps, dt)}
+                a.lattice, a.K, a.tau, dims[0], dims[1], dims[2], steps, dt),
+            "single_core": {"value": C * steps1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
+                            "sample": "the same sub-lattice, %d steps, %.1f s" % (steps1, dt1)}}
 
 
 # ------------------------------------------------------------------ clocks
