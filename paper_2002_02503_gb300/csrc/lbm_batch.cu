@@ -106,7 +106,8 @@ struct lbm_pool {
     int max_slots;
     cudaStream_t compute, io, capture;
     bool own_io;
-    int block, grid;
+    int block;
+    int grids[3];  // persistent grid of each slot-mode kernel
     int cpt;  // most cells per thread a slot may run (1 or 2)
     int qexp; // fixed-point storage: grid step 2^qexp
     // double-buffered slot tables
@@ -156,7 +157,7 @@ lbm_status get_graph(lbm_pool *p, long long chunk, int b, cudaGraphExec_t *out) 
     if (e != cudaSuccess) return set_cuda_error(e, "pool: begin capture");
     cudaError_t le = cudaSuccess;
     for (long long s = 0; s < chunk && le == cudaSuccess; ++s)
-        le = p->ks->batch(p->d_table[b], p->d_header[b], int(s), p->grid, p->block, p->cpt, p->capture);
+        le = p->ks->batch(p->d_table[b], p->d_header[b], int(s), p->grids, p->block, p->cpt, p->capture);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(p->capture, &g);
     if (le != cudaSuccess) {
@@ -179,49 +180,61 @@ void drop_graphs(lbm_pool *p) {
 }
 
 lbm_status set_geometry(lbm_pool *p, int block, int cpt) {
-    int occ = p->ks->batch_occupancy(block, cpt);
-    if (occ <= 0) return set_error(LBM_ERR_CUDA, "pool: batch kernel occupancy query failed");
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return set_cuda_error(e, "pool: device query");
+    int grids[3];
+    for (int m = 0; m < 3; ++m) {
+        const int occ = p->ks->batch_occupancy(block, m);
+        if (occ <= 0) return set_error(LBM_ERR_CUDA, "pool: batch kernel occupancy query failed");
+        grids[m] = occ * sms;
+    }
     p->block = block;
     p->cpt = cpt;
-    p->grid = occ * sms;
+    for (int m = 0; m < 3; ++m) p->grids[m] = grids[m];
     drop_graphs(p);
     return LBM_OK;
 }
 
-// Writes the table of resident requests with steps left into buffer b; returns slot count.
+// Slot mode of a request: one cell per thread, or two -- x-neighbours (row vectors) for
+// even nx, flat-index neighbours otherwise.
+int slot_mode(const lbm_pool *p, const Request &r) { return p->cpt == 1 ? 0 : (r.nx % 2 == 0 ? 1 : 2); }
+
+// Writes the table of resident requests with steps left into buffer b, grouped by slot mode
+// (each mode's kernel walks its own unit range); returns the slot count.
 int build_table(lbm_pool *p, int b, int *units_total) {
     int n = 0, units = 0;
-    for (int64_t id : p->order) {
-        Request &r = p->reqs[id];
-        const int64_t left = r.steps_total - r.steps_sched;
-        if (left <= 0) continue;
-        BatchSlot &s = p->h_table[b][n];
-        s.buf[0] = r.buf[0];
-        s.buf[1] = r.buf[1];
-        s.nx = r.nx;
-        s.ny = r.ny;
-        s.nz = r.nz;
-        // two cells per thread: x-neighbours (row vectors) for even nx, flat neighbours otherwise
-        s.mode = p->cpt == 1 ? 0 : (r.nx % 2 == 0 ? 1 : 2);
-        s.ncx = s.mode == 1 ? r.nx / 2 : r.nx;
-        s.threads = int(s.mode == 0 ? r.C : (r.C + 1) / 2);
-        s.P = r.C;
-        s.relax = r.relax;
-        s.rho0 = r.rho0;
-        s.parity = r.parity;
-        s.steps_left = int(std::min<int64_t>(left, 1 << 30));
-        s.unit0 = units;
-        s.units = int((s.threads + p->block - 1) / p->block);
-        s.qs = qscale_of_exponent(p->qexp);
-        s.status = r.status;
-        fastdiv_init(unsigned(s.ncx), &s.mx, &s.sx);
-        fastdiv_init(unsigned(r.ny), &s.my, &s.sy);
-        units += s.units;
-        ++n;
+    for (int m = 0; m < 3; ++m) {
+        p->h_header[b][2 + m] = units;
+        for (int64_t id : p->order) {
+            Request &r = p->reqs[id];
+            const int64_t left = r.steps_total - r.steps_sched;
+            if (left <= 0 || slot_mode(p, r) != m) continue;
+            BatchSlot &s = p->h_table[b][n];
+            s.buf[0] = r.buf[0];
+            s.buf[1] = r.buf[1];
+            s.nx = r.nx;
+            s.ny = r.ny;
+            s.nz = r.nz;
+            s.mode = m;
+            s.ncx = m == 1 ? r.nx / 2 : r.nx;
+            s.threads = int(m == 0 ? r.C : (r.C + 1) / 2);
+            s.P = r.C;
+            s.relax = r.relax;
+            s.rho0 = r.rho0;
+            s.parity = r.parity;
+            s.steps_left = int(std::min<int64_t>(left, 1 << 30));
+            s.unit0 = units;
+            s.units = int((s.threads + p->block - 1) / p->block);
+            s.qs = qscale_of_exponent(p->qexp);
+            s.status = r.status;
+            fastdiv_init(unsigned(s.ncx), &s.mx, &s.sx);
+            fastdiv_init(unsigned(r.ny), &s.my, &s.sy);
+            units += s.units;
+            ++n;
+        }
+        p->h_header[b][5 + m] = units;
     }
     p->h_header[b][0] = units;
     p->h_header[b][1] = n;
@@ -351,7 +364,8 @@ lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, 
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaMallocHost(reinterpret_cast<void **>(&p->h_table[b]), sizeof(BatchSlot) * max_slots);
-        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&p->h_header[b]), 2 * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMallocHost(reinterpret_cast<void **>(&p->h_header[b]), kBatchHeaderInts * sizeof(int));
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking);
     for (int k = 0; k < kEventRing && e == cudaSuccess; ++k)
@@ -487,7 +501,8 @@ lbm_status lbm_pool_advance(lbm_pool *p, int64_t chunk, int *active) {
     }
     e = cudaMemcpyAsync(p->d_table[b], p->h_table[b], sizeof(BatchSlot) * n, cudaMemcpyHostToDevice, p->compute);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], 2 * sizeof(int), cudaMemcpyHostToDevice, p->compute);
+        e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], kBatchHeaderInts * sizeof(int),
+                            cudaMemcpyHostToDevice, p->compute);
     if (e != cudaSuccess) return set_cuda_error(e, "pool: table upload");
     cudaGraphExec_t g;
     rs = get_graph(p, chunk, b, &g);
@@ -605,7 +620,8 @@ lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us) {
     cudaError_t e = cudaMemcpyAsync(p->d_table[b], p->h_table[b], sizeof(BatchSlot) * n, cudaMemcpyHostToDevice,
                                     p->compute);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], 2 * sizeof(int), cudaMemcpyHostToDevice, p->compute);
+        e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], kBatchHeaderInts * sizeof(int),
+                            cudaMemcpyHostToDevice, p->compute);
     for (int64_t id : p->order) {
         Request &r = p->reqs[id];
         if (!r.waited_init && e == cudaSuccess) e = cudaStreamWaitEvent(p->compute, r.init_event, 0);
@@ -623,12 +639,13 @@ lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us) {
         build_table(p, b, &units);  // units depend on the block size and the cells per thread
         e = cudaMemcpyAsync(p->d_table[b], p->h_table[b], sizeof(BatchSlot) * n, cudaMemcpyHostToDevice, p->compute);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], 2 * sizeof(int), cudaMemcpyHostToDevice, p->compute);
+            e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], kBatchHeaderInts * sizeof(int),
+                            cudaMemcpyHostToDevice, p->compute);
         for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grid, p->block, p->cpt, p->compute);
+            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grids, p->block, p->cpt, p->compute);
         if (e == cudaSuccess) e = cudaEventRecord(e0, p->compute);
         for (int it = 0; it < iters && e == cudaSuccess; ++it)
-            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grid, p->block, p->cpt, p->compute);
+            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grids, p->block, p->cpt, p->compute);
         if (e == cudaSuccess) e = cudaEventRecord(e1, p->compute);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -79,28 +79,31 @@ __device__ __forceinline__ void pull_collide_store_pair(const typename ST::S *__
 }
 
 // ------------------------------------------------------------------ batched step
-// Persistent kernel over the work units of every slot in a table (one unit =
-// blockDim.x consecutive threads of one lattice).  A slot runs in the mode its table
-// entry names: one cell per thread, or two -- x-neighbours with row vector loads for even
-// nx, consecutive cells of the flat index for odd nx -- whose collision runs on the paired
-// FP32 instructions.  A CTA serves one unit, so the mode is uniform across it and depends
-// only on the slot, never on the other residents.  One launch
-// advances every slot with step_index < steps_left by one step; the slot's buffers
-// alternate with its parity.  The table lives in device memory, so a captured graph
-// of launches stays valid while the host rewrites the table between chunks.
+// Persistent kernels over the work units of a slot table (one unit = blockDim.x consecutive
+// threads of one lattice).  The table is sorted by the slots' modes, and each mode has its
+// own kernel over its own range of units, so that each is register-allocated for one code
+// path: MODE 0 runs one cell per thread; MODE 1 two x-neighbours per thread (row vectors,
+// even nx); MODE 2 two consecutive cells of the flat index per thread (any nx).  Modes 1 and
+// 2 run the collision on the paired FP32 instructions.  A request's mode depends only on the
+// pool setting and its own nx, never on the other residents.  One launch per mode advances
+// every slot of that mode with step_index < steps_left by one step; the slot's buffers
+// alternate with its parity.  Header: [total units, slots, first unit of modes 0..2, end
+// unit of modes 0..2] (kBatchHeaderInts).  The table lives in device memory, so a captured
+// graph of launches stays valid while the host rewrites the table between chunks.
+
 __device__ __forceinline__ int fastdiv(int n, unsigned int m, unsigned int s) {
     return int((__umulhi((unsigned int)n, m) + (unsigned int)n) >> s);
 }
 
-template <class LT, int K, class ST, int VMAX>
+template <class LT, int K, class ST, int MODE>
 __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__restrict__ slots,
                                                          const int *__restrict__ header, int step_index) {
-    const int total_units = header[0];
     const int nslots = header[1];
+    const int u_begin = header[2 + MODE], u_end = header[5 + MODE];
     // grid-stride over units (neighbouring CTAs work on neighbouring rows at the same time);
     // units only increase, so each thread walks the slot index forward without a barrier
     int slot = 0;
-    for (int unit = blockIdx.x; unit < total_units; unit += gridDim.x) {
+    for (int unit = u_begin + int(blockIdx.x); unit < u_end; unit += gridDim.x) {
         if (slot + 1 < nslots && slots[slot + 1].unit0 <= unit) {
             int lo = slot + 1, hi = nslots - 1;  // last slot with unit0 <= unit
             while (lo < hi) {
@@ -118,44 +121,49 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__rest
         const auto *src = static_cast<const typename ST::S *>(sl.buf[cur]);
         auto *dst = static_cast<typename ST::S *>(sl.buf[cur ^ 1]);
         const typename ST::T relax(sl.relax), rho0(sl.rho0), kq(0);
-        if (VMAX == 2 && sl.mode == 2) {
+        if constexpr (MODE == 2) {
             if (t >= total) continue;  // no warp collectives on this path
             const int c0 = 2 * t;
             const int row = fastdiv(c0, sl.mx, sl.sx);  // c0 / nx
             const int z = fastdiv(row, sl.my, sl.sy);
             pull_collide_store_pair<LT, K, ST>(src, dst, sl.nx, sl.ny, sl.nz, sl.P, c0 - row * sl.nx, row - z * sl.ny,
                                                z, (long long)c0 + 1 < sl.P, relax, rho0, sl.qs, sl.status);
-            continue;
+        } else {
+            const bool active = t < total;
+            if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
+            const int row = fastdiv(t, sl.mx, sl.sx);  // t / ncx
+            const int chunk = t - row * sl.ncx;
+            const int z = fastdiv(row, sl.my, sl.sy);
+            const int y = row - z * sl.ny;
+            pull_collide_store<LT, K, ST, MODE == 1 ? 2 : 1>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk,
+                                                             active, relax, rho0, kq, sl.qs, sl.status);
         }
-        const bool active = t < total;
-        if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
-        const int row = fastdiv(t, sl.mx, sl.sx);  // t / ncx
-        const int chunk = t - row * sl.ncx;
-        const int z = fastdiv(row, sl.my, sl.sy);
-        const int y = row - z * sl.ny;
-        if (VMAX == 2 && sl.mode == 1)
-            pull_collide_store<LT, K, ST, VMAX>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk, active, relax,
-                                                rho0, kq, sl.qs, sl.status);
-        else
-            pull_collide_store<LT, K, ST, 1>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk, active, relax,
-                                             rho0, kq, sl.qs, sl.status);
     }
 }
 
+// One step of every slot: the MODE 0 kernel with one cell per thread (cpt = 1), else the
+// MODE 1 and MODE 2 kernels; grids[m] is mode m's persistent grid.
 template <class LT, int K, class ST>
-cudaError_t launch_batch(const BatchSlot *slots, const int *header, int step_index, int grid, int block, int cpt,
-                         cudaStream_t stream) {
-    if (cpt == 2) batch_step_kernel<LT, K, ST, 2><<<grid, block, 0, stream>>>(slots, header, step_index);
-    else batch_step_kernel<LT, K, ST, 1><<<grid, block, 0, stream>>>(slots, header, step_index);
+cudaError_t launch_batch(const BatchSlot *slots, const int *header, int step_index, const int *grids, int block,
+                         int cpt, cudaStream_t stream) {
+    if (cpt == 2) {
+        batch_step_kernel<LT, K, ST, 1><<<grids[1], block, 0, stream>>>(slots, header, step_index);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        batch_step_kernel<LT, K, ST, 2><<<grids[2], block, 0, stream>>>(slots, header, step_index);
+    } else {
+        batch_step_kernel<LT, K, ST, 0><<<grids[0], block, 0, stream>>>(slots, header, step_index);
+    }
     return cudaGetLastError();
 }
 
 template <class LT, int K, class ST>
-int batch_occupancy(int block, int cpt) {
+int batch_occupancy(int block, int mode) {
     int n = 0;
-    cudaError_t e = cpt == 2
-                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 2>, block, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 1>, block, 0);
+    cudaError_t e;
+    if (mode == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 2>, block, 0);
+    else if (mode == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 1>, block, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 0>, block, 0);
     return e == cudaSuccess ? n : 0;
 }
 

@@ -108,6 +108,10 @@ struct BatchSlot {
     unsigned int *status;         // this request's status word (kStatusRange)
 };
 
+// Header of a slot table: total units, slots, first unit of slot modes 0..2, end unit of
+// slot modes 0..2.
+constexpr int kBatchHeaderInts = 8;
+
 // Division by a runtime constant d (1 <= d < 2^31) as q = (umulhi(n, m) + n) >> s for
 // 0 <= n < 2^31 -- the round-up multiply-and-shift method of Granlund and Montgomery (1994):
 // s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1, so that (m + 2^32) / 2^(32+s) exceeds 1/d by
@@ -120,8 +124,8 @@ inline void fastdiv_init(unsigned int d, unsigned int *m, unsigned int *s) {
 }
 
 typedef cudaError_t (*step_fn)(const StepArgs &, int block_threads, cudaStream_t);
-typedef cudaError_t (*batch_fn)(const BatchSlot *slots, const int *header, int step_index, int grid, int block,
-                                int cells_per_thread, cudaStream_t);
+typedef cudaError_t (*batch_fn)(const BatchSlot *slots, const int *header, int step_index, const int *grids,
+                                int block, int cells_per_thread, cudaStream_t);
 typedef cudaError_t (*init_fn)(const InitArgs &, cudaStream_t);
 typedef cudaError_t (*pull_fn)(const PullArgs &, cudaStream_t);
 typedef cudaError_t (*reduce_fn)(const ReduceArgs &, cudaStream_t);
@@ -136,7 +140,7 @@ struct KernelSet {
     reduce_fn conservation;  // nvals = 4
     reduce_fn mode;          // nvals = 2
     batch_fn batch;          // persistent multi-lattice step (1 or at most 2 cells per thread)
-    int (*batch_occupancy)(int block, int cells_per_thread);
+    int (*batch_occupancy)(int block, int mode);  // blocks per SM of the slot-mode kernel
     step_fn bgk;             // BGK comparison operator, register pull with V = 1
     step_fn theta;           // filtered collision with the energy-flux term (K >= 3), V = 1
     bool (*staged_applies)(int nx);  // variant 1 needs nx * sizeof(storage) % 16 == 0 and a fitting tile
