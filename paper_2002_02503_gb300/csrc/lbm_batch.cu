@@ -105,7 +105,6 @@ struct lbm_pool {
     Arena arena;
     int max_slots;
     cudaStream_t compute, io, capture;
-    bool own_io;
     int block;
     int grids[3];  // persistent grid of each slot-mode kernel
     int cpt;  // most cells per thread a slot may run (1 or 2)
@@ -115,7 +114,6 @@ struct lbm_pool {
     int *d_header[2];
     BatchSlot *h_table[2];
     int *h_header[2];
-    void *d_meta;  // one allocation-free region: carved from the arena's tail
     std::map<int64_t, Request> reqs;
     std::vector<int64_t> order;       // resident request ids in admission order
     int64_t next_id;
@@ -348,7 +346,6 @@ lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, 
     p->max_slots = max_slots;
     p->compute = static_cast<cudaStream_t>(compute_stream);
     p->io = static_cast<cudaStream_t>(io_stream);
-    p->own_io = false;
     p->next_id = 1;
     p->chunks = 0;
     p->completed = 0;
