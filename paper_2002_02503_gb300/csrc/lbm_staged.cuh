@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdlib.h>
 
+#include <atomic>
+
 #include "lbm_core.cuh"
 #include "lbm_internal.h"
 
@@ -273,17 +275,17 @@ cudaError_t launch_step_staged(const StepArgs &a, int block, cudaStream_t stream
     staged_geometry<LT, ST>(a.nx, &R, &S, &smem, &threads);
     if (R == 0) return cudaErrorInvalidValue;
     // opt in to large dynamic shared memory once per device (the attribute is per device)
-    static unsigned long long configured = 0;
+    static std::atomic<unsigned long long> configured{0};  // solvers on other threads share it
     {
         int cur = 0;
         cudaError_t e = cudaGetDevice(&cur);
         if (e != cudaSuccess) return e;
         const unsigned long long bit = cur < 64 ? (1ull << cur) : 0ull;
-        if (!bit || !(configured & bit)) {
+        if (!bit || !(configured.load() & bit)) {
             e = cudaFuncSetAttribute(step_staged_kernel<LT, K, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      227 * 1024);
             if (e != cudaSuccess) return e;
-            configured |= bit;
+            configured.fetch_or(bit);
         }
     }
     // LBM_TEST_STAGED_EXTRA_TX=<bytes>: test hook that makes every CTA's first wait expire (read once)
