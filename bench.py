@@ -61,42 +61,69 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=50.0)
     p.add_argument("--extra-steps", type=int, default=200)
     p.add_argument("--precision-report", action="store_true",
-                   help="D3Q19 512^3 Taylor-Green tau=0.52, 500 steps: FP32/FP16/BF16/Q16 storage against FP64 "
-                        "storage")
+                   help="error of every storage form against FP64 storage on the headline, Galilean-invariance "
+                        "and 512^3 workloads")
     return p.parse_args()
 
 
+# (label, lattice, dims, K, tau, fields, steps, fixed-point range): the precision report's workloads.
+# fields: ("tg", u0) = Taylor-Green; ("shear", U) = u_y = 0.01 sin(2 pi x / n) on a background U_x.
+PRECISION_CONFIGS = [
+    ("D3Q19 256^3 Taylor-Green u0=0.05 tau=0.55 K=2, 1000 steps", "D3Q19", (256, 256, 256), 2, 0.55,
+     ("tg", 0.05), 1000, 0.25),
+    ("D3Q27 192^3 shear wave 0.01 on U_x=0.1, tau=0.6 K=3, 2000 steps", "D3Q27", (192, 192, 192), 3, 0.6,
+     ("shear", 0.1), 2000, 0.5),
+    ("D3Q39 192^3 shear wave 0.01 on U_x=0.1, tau=0.6 K=4, 2000 steps", "D3Q39", (192, 192, 192), 4, 0.6,
+     ("shear", 0.1), 2000, 1.0),
+    ("D3Q19 512^3 Taylor-Green u0=0.05 tau=0.52 K=2, 500 steps", "D3Q19", (512, 512, 512), 2, 0.52,
+     ("tg", 0.05), 500, 0.25),
+]
+
+
 def precision_report(stream):
-    """Relative u and rho errors of the FP32, FP16, BF16 and 16-bit fixed-point (range 1/4) storage
-    forms after 500 steps of the
-    D3Q19 512^3 Taylor-Green vortex (u0 = 0.05, tau = 0.52, K = 2), measured against the same run
-    with FP64 storage and arithmetic (the FP64 oracle is too slow for this size; the FP64 path
-    matches it within 1e-12 on the parity cases)."""
+    """Errors of the FP32, FP16, BF16 and 16-bit fixed-point storage forms on each workload of
+    PRECISION_CONFIGS, against the same run with FP64 storage and arithmetic (the FP64 oracle is
+    too slow for these sizes; the library's FP64 path matches it within 1e-12 on the parity
+    cases).  Taylor-Green: max|du| / max|u| and max|drho| / rho.  Shear wave: the same for the
+    decaying component u_y, and the relative error of its Fourier amplitude at k = 1 (the
+    quantity the decay-rate fit uses)."""
     import torch
 
     from paper_2002_02503_gb300 import fields, lbm
 
-    dims = (512, 512, 512)
-    rho, u = fields.taylor_green_3d(dims, 0.05, 1.0 / 3.0)
-    out = {}
-    ref = None
-    for storage in ("f64", "f32", "f16", "bf16", "q16"):
-        s = lbm.Solver("D3Q19", dims, 0.52, 2, storage, stream=stream,
-                       storage_range=Q16_RANGE if storage == "q16" else None)
-        s.set_fields(rho, u)
-        s.step(500)
-        r, uu = s.moments()
-        s.close()
-        del s
-        torch.cuda.empty_cache()
-        if ref is None:
-            ref = (r, uu)
-            continue
-        out[storage] = {"rel_u": float(np.max(np.abs(uu - ref[1])) / np.max(np.abs(ref[1]))),
-                        "rel_rho": float(np.max(np.abs(r - ref[0]) / ref[0]))}
-        del r, uu
-    return {"workload": "D3Q19 512^3 Taylor-Green u0=0.05 tau=0.52 K=2, 500 steps",
-            "reference": "FP64 storage and arithmetic (same library)", "errors": out}
+    report = []
+    for label, lat, dims, K, tau, (kind, amp), steps, q_range in PRECISION_CONFIGS:
+        if kind == "tg":
+            rho, u = fields.taylor_green_3d(dims, amp, LATTICE_T0[lat])
+        else:
+            rho, u = fields.shear_wave(dims, 0.01, 3, 1, 0, background=(amp, 0.0, 0.0))
+        out, ref = {}, None
+        for storage in ("f64", "f32", "f16", "bf16", "q16"):
+            s = lbm.Solver(lat, dims, tau, K, storage, stream=stream,
+                           storage_range=q_range if storage == "q16" else None)
+            s.set_fields(rho, u)
+            s.step(steps)
+            r, uu = s.moments()
+            mode = s.mode((1, 0, 0), 1) if kind == "shear" else None
+            s.close()
+            del s
+            torch.cuda.empty_cache()
+            if kind == "shear":
+                uu = uu[1]
+            if ref is None:
+                ref = (r, uu, mode)
+                continue
+            e = {"rel_u": float(np.max(np.abs(uu - ref[1])) / np.max(np.abs(ref[1]))),
+                 "rel_rho": float(np.max(np.abs(r - ref[0]) / ref[0]))}
+            if kind == "shear":
+                e["rel_mode_amplitude"] = float(abs(abs(mode) - abs(ref[2])) / abs(ref[2]))
+            if storage == "q16":
+                e["range"] = q_range
+            out[storage] = e
+            del r, uu
+        report.append({"workload": label, "errors": out})
+        del rho, u
+    return {"reference": "FP64 storage and arithmetic (same library)", "configs": report}
 
 
 # (lattice, dims, K, storage, tau, u0): the other lattices and storages of the workload family
