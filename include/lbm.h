@@ -146,11 +146,14 @@ lbm_status lbm_set_distributions(lbm_solver *s, const void *src, size_t bytes, l
 lbm_status lbm_time(const lbm_solver *s, int64_t *t);
 
 /* Kernel configuration of the step.  variant: 0 = register pull (vector loads
- * plus warp shuffles for the x shift), 1 = persistent shared-memory row
- * staging through bulk asynchronous copies.  cells_per_thread: 1, 2, 4 or 8 (must
- * divide nx).  block_threads: 32..1024, a multiple of 32.  A negative variant
- * and a zero cells_per_thread or block_threads keep the current setting.
- * LBM_ERR_UNSUPPORTED if the combination is not built. */
+ * plus warp shuffles for the x shift; cells_per_thread 1, 2, 4 or 8 x-neighbours, which
+ * must divide nx), 1 = persistent shared-memory row staging through bulk asynchronous
+ * copies (cells_per_thread 1), 2 = two consecutive cells of the flat index per thread with
+ * direct loads (cells_per_thread 2, any nx: the paired collision for odd nx).  The
+ * collision runs on the paired FP32 instructions whenever a thread holds two or more cells.
+ * block_threads: 32..1024, a multiple of 32.  A negative variant and a zero
+ * cells_per_thread or block_threads keep the current setting.  LBM_ERR_UNSUPPORTED if the
+ * combination is not built (BGK and the energy-flux term run variant 0 with one cell). */
 lbm_status lbm_set_kernel(lbm_solver *s, int variant, int cells_per_thread, int block_threads);
 lbm_status lbm_get_kernel(const lbm_solver *s, int *variant, int *cells_per_thread, int *block_threads);
 

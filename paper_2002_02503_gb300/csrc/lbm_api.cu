@@ -202,6 +202,7 @@ step_fn step_for(const lbm_solver *s, int variant, int V) {
     }
     if (variant == 1)
         return (s->ks->staged && s->ks->staged_applies && s->ks->staged_applies(s->nx)) ? s->ks->staged : nullptr;
+    if (variant == 2) return V == 2 ? s->ks->pair : nullptr;  // two cells of the flat index per thread
     return nullptr;
 }
 
@@ -754,6 +755,8 @@ lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us) {
         for (int b : {128, 256})
             if (step_for(s, 0, V) && nc < 16) cands[nc++] = Cand{0, V, b};
     if (s->ks->staged && nc < 16) cands[nc++] = Cand{1, 1, s->ks->staged_block};
+    for (int b : {128, 256})
+        if (step_for(s, 2, 2) && nc < 16) cands[nc++] = Cand{2, 2, b};
     lbm_status rc = LBM_OK;
     for (int k = 0; k < nc && rc == LBM_OK; ++k) {
         step_fn fn = step_for(s, cands[k].variant, cands[k].V);

@@ -78,6 +78,44 @@ __device__ __forceinline__ void pull_collide_store_pair(const typename ST::S *__
     }
 }
 
+// Single-lattice step on flat cell pairs (step variant 2): thread t updates cells 2t and
+// 2t + 1 of the flat index, for any nx -- the variant that gives odd-sized lattices the
+// paired collision.  Grid-stride over ceil(C / 2) pairs.
+template <class LT, int K, class ST>
+__global__ void __launch_bounds__(256) step_pair_kernel(const typename ST::S *__restrict__ src,
+                                                        typename ST::S *__restrict__ dst, int nx, int ny, int nz,
+                                                        long long P, typename ST::T relax, typename ST::T rho0,
+                                                        QScale qs, unsigned int *__restrict__ status) {
+    const long long pairs = (P + 1) / 2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < pairs;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long c0 = 2 * t;
+        const long long row = c0 / nx;
+        const int z = int(row / ny);
+        pull_collide_store_pair<LT, K, ST>(src, dst, nx, ny, nz, P, int(c0 - row * nx), int(row - (long long)z * ny),
+                                           z, c0 + 1 < P, relax, rho0, qs, status);
+    }
+}
+
+template <class LT, int K, class ST>
+cudaError_t launch_step_pair(const StepArgs &a, int block, cudaStream_t stream) {
+    using T = typename ST::T;
+    if (block <= 0 || block > 256) block = 256;  // __launch_bounds__(256)
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_pair_kernel<LT, K, ST>, block, 0);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long pairs = (a.P + 1) / 2;
+    long long grid = (pairs + block - 1) / block;
+    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * sms * 8;  // a few waves, then stride
+    if (grid > cap) grid = cap;
+    step_pair_kernel<LT, K, ST><<<(unsigned)grid, block, 0, stream>>>(
+        static_cast<const typename ST::S *>(a.src), static_cast<typename ST::S *>(a.dst), a.nx, a.ny, a.nz, a.P,
+        T(a.relax), T(a.rho0), a.qs, a.status);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ batched step
 // Persistent kernels over the work units of a slot table (one unit = blockDim.x consecutive
 // threads of one lattice).  The table is sorted by the slots' modes, and each mode has its

@@ -540,6 +540,7 @@ const KernelSet *make_kernel_set() {
         &launch_step_direct<LT, K, ST, 1, true>,
         theta_if_built<LT, K, ST>(),
         staged_check_if_built<LT, ST>(),
+        &launch_step_pair<LT, K, ST>,
     };
     return &ks;
 }

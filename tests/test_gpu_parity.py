@@ -9,8 +9,8 @@ import pytest
 import oracle
 from paper_2002_02503_gb300 import fields, lbm
 
-from _lbmtest import (DIMS, TOL_F32, TOL_F64, oracle_reference, perm_lib_to_oracle, raw_from_f, rel_f, rel_u,
-                      to_lib_order)
+from _lbmtest import (DIMS, TOL_F32, TOL_F64, TOL_U16, oracle_reference, perm_lib_to_oracle, raw_from_f, rel_f,
+                      rel_u, to_lib_order)
 
 pytestmark = pytest.mark.gpu
 
@@ -108,6 +108,8 @@ def _built_variants(name, K, storage, nx):
         out.append((1, 1, 256))
     except lbm.LbmError:
         pass
+    lbm.lbm_set_kernel(s.handle, 2, 2, 128)  # flat cell pairs: built for every lattice and storage
+    out.append((2, 2, 128))
     s.close()
     return out
 
@@ -374,3 +376,25 @@ def test_steps_are_bitwise_deterministic(variant, storage):
         raws.append(raw)
         s.close()
     np.testing.assert_array_equal(raws[0], raws[1])
+
+
+@pytest.mark.parametrize("name,K,storage,dims", [("D3Q19", 3, "f32", (33, 19, 13)), ("D3Q19", 2, "f16", (45, 23, 9)),
+                                                 ("D3Q39", 4, "f32", (29, 17, 11)), ("D2Q9", 3, "f32", (71, 45, 1)),
+                                                 ("D3Q27", 3, "q16", (31, 21, 15)), ("D3Q15", 2, "f64", (25, 13, 7))])
+def test_flat_pair_variant_on_odd_lattices(name, K, storage, dims):
+    """Step variant 2 (two consecutive cells of the flat index per thread, any nx; the last
+    thread of an odd cell count holds one cell) against the oracle on odd-sized lattices."""
+    D = lbm.lbm_lattice_info(name)["D"]
+    rho, u = fields.random_smooth_fields(dims, D, salt=90)
+    f_ref, r_ref, u_ref = oracle_reference(name, K, 0.6, dims, rho, u, 30)
+    s = lbm.Solver(name, dims, 0.6, K, storage, storage_range=0.5 if storage == "q16" else None)
+    lbm.lbm_set_kernel(s.handle, 2, 2, 256)
+    assert lbm.lbm_get_kernel(s.handle)[:2] == (2, 2)
+    s.set_fields(rho, u)
+    s.step(30)
+    r, uu = s.moments()
+    f = s.f()
+    s.close()
+    tol = {"f32": TOL_F32, "f64": TOL_F64, "f16": 2e-3, "q16": TOL_U16}[storage]
+    assert rel_u(uu, u_ref) < tol
+    assert rel_f(f, to_lib_order(name, f_ref)) < tol
