@@ -754,12 +754,13 @@ lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us) {
     for (int V : {1, 2, 4, 8})
         for (int b : {128, 256})
             if (step_for(s, 0, V) && nc < 16) cands[nc++] = Cand{0, V, b};
-    if (s->ks->staged && nc < 16) cands[nc++] = Cand{1, 1, s->ks->staged_block};
+    if (step_for(s, 1, 1) && nc < 16) cands[nc++] = Cand{1, 1, s->ks->staged_block};  // where it applies
     for (int b : {128, 256})
         if (step_for(s, 2, 2) && nc < 16) cands[nc++] = Cand{2, 2, b};
     lbm_status rc = LBM_OK;
     for (int k = 0; k < nc && rc == LBM_OK; ++k) {
         step_fn fn = step_for(s, cands[k].variant, cands[k].V);
+        if (!fn) continue;  // every candidate was checked above; kept as a guard
         cudaError_t e = cudaSuccess;
         for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = fn(a, cands[k].block, s->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s->stream);

@@ -398,3 +398,23 @@ def test_flat_pair_variant_on_odd_lattices(name, K, storage, dims):
     tol = {"f32": TOL_F32, "f64": TOL_F64, "f16": 2e-3, "q16": TOL_U16}[storage]
     assert rel_u(uu, u_ref) < tol
     assert rel_f(f, to_lib_order(name, f_ref)) < tol
+
+
+@pytest.mark.parametrize("storage,dims", [("f32", (45, 23, 9)), ("f16", (33, 19, 13)), ("q16", (31, 17, 11))])
+def test_autotune_on_odd_widths(storage, dims):
+    """Odd nx rules out the x-vector widths and the staged variant (its rows are not 16-byte
+    multiples); the autotuner must consider only what applies and leave the state unchanged."""
+    rho, u = fields.random_smooth_fields(dims, 3, salt=91)
+    f_ref, r_ref, u_ref = oracle_reference("D3Q19", 3, 0.6, dims, rho, u, 12)
+    s = lbm.Solver("D3Q19", dims, 0.6, 3, storage, storage_range=0.5 if storage == "q16" else None)
+    s.set_fields(rho, u)
+    s.step(6)
+    us = lbm.lbm_autotune(s.handle, 2)
+    assert us > 0
+    variant, cpt, _ = lbm.lbm_get_kernel(s.handle)
+    assert (variant, cpt) in ((0, 1), (2, 2))
+    s.step(6)
+    r, uu = s.moments()
+    s.close()
+    tol = {"f32": TOL_F32, "f16": 2e-3, "q16": TOL_U16}[storage]
+    assert rel_u(uu, u_ref) < tol
