@@ -1,6 +1,7 @@
-// lbm_batch_kernels.cuh -- the batched multi-lattice step of the pools: flat cell pairs
-// and the persistent kernel over a device slot table.  Included by lbm_kernels.cuh after
-// the register-pull step (pull_collide_store), which it reuses.
+// lbm_batch_kernels.cuh -- flat cell pairs (two consecutive cells of the flat index per
+// thread, any nx), the single-lattice step built on them (variant 2), and the batched
+// multi-lattice step of the pools: persistent kernels over a device slot table.  Included
+// by lbm_kernels.cuh after the register-pull step (pull_collide_store), which it reuses.
 #pragma once
 
 namespace lbm {
