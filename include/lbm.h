@@ -185,7 +185,10 @@ lbm_status lbm_get_storage_range(const lbm_solver *s, double *range);
 /* Autotuner: times every built kernel configuration for this solver on its own
  * buffers (reads the current state, writes only the idle buffer, so the state is
  * unchanged) over `iters` launches each and keeps the fastest.  best_us, if not
- * NULL, receives the average step time of the chosen configuration. */
+ * NULL, receives the average step time of the chosen configuration.  With the
+ * environment variable LBM_AUTOTUNE_CACHE naming a file, a choice stored there for the
+ * same device, lattice, K, storage, dims and collision mode is applied without timing
+ * (best_us then reports the stored time), and a new choice is appended to the file. */
 lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us);
 
 /* Global FP64 sums {sum rho, sum rho u_x, sum rho u_y, sum rho u_z} of stored

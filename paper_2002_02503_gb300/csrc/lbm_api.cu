@@ -13,7 +13,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "lbm_internal.h"
@@ -736,10 +739,73 @@ lbm_status lbm_get_kernel(const lbm_solver *s, int *variant, int *V, int *block)
     return LBM_OK;
 }
 
+// Autotuner cache (LBM_AUTOTUNE_CACHE=<file>): one line per tuned problem,
+//   <key> <variant> <cells_per_thread> <block> <us per step>
+// keyed by device name, lattice, K, storage, dims and collision mode.  Lines are appended;
+// the last one for a key wins.  A process-wide mutex orders this process's readers and writers.
+namespace {
+std::mutex g_tune_cache_mu;
+
+std::string tune_key(const lbm_solver *s) {
+    cudaDeviceProp prop;
+    int dev = 0;
+    std::string name = "gpu";
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char &c : name)
+        if (c == ' ') c = '_';
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s|L%d|K%d|S%d|%dx%dx%d|M%d|T%d", name.c_str(), int(s->lat), s->K, int(s->st), s->nx,
+             s->ny, s->nz, int(s->model), s->theta != 0.0 ? 1 : 0);
+    return buf;
+}
+
+bool tune_cache_lookup(const char *path, const std::string &key, int *variant, int *V, int *block, double *us) {
+    std::lock_guard<std::mutex> lock(g_tune_cache_mu);
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char k[256];
+    int v, c, b;
+    double t;
+    bool found = false;
+    while (fscanf(f, "%255s %d %d %d %lf", k, &v, &c, &b, &t) == 5)
+        if (key == k) {
+            *variant = v;
+            *V = c;
+            *block = b;
+            *us = t;
+            found = true;
+        }
+    fclose(f);
+    return found;
+}
+
+void tune_cache_store(const char *path, const std::string &key, int variant, int V, int block, double us) {
+    std::lock_guard<std::mutex> lock(g_tune_cache_mu);
+    FILE *f = fopen(path, "a");
+    if (!f) return;  // the cache is an optimisation: a file that cannot be written is skipped
+    fprintf(f, "%s %d %d %d %.3f\n", key.c_str(), variant, V, block, us);
+    fclose(f);
+}
+}  // namespace
+
 lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us) {
     LBM_NVTX_RANGE("lbm_autotune");
     if (lbm_status r = check_solver(s)) return r;
     if (iters < 1) iters = 1;
+    const char *cache = getenv("LBM_AUTOTUNE_CACHE");
+    const std::string key = cache && *cache ? tune_key(s) : std::string();
+    if (!key.empty()) {
+        int v = 0, V = 0, b = 0;
+        double us = 0.0;
+        if (tune_cache_lookup(cache, key, &v, &V, &b, &us) && step_for(s, v, V) && b >= 32 && b <= 1024 &&
+            b % 32 == 0) {
+            s->variant = v;
+            s->V = V;
+            s->block = b;
+            if (best_us) *best_us = us;
+            return LBM_OK;
+        }
+    }
     cudaEvent_t e0, e1;
     LBM_CUDA(cudaEventCreate(&e0), "autotune: event");
     LBM_CUDA(cudaEventCreate(&e1), "autotune: event");
@@ -787,6 +853,7 @@ lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us) {
     s->V = bV;
     s->block = bb;
     if (best_us) *best_us = 1000.0 * best / iters;
+    if (!key.empty()) tune_cache_store(cache, key, bv, bV, bb, 1000.0 * best / iters);
     return LBM_OK;
 }
 

@@ -418,3 +418,30 @@ def test_autotune_on_odd_widths(storage, dims):
     s.close()
     tol = {"f32": TOL_F32, "f16": 2e-3, "q16": TOL_U16}[storage]
     assert rel_u(uu, u_ref) < tol
+
+
+def test_autotune_cache_file(tmp_path, monkeypatch):
+    """LBM_AUTOTUNE_CACHE: the first autotune of a problem appends its choice to the file; a later
+    solver of the same problem takes that choice without timing, and another problem tunes anew."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("LBM_AUTOTUNE_CACHE", str(path))
+    dims = (64, 24, 16)
+    rho, u = fields.random_smooth_fields(dims, 3, salt=92)
+    a = lbm.Solver("D3Q19", dims, 0.6, 3, "f32")
+    a.set_fields(rho, u)
+    us = lbm.lbm_autotune(a.handle, 2)
+    chosen = lbm.lbm_get_kernel(a.handle)
+    a.close()
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].split()[1:4] == [str(x) for x in chosen]
+    b = lbm.Solver("D3Q19", dims, 0.6, 3, "f32")
+    b.set_fields(rho, u)
+    assert lbm.lbm_autotune(b.handle, 2) == pytest.approx(us, rel=1e-3)
+    assert lbm.lbm_get_kernel(b.handle) == chosen
+    b.close()
+    assert len(path.read_text().splitlines()) == 1
+    c = lbm.Solver("D3Q19", dims, 0.6, 2, "f32")  # another truncation order: another key
+    c.set_fields(rho, u)
+    lbm.lbm_autotune(c.handle, 2)
+    c.close()
+    assert len(path.read_text().splitlines()) == 2
