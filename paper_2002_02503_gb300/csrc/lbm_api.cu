@@ -385,6 +385,8 @@ lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm
     a.rho0 = s->rho0;
     a.qs = qscale_of_exponent(s->qexp);
     a.status = s->status;
+    // the state is replaced: events recorded for the old one no longer apply
+    LBM_CUDA(cudaMemsetAsync(s->status, 0, sizeof(unsigned int), s->stream), "set_fields: status word");
     if (mem == LBM_MEM_DEVICE) {
         a.rho = rho;
         a.u = u;
@@ -621,7 +623,9 @@ lbm_status lbm_get_distributions(lbm_solver *s, void *dst, size_t bytes, lbm_mem
     LBM_NVTX_RANGE("lbm_get_distributions");
     if (lbm_status r = check_solver(s)) return r;
     if (!dst) return fail(LBM_ERR_INVALID_ARG, "dst is NULL");
+    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return fail(LBM_ERR_INVALID_ARG, "bad lbm_mem");
     if (bytes != s->buf_bytes) return fail(LBM_ERR_INVALID_ARG, "bytes must be %zu", s->buf_bytes);
+    if (lbm_status st = check_device_status(s)) return st;  // no checkpoint of a state known to be invalid
     LBM_CUDA(cudaMemcpyAsync(dst, s->buf[s->cur], bytes,
                              mem == LBM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s->stream),
              "get_distributions: copy");
@@ -634,8 +638,11 @@ lbm_status lbm_set_distributions(lbm_solver *s, const void *src, size_t bytes, l
     LBM_NVTX_RANGE("lbm_set_distributions");
     if (lbm_status r = check_solver(s)) return r;
     if (!src) return fail(LBM_ERR_INVALID_ARG, "src is NULL");
+    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return fail(LBM_ERR_INVALID_ARG, "bad lbm_mem");
     if (bytes != s->buf_bytes) return fail(LBM_ERR_INVALID_ARG, "bytes must be %zu", s->buf_bytes);
     if (t < 0) return fail(LBM_ERR_INVALID_ARG, "t must be >= 0");
+    // the state is replaced: events recorded for the old one no longer apply
+    LBM_CUDA(cudaMemsetAsync(s->status, 0, sizeof(unsigned int), s->stream), "set_distributions: status word");
     LBM_CUDA(cudaMemcpyAsync(s->buf[0], src, bytes,
                              mem == LBM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s->stream),
              "set_distributions: copy");

@@ -353,3 +353,29 @@ def test_checkpoint_round_trip_in_fixed_point():
     pool = lbm.Pool("D3Q19", 2, "q16", 1 << 24, 4, storage_range=2.0 ** -3)
     assert lbm.lbm_pool_get_storage_range(pool.handle) == 0.125
     pool.close()
+
+
+def test_range_report_belongs_to_the_state_it_came_from():
+    """A range exit is reported once, by the next synchronising call (a checkpoint read included);
+    replacing the state (set_fields, set_distributions) starts with a clean record."""
+    rho_b, u_b = _converging_pair(8, 0.074)
+    s = lbm.Solver("D3Q19", (8, 8, 8), 0.51, 2, "q16", storage_range=0.25)
+    s.set_fields(rho_b, u_b)
+    s.step(3)  # leaves the range
+    raw = np.empty(s.raw_bytes(), dtype=np.uint8)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_get_distributions(s.handle, raw)
+    assert e.value.status == lbm.LBM_ERR_RANGE
+    s.step(3)  # leaves it again (garbage in, flagged out)
+    rho, u = fields.taylor_green_3d((8, 8, 8), 0.02, 1.0 / 3.0)
+    s.set_fields(rho, u)  # a new state: the pending report is dropped, not blamed on it
+    s.step(2)
+    s.moments()
+    good = np.empty_like(raw)
+    lbm.lbm_get_distributions(s.handle, good)
+    s.set_fields(rho_b, u_b)
+    s.step(3)
+    lbm.lbm_set_distributions(s.handle, good, 2)  # restoring a valid checkpoint also starts clean
+    s.step(1)
+    s.moments()
+    s.close()
