@@ -138,7 +138,10 @@ lbm_status lbm_conservation(lbm_solver *s, double out[4]);
 lbm_status lbm_mode_amplitude(lbm_solver *s, const int64_t k[3], int component, double out[2]);
 
 /* Checkpoint: the raw stored distributions (bytes = Q*C*sizeof(storage)) and
- * the step counter.  get synchronises; set replaces the state. */
+ * the step counter.  get synchronises and, like the other synchronising calls, first
+ * reports a pending status (LBM_ERR_RANGE, LBM_ERR_TIMEOUT) instead of saving a state known
+ * to be invalid; set replaces the state and clears any pending status of the old one (so
+ * does lbm_set_fields).  A fixed-point checkpoint restores under the range it was taken with. */
 lbm_status lbm_get_distributions(lbm_solver *s, void *dst, size_t bytes, lbm_mem mem, int64_t *t);
 lbm_status lbm_set_distributions(lbm_solver *s, const void *src, size_t bytes, lbm_mem mem, int64_t t);
 
