@@ -121,7 +121,7 @@ struct lbm_pool {
     long long completed;              // all chunks < completed are known done
     cudaEvent_t chunk_events[kEventRing];
     std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;  // (chunk length, table buffer)
-    std::mutex mu;
+    mutable std::mutex mu;  // every entry point holds it: a pool serialises its own calls
 };
 
 namespace {
@@ -590,6 +590,7 @@ lbm_status lbm_pool_sync(lbm_pool *p) {
 
 lbm_status lbm_pool_stats(const lbm_pool *p, size_t *free_bytes, int *resident, int *done) {
     if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    std::lock_guard<std::mutex> lock(p->mu);
     if (free_bytes) *free_bytes = p->arena.free_bytes();
     int res = 0, dn = 0;
     for (auto &kv : p->reqs) {
@@ -682,6 +683,7 @@ lbm_status lbm_pool_set_storage_range(lbm_pool *p, double range) {
 lbm_status lbm_pool_get_storage_range(const lbm_pool *p, double *range) {
     if (!p || !range) return set_error(LBM_ERR_INVALID_ARG, "pool and range are required");
     if (p->st != LBM_STORE_Q16) return set_error(LBM_ERR_UNSUPPORTED, "only the fixed-point storage has a range");
+    std::lock_guard<std::mutex> lock(p->mu);
     *range = ldexp(1.0, p->qexp + 15);
     return LBM_OK;
 }
@@ -701,6 +703,7 @@ lbm_status lbm_pool_set_kernel(lbm_pool *p, int cells_per_thread, int block_thre
 
 lbm_status lbm_pool_get_kernel(const lbm_pool *p, int *cells_per_thread, int *block_threads) {
     if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
+    std::lock_guard<std::mutex> lock(p->mu);
     if (cells_per_thread) *cells_per_thread = p->cpt;
     if (block_threads) *block_threads = p->block;
     return LBM_OK;

@@ -294,3 +294,49 @@ def test_many_small_requests_under_memory_pressure():
         s.close()
         assert rel_f(out[k][0], r) < TOL_F32, k
         assert np.max(np.abs(out[k][1] - uu)) < TOL_F32 * u0, k
+
+
+def test_two_threads_share_a_pool():
+    """A pool serialises its own calls: two host threads submitting, advancing, polling and
+    collecting their own requests on one pool at once get, bit for bit, the results the same
+    requests give alone."""
+    import threading
+
+    g = np.random.default_rng(5)
+    reqs = [(int(g.integers(8, 30)), float(g.uniform(0.55, 0.9)), float(g.uniform(0.02, 0.06)),
+             int(g.integers(5, 60))) for _ in range(16)]
+    pool = lbm.Pool("D3Q19", 3, "f32", 1 << 30, 64)
+    lbm.lbm_pool_set_kernel(pool.handle, 2, 128)
+    out, errors = {}, []
+
+    def worker(ks):
+        try:
+            ids = {}
+            for k in ks:
+                sd, tau, u0, n = reqs[k]
+                rho, u = _tg(sd, u0)
+                rid = None
+                while rid is None:
+                    rid = pool.submit((sd,) * 3, tau, rho, u, n)
+                ids[k] = rid
+            while ids:
+                pool.advance(9)
+                for k, rid in list(ids.items()):
+                    if pool.poll(rid)[0]:
+                        out[k] = pool.result(rid, reqs[k][0] ** 3)
+                        del ids[k]
+                pool.stats()
+        except Exception as e:  # reported by the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(range(j, 16, 2),)) for j in (0, 1)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errors, errors
+    assert pool.stats()["resident"] == 0
+    pool.close()
+    for k, req in enumerate(reqs):
+        alone = _run_pool([req], kernel=(2, 128))[0]
+        np.testing.assert_array_equal(out[k][1], alone[1])
