@@ -137,9 +137,20 @@ PER_LATTICE = [
     ("D3Q19", (512, 512, 512), 2, "q16", 0.52, 0.05),
 ]
 
+# The extensions of the method (energy-flux term, K = 5, D3Q15, the BGK comparison operator):
+# (lattice, dims, K, storage, tau, u0, model, theta)
+PER_MODE = [
+    ("D3Q19", (256, 256, 256), 3, "f32", 0.6, 0.05, "filtered", 0.5),
+    ("D3Q39", (192, 192, 192), 4, "f32", 0.6, 0.05, "filtered", 0.5),
+    ("D3Q39", (192, 192, 192), 5, "f32", 0.6, 0.05, "filtered", 0.0),
+    ("D3Q15", (256, 256, 256), 3, "f32", 0.6, 0.05, "filtered", 0.0),
+    ("D3Q19", (256, 256, 256), 3, "f32", 0.6, 0.05, "bgk", 0.0),
+]
 
-def measure_lattice(lattice, dims, K, storage, tau, u0, steps, stream):
-    """Autotuned MLUPS and HBM fraction of one configuration (CUDA events on the solver stream)."""
+
+def measure_lattice(lattice, dims, K, storage, tau, u0, steps, stream, model="filtered", theta=0.0):
+    """Autotuned MLUPS and HBM fraction of one configuration (CUDA events on the solver stream).
+    model / theta: the collision operator (BGK comparison, energy-flux weight)."""
     import torch
 
     from paper_2002_02503_gb300 import fields, lbm
@@ -147,6 +158,8 @@ def measure_lattice(lattice, dims, K, storage, tau, u0, steps, stream):
     rho, u = fields.taylor_green_3d(dims, u0, LATTICE_T0[lattice])
     s = lbm.Solver(lattice, dims, tau, K, storage, stream=stream,
                    storage_range=Q16_RANGE if storage == "q16" else None)
+    lbm.lbm_set_collision(s.handle, model)
+    lbm.lbm_set_energy_flux(s.handle, theta)
     s.set_fields(rho, u)
     del rho, u
     lbm.lbm_autotune(s.handle, 10)
@@ -166,7 +179,8 @@ def measure_lattice(lattice, dims, K, storage, tau, u0, steps, stream):
     bpu = 2 * LATTICE_Q[lattice] * STORE_BYTES[storage]
     peak, _ = measured_peak()
     mlups = C * steps / (ms / 1e3) / 1e6
-    return {"workload": "%s %dx%dx%d %s K=%d" % (lattice, dims[0], dims[1], dims[2], storage, K),
+    mode = "" if model == "filtered" and theta == 0.0 else (" BGK" if model == "bgk" else " theta=%g" % theta)
+    return {"workload": "%s %dx%dx%d %s K=%d%s" % (lattice, dims[0], dims[1], dims[2], storage, K, mode),
             "MLUPS": mlups, "bytes_per_update": bpu, "achieved_GBs": mlups * 1e6 * bpu / 1e9,
             "frac_of_measured_hbm": mlups * 1e6 * bpu / 1e9 / peak, "ms_per_step": ms / steps,
             "kernel": {"variant": variant, "cells_per_thread": cpt, "block": block}}
@@ -466,6 +480,8 @@ def run_ours(a):
         if not a.no_extras:
             with torch.cuda.stream(stream):
                 extras["per_lattice"] = [measure_lattice(*cfg, a.extra_steps, stream) for cfg in PER_LATTICE]
+                extras["per_mode"] = [measure_lattice(*cfg[:6], a.extra_steps, stream, model=cfg[6], theta=cfg[7])
+                                      for cfg in PER_MODE]
             from paper_2002_02503_gb300 import serve
 
             peak, _ = measured_peak()
