@@ -173,8 +173,7 @@ lbm_status lbm_set_collision(lbm_solver *s, lbm_collision model);
  * fhat^{neq,q} the Hermite series of Eq. filter-Q (the relative-frame flux Qt of
  * Eq. Q_def) truncated at the solver's K, so theta needs K >= 3.  theta = 0 (the
  * default) is the paper's Sec. 3 collision.  Applies to the filtered collision;
- * runs variant 0 with one cell per thread, or two (even nx, FP32 arithmetic; the
- * autotuner considers both).  LBM_ERR_UNSUPPORTED for K = 2. */
+ * runs one cell per thread.  LBM_ERR_UNSUPPORTED for K = 2. */
 lbm_status lbm_set_energy_flux(lbm_solver *s, double theta);
 
 /* Range R of the fixed-point storage (LBM_STORE_Q16): -R <= h_i < R, grid step R / 2^15.

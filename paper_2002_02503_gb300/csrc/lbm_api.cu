@@ -197,11 +197,7 @@ StepArgs step_args(const lbm_solver *s, int from) {
 
 step_fn step_for(const lbm_solver *s, int variant, int V) {
     if (s->model == LBM_COLLISION_BGK) return (variant == 0 && V == 1) ? s->ks->bgk : nullptr;
-    if (s->theta != 0.0) {
-        if (variant != 0) return nullptr;
-        if (V == 1) return s->ks->theta;
-        return (V == 2 && s->nx % 2 == 0) ? s->ks->theta_pair : nullptr;
-    }
+    if (s->theta != 0.0) return (variant == 0 && V == 1) ? s->ks->theta : nullptr;
     if (variant == 0) {
         int k = v_index(V);
         if (k < 0 || s->nx % V) return nullptr;

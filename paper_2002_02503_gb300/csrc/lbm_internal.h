@@ -145,7 +145,6 @@ struct KernelSet {
     step_fn theta;           // filtered collision with the energy-flux term (K >= 3), V = 1
     bool (*staged_applies)(int nx);  // variant 1 needs nx * sizeof(storage) % 16 == 0 and a fitting tile
     step_fn pair;            // variant 2: flat cell pairs (two cells of the flat index per thread), any nx
-    step_fn theta_pair;      // energy-flux step, V = 2 (paired FP32 collision; null for FP64 arithmetic)
 };
 
 // Defined in the instantiation units, one per lattice.

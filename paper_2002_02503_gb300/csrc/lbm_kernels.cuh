@@ -523,14 +523,6 @@ constexpr step_fn theta_if_built() {
     else return nullptr;
 }
 
-// The energy-flux step with two x-neighbours per thread on the paired FP32 instructions
-// (FP32 arithmetic only: with FP64 the pair would only double the registers).
-template <class LT, int K, class ST>
-constexpr step_fn theta_pair_if_built() {
-    if constexpr (K >= 3 && sizeof(typename ST::T) == 4) return &launch_step_direct<LT, K, ST, 2, false, true>;
-    else return nullptr;
-}
-
 template <class LT, int K, class ST>
 const KernelSet *make_kernel_set() {
     static const KernelSet ks = {
@@ -549,7 +541,6 @@ const KernelSet *make_kernel_set() {
         theta_if_built<LT, K, ST>(),
         staged_check_if_built<LT, ST>(),
         &launch_step_pair<LT, K, ST>,
-        theta_pair_if_built<LT, K, ST>(),
     };
     return &ks;
 }

@@ -445,30 +445,3 @@ def test_autotune_cache_file(tmp_path, monkeypatch):
     lbm.lbm_autotune(c.handle, 2)
     c.close()
     assert len(path.read_text().splitlines()) == 2
-
-
-@pytest.mark.parametrize("name,K,theta", [("D3Q19", 3, 0.7), ("D3Q27", 3, 0.7), ("D3Q39", 4, 0.7), ("D3Q15", 3, 0.3)])
-@pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_energy_flux_with_two_cells_per_thread(name, K, theta, storage):
-    """The energy-flux step with two x-neighbours per thread (paired FP32 collision) against the
-    oracle, where it is built."""
-    dims = DIMS[name]
-    D = lbm.lbm_lattice_info(name)["D"]
-    rho, u = fields.random_smooth_fields(dims, D, salt=40 + K)
-    f_ref = oracle.run(name, K, 0.6, dims, oracle.init_eq(name, K, dims, rho, u), 50, theta=theta)
-    r_ref, u_ref = oracle.moments(name, dims, f_ref)
-    s = lbm.Solver(name, dims, 0.6, K, storage)
-    lbm.lbm_set_energy_flux(s.handle, theta)
-    try:
-        lbm.lbm_set_kernel(s.handle, 0, 2, 128)
-    except lbm.LbmError as e:
-        assert e.status == lbm.LBM_ERR_UNSUPPORTED
-        s.close()
-        pytest.skip("not built for this lattice")
-    s.set_fields(rho, u)
-    s.step(50)
-    r, uu = s.moments()
-    s.close()
-    tol = TOL_F32 if storage == "f32" else 2e-3
-    assert rel_u(uu, u_ref) < tol
-    assert rel_f(r, r_ref) < tol
