@@ -338,6 +338,30 @@ class Solver:
     def raw_bytes(self):
         return self.info["Q"] * self.C * STORAGE_BYTES[self.storage]
 
+    def autotune(self, iters=10):
+        return lbm_autotune(self.handle, iters)
+
+    def set_kernel(self, variant=-1, cells_per_thread=0, block_threads=0):
+        lbm_set_kernel(self.handle, variant, cells_per_thread, block_threads)
+
+    def kernel(self):
+        return lbm_get_kernel(self.handle)
+
+    def set_collision(self, model):
+        lbm_set_collision(self.handle, model)
+
+    def set_energy_flux(self, theta):
+        lbm_set_energy_flux(self.handle, theta)
+
+    def checkpoint(self):
+        """(raw stored distributions as a uint8 array, step counter)."""
+        raw = np.empty(self.raw_bytes(), dtype=np.uint8)
+        t = lbm_get_distributions(self.handle, raw)
+        return raw, t
+
+    def restore(self, raw, t):
+        lbm_set_distributions(self.handle, raw, t)
+
 
 # ----------------------------------------------------------------- pool (batched / served solves)
 def lbm_pool_request_bytes(lattice, dims, storage):
@@ -433,7 +457,9 @@ def lbm_pool_destroy(h):
 
 
 class Pool:
-    """Owns a pool handle plus its device arena (a torch uint8 tensor) and two streams."""
+    """Owns a pool handle plus its device arena (a torch uint8 tensor) and two streams
+    (compute: the batched steps; io: uploads and result downloads).  ``storage_range`` sets
+    the range of a fixed-point pool ("q16")."""
 
     def __init__(self, lattice, K, storage, arena_bytes, max_slots=256, device=None, storage_range=None):
         import torch
@@ -481,3 +507,15 @@ class Pool:
 
     def stats(self):
         return lbm_pool_stats(self.handle)
+
+    def cancel(self, rid):
+        lbm_pool_cancel(self.handle, rid)
+
+    def autotune(self, iters=5):
+        return lbm_pool_autotune(self.handle, iters)
+
+    def set_kernel(self, cells_per_thread=0, block_threads=0):
+        lbm_pool_set_kernel(self.handle, cells_per_thread, block_threads)
+
+    def kernel(self):
+        return lbm_pool_get_kernel(self.handle)

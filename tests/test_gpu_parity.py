@@ -445,3 +445,29 @@ def test_autotune_cache_file(tmp_path, monkeypatch):
     lbm.lbm_autotune(c.handle, 2)
     c.close()
     assert len(path.read_text().splitlines()) == 2
+
+
+def test_solver_convenience_methods():
+    """The Solver class's checkpoint / restore, kernel and collision methods round-trip."""
+    dims = DIMS["D3Q19"]
+    rho, u = fields.random_smooth_fields(dims, 3, salt=93)
+    a = lbm.Solver("D3Q19", dims, 0.6, 3, "f32")
+    a.set_fields(rho, u)
+    a.autotune(2)
+    a.set_kernel(0, 1, 128)
+    assert a.kernel() == (0, 1, 128)
+    a.step(7)
+    raw, t = a.checkpoint()
+    assert t == 7
+    a.step(5)
+    b = lbm.Solver("D3Q19", dims, 0.6, 3, "f32")
+    b.restore(raw, t)
+    b.set_kernel(0, 1, 128)
+    b.step(5)
+    np.testing.assert_array_equal(a.checkpoint()[0], b.checkpoint()[0])
+    b.set_collision("bgk")
+    b.set_collision("filtered")
+    b.set_energy_flux(0.5)
+    b.set_energy_flux(0.0)
+    a.close()
+    b.close()
