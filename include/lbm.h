@@ -177,9 +177,12 @@ lbm_status lbm_set_collision(lbm_solver *s, lbm_collision model);
 lbm_status lbm_set_energy_flux(lbm_solver *s, double theta);
 
 /* Range R of the fixed-point storage (LBM_STORE_Q16): -R <= h_i < R, grid step R / 2^15.
- * R must be a power of two in [2^-8, 2^8].  The stored codes are not converted, so set
- * it before lbm_set_fields or lbm_set_distributions (a checkpoint restores with the
- * range it was taken with).  |h_i| is about |c_i . u| / T0 plus the density excursion
+ * R must be a power of two in [2^-8, 2^8], or 0 for an automatic range: each later
+ * lbm_set_fields first measures max |h| of the initial f^eq on the device and takes the
+ * smallest power of two R >= 1.25 max |h| (read it back with lbm_get_storage_range); a later
+ * exit from that range is reported as usual.  A nonzero R turns the automatic choice off.
+ * The stored codes are not converted, so set R before lbm_set_fields or
+ * lbm_set_distributions (a checkpoint restores with the range it was taken with).  |h_i| is about |c_i . u| / T0 plus the density excursion
  * rho - rho0 and the non-equilibrium part, so R = 1/4 holds flows with |c_i . u| up to
  * about 0.07 on the T0 = 1/3 lattices.  LBM_ERR_UNSUPPORTED for the floating forms. */
 lbm_status lbm_set_storage_range(lbm_solver *s, double range);

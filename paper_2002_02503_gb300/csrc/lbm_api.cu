@@ -167,6 +167,7 @@ struct lbm_solver {
     lbm_collision model;
     double theta;  // energy-flux weight (Eq. pq); 0 = the paper's Sec. 3 collision
     int qexp;      // fixed-point storage: grid step 2^qexp (range 2^(qexp + 15))
+    bool qauto;    // fixed-point storage: choose the range at each lbm_set_fields
     double graph_theta;
     // Captured graphs of kGraphSteps consecutive steps, one per starting buffer; rebuilt
     // when the kernel configuration changes.  They cut the per-step launch cost, which
@@ -341,6 +342,7 @@ lbm_status lbm_create(lbm_lattice lat, const int64_t dims[3], double tau, int K,
     s->ks = ks;
     s->model = LBM_COLLISION_FILTERED_GI;
     s->qexp = -15;  // fixed-point range 1
+    s->qauto = false;
     s->variant = 0;
     s->block = 256;
     s->V = 1;
@@ -370,23 +372,10 @@ lbm_status lbm_destroy(lbm_solver *s) {
     return LBM_OK;
 }
 
-lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm_mem mem) {
-    LBM_NVTX_RANGE("lbm_set_fields");
-    if (lbm_status r = check_solver(s)) return r;
-    if (!rho || !u) return fail(LBM_ERR_INVALID_ARG, "rho and u are required");
-    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return fail(LBM_ERR_INVALID_ARG, "bad lbm_mem");
+// One pass of the init kernel over the whole lattice: f^eq of (rho, u), from device memory
+// directly or staged from the host through the idle buffer.
+static lbm_status init_pass(lbm_solver *s, const double *rho, const double *u, lbm_mem mem, InitArgs a) {
     const int D = s->li.D;
-    InitArgs a = {};
-    a.dst = s->buf[0];
-    a.nx = s->nx;
-    a.ny = s->ny;
-    a.nz = s->nz;
-    a.P = s->C;
-    a.rho0 = s->rho0;
-    a.qs = qscale_of_exponent(s->qexp);
-    a.status = s->status;
-    // the state is replaced: events recorded for the old one no longer apply
-    LBM_CUDA(cudaMemsetAsync(s->status, 0, sizeof(unsigned int), s->stream), "set_fields: status word");
     if (mem == LBM_MEM_DEVICE) {
         a.rho = rho;
         a.u = u;
@@ -394,30 +383,73 @@ lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm
         a.c0 = 0;
         a.count = s->C;
         LBM_CUDA(s->ks->init(a, s->stream), "set_fields: init kernel");
-    } else {
-        char *stage;
-        size_t cap;
-        staging(s, 0, &stage, &cap);
-        const long long per = (long long)(cap / (sizeof(double) * (1 + D)));
-        if (per < 1) return fail(LBM_ERR_OUT_OF_MEMORY, "staging area too small");
-        for (long long c0 = 0; c0 < s->C; c0 += per) {
-            const long long n = std::min(per, s->C - c0);
-            double *drho = reinterpret_cast<double *>(stage);
-            double *du = drho + n;
-            LBM_CUDA(cudaMemcpyAsync(drho, rho + c0, n * sizeof(double), cudaMemcpyHostToDevice, s->stream),
-                     "set_fields: copy rho");
-            for (int d = 0; d < D; ++d)
-                LBM_CUDA(cudaMemcpyAsync(du + d * n, u + d * s->C + c0, n * sizeof(double), cudaMemcpyHostToDevice,
-                                         s->stream),
-                         "set_fields: copy u");
-            a.rho = drho;
-            a.u = du;
-            a.ustride = n;
-            a.c0 = c0;
-            a.count = n;
-            LBM_CUDA(s->ks->init(a, s->stream), "set_fields: init kernel");
+        return LBM_OK;
+    }
+    char *stage;
+    size_t cap;
+    staging(s, 0, &stage, &cap);
+    const long long per = (long long)(cap / (sizeof(double) * (1 + D)));
+    if (per < 1) return fail(LBM_ERR_OUT_OF_MEMORY, "staging area too small");
+    for (long long c0 = 0; c0 < s->C; c0 += per) {
+        const long long n = std::min(per, s->C - c0);
+        double *drho = reinterpret_cast<double *>(stage);
+        double *du = drho + n;
+        LBM_CUDA(cudaMemcpyAsync(drho, rho + c0, n * sizeof(double), cudaMemcpyHostToDevice, s->stream),
+                 "set_fields: copy rho");
+        for (int d = 0; d < D; ++d)
+            LBM_CUDA(cudaMemcpyAsync(du + d * n, u + d * s->C + c0, n * sizeof(double), cudaMemcpyHostToDevice,
+                                     s->stream),
+                     "set_fields: copy u");
+        a.rho = drho;
+        a.u = du;
+        a.ustride = n;
+        a.c0 = c0;
+        a.count = n;
+        LBM_CUDA(s->ks->init(a, s->stream), "set_fields: init kernel");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm_mem mem) {
+    LBM_NVTX_RANGE("lbm_set_fields");
+    if (lbm_status r = check_solver(s)) return r;
+    if (!rho || !u) return fail(LBM_ERR_INVALID_ARG, "rho and u are required");
+    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return fail(LBM_ERR_INVALID_ARG, "bad lbm_mem");
+    InitArgs a = {};
+    a.dst = s->buf[0];
+    a.nx = s->nx;
+    a.ny = s->ny;
+    a.nz = s->nz;
+    a.P = s->C;
+    a.rho0 = s->rho0;
+    a.status = s->status;
+    // the state is replaced: events recorded for the old one no longer apply
+    LBM_CUDA(cudaMemsetAsync(s->status, 0, sizeof(unsigned int), s->stream), "set_fields: status word");
+    if (s->st == LBM_STORE_Q16 && s->qauto) {
+        // automatic range: measure the largest |h| of f^eq, then take the smallest power of two
+        // R >= 1.25 max|h| (headroom for the flow to develop; an exit is still reported)
+        unsigned int *hm = reinterpret_cast<unsigned int *>(s->red_out);
+        LBM_CUDA(cudaMemsetAsync(hm, 0, sizeof(unsigned int), s->stream), "set_fields: range word");
+        InitArgs m = a;
+        m.hmax = hm;
+        if (lbm_status r = init_pass(s, rho, u, mem, m)) return r;
+        unsigned int bits = 0;
+        LBM_CUDA(cudaMemcpyAsync(&bits, hm, sizeof(bits), cudaMemcpyDeviceToHost, s->stream), "set_fields: range");
+        LBM_CUDA(cudaStreamSynchronize(s->stream), "set_fields: synchronize");
+        float h = 0.f;
+        memcpy(&h, &bits, sizeof(h));
+        if (!isfinite(h)) return fail(LBM_ERR_RANGE, "set_fields: f^eq is not finite");
+        int e2 = -8;
+        while (e2 < 8 && ldexp(1.0, e2) < 1.25 * double(h)) ++e2;
+        if (ldexp(1.0, e2) < 1.25 * double(h))
+            return fail(LBM_ERR_RANGE, "set_fields: f^eq needs a range above 2^8 (max |h| = %g)", double(h));
+        if (e2 - 15 != s->qexp) {
+            drop_step_graphs(s);  // the grid step is baked into captured launches
+            s->qexp = e2 - 15;
         }
     }
+    a.qs = qscale_of_exponent(s->qexp);
+    if (lbm_status r = init_pass(s, rho, u, mem, a)) return r;
     LBM_CUDA(cudaStreamSynchronize(s->stream), "set_fields: synchronize");
     s->cur = 0;
     s->t = 0;
@@ -719,11 +751,16 @@ lbm_status lbm_set_energy_flux(lbm_solver *s, double theta) {
 lbm_status lbm_set_storage_range(lbm_solver *s, double range) {
     if (lbm_status r = check_solver(s)) return r;
     if (s->st != LBM_STORE_Q16) return fail(LBM_ERR_UNSUPPORTED, "only the fixed-point storage has a range");
+    if (range == 0.0) {  // automatic: chosen from the fields at each lbm_set_fields
+        s->qauto = true;
+        return LBM_OK;
+    }
     int e2 = 0;
     const double m = frexp(range, &e2);  // range = m 2^e2, m in [1/2, 1)
     if (!(range > 0.0) || !isfinite(range) || m != 0.5 || e2 - 1 < -8 || e2 - 1 > 8)
         return fail(LBM_ERR_INVALID_ARG, "range must be a power of two in [2^-8, 2^8] (got %g)", range);
     const int qexp = (e2 - 1) - 15;
+    s->qauto = false;
     if (qexp != s->qexp) {
         drop_step_graphs(s);  // the grid step is baked into captured launches
         s->qexp = qexp;

@@ -60,6 +60,7 @@ struct InitArgs {
     double rho0;
     QScale qs;
     unsigned int *status;  // receives kStatusRange when a value does not fit the fixed-point range
+    unsigned int *hmax;    // when set: store nothing, only raise *hmax to the largest |h| (float bits)
 };
 
 struct PullArgs {

@@ -241,10 +241,11 @@ template <class LT, int K, class ST>
 __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__restrict__ rho,
                             const double *__restrict__ u, long long ustride, long long c0, long long count, int nx,
                             int ny, int nz, long long P, double rho0, QScale qs,
-                            unsigned int *__restrict__ status) {
+                            unsigned int *__restrict__ status, unsigned int *__restrict__ hmax) {
     using S = typename ST::S;
     using T = typename ST::T;
     unsigned int acc = 0u;
+    unsigned int hbits = 0u;  // largest |h| seen, as float bits (ordered like the values; NaN above all)
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
          k += (long long)gridDim.x * blockDim.x) {
         const long long cell = c0 + k;
@@ -257,6 +258,11 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
         for (int a = 0; a < LT::D; ++a) uu[a] = T(u[a * ustride + k]);
         T g[LT::Q];
         equilibrium_shifted<LT, K, T>(T(r), T(r - rho0), uu, g);
+        if (hmax) {  // measuring pass (automatic fixed-point range): nothing is stored
+#pragma unroll
+            for (int i = 0; i < LT::Q; ++i) hbits = max(hbits, __float_as_uint(fabsf(float(g[i]))));
+            continue;
+        }
 #pragma unroll
         for (int i = 0; i < LT::Q; ++i) {
             const int xs = wrapn(x - vel<LT>(i, 0), nx);
@@ -268,6 +274,10 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
     if constexpr (ST::id == LBM_STORE_Q16) {
         if (range_exceeded(acc) && status) atomicOr(status, kStatusRange);
     }
+    if (hmax) {  // every thread of the (full) warps gets here: one atomic per warp
+        hbits = __reduce_max_sync(kFull, hbits);
+        if ((threadIdx.x & 31) == 0) atomicMax(hmax, hbits);
+    }
 }
 
 template <class LT, int K, class ST>
@@ -277,7 +287,7 @@ cudaError_t launch_init(const InitArgs &a, cudaStream_t stream) {
     if (blocks > 65535) blocks = 65535;
     init_kernel<LT, K, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<typename ST::S *>(a.dst), a.rho, a.u,
                                                                   a.ustride, a.c0, a.count, a.nx, a.ny, a.nz, a.P,
-                                                                  a.rho0, a.qs, a.status);
+                                                                  a.rho0, a.qs, a.status, a.hmax);
     return cudaGetLastError();
 }
 

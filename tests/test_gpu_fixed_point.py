@@ -379,3 +379,27 @@ def test_range_report_belongs_to_the_state_it_came_from():
     s.step(1)
     s.moments()
     s.close()
+
+
+@pytest.mark.parametrize("u0,want", [(0.05, 0.25), (0.005, 2.0 ** -5)])
+def test_automatic_range(u0, want):
+    """Range 0 = automatic: set_fields measures max|h| of f^eq and takes the smallest power of two
+    R >= 1.25 max|h|; the run then matches the oracle within the 16-bit bound."""
+    name, K, dims = "D3Q19", 3, (32, 24, 16)
+    rho, u = fields.taylor_green_3d(dims, u0, 1.0 / 3.0)
+    # the largest |h| of the truncated equilibrium, from the oracle (h = (f - w rho0) / w)
+    f0 = oracle.init_eq(name, K, dims, rho, u)
+    w = oracle.lattice(name)["w"][:, None]
+    hmax = np.abs((f0 - w) / w).max()
+    assert want / 2 < 1.25 * hmax <= want
+    s = lbm.Solver(name, dims, 0.6, K, "q16", storage_range=0.0)
+    s.set_fields(rho, u)
+    assert lbm.lbm_get_storage_range(s.handle) == want
+    s.step(40)
+    r, uu = s.moments()
+    _, r_ref, u_ref = oracle_reference(name, K, 0.6, dims, rho, u, 40)
+    assert rel_u(uu, u_ref) < TOL_U16
+    lbm.lbm_set_storage_range(s.handle, 1.0)  # an explicit range turns the automatic choice off
+    s.set_fields(rho, u)
+    assert lbm.lbm_get_storage_range(s.handle) == 1.0
+    s.close()
