@@ -153,7 +153,7 @@ def test_set_fields_beyond_the_range_is_reported():
 
 def test_range_must_be_a_power_of_two_and_floating_forms_have_none():
     s = lbm.Solver("D3Q19", DIMS["D3Q19"], 0.6, 3, "q16")
-    for bad in (0.3, 0.0, -1.0, 2.0 ** -9, 2.0 ** 9, float("nan")):
+    for bad in (0.3, -1.0, 2.0 ** -9, 2.0 ** 9, float("nan")):  # (0 selects the automatic range)
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_set_storage_range(s.handle, bad)
         assert e.value.status == lbm.LBM_ERR_INVALID_ARG
