@@ -279,11 +279,14 @@ lbm_status lbm_pool_sync(lbm_pool *p);
 lbm_status lbm_pool_stats(const lbm_pool *p, size_t *free_bytes, int *resident, int *done);
 
 /* Range R of a fixed-point pool (LBM_STORE_Q16), as lbm_set_storage_range: a power of two
- * in [2^-8, 2^8], default 1, the same for every request.  Only while no request is
- * resident (LBM_ERR_BUSY otherwise).  A request whose f^eq does not fit is refused by
- * lbm_pool_submit with LBM_ERR_RANGE.  LBM_ERR_UNSUPPORTED for the floating forms. */
+ * in [2^-8, 2^8], default 1, the same for every request; or 0: each request gets its own
+ * range at admission, the smallest power of two >= 1.25 max |h| of its f^eq (measured on the
+ * device; lbm_pool_request_range reads it; the get call then reports 0).  Only while no
+ * request is resident (LBM_ERR_BUSY otherwise).  A request whose f^eq does not fit is refused
+ * by lbm_pool_submit with LBM_ERR_RANGE.  LBM_ERR_UNSUPPORTED for the floating forms. */
 lbm_status lbm_pool_set_storage_range(lbm_pool *p, double range);
 lbm_status lbm_pool_get_storage_range(const lbm_pool *p, double *range);
+lbm_status lbm_pool_request_range(const lbm_pool *p, int64_t id, double *range);
 
 /* Kernel configuration of the batched step.  cells_per_thread: the most cells a thread
  * updates, 1 or 2 (the default); a request whose nx is odd always runs 1, so a request's

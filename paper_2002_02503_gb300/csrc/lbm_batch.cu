@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <map>
@@ -88,6 +89,7 @@ struct Request {
     size_t off, bytes;
     void *buf[2];
     unsigned int *status;              // device status word (kStatusRange), after the two buffers
+    int qexp;                          // fixed-point storage: this request's grid step 2^qexp
     bool waited_init;                  // compute stream already waits on its init event
     cudaEvent_t init_event;
     long long finish_chunk;            // chunk counter of its last step (-1 while running)
@@ -109,6 +111,7 @@ struct lbm_pool {
     int grids[3];  // persistent grid of each slot-mode kernel
     int cpt;  // most cells per thread a slot may run (1 or 2)
     int qexp; // fixed-point storage: grid step 2^qexp
+    bool qauto;  // fixed-point storage: each request's range chosen from its own f^eq at admission
     // double-buffered slot tables
     BatchSlot *d_table[2];
     int *d_header[2];
@@ -225,7 +228,7 @@ int build_table(lbm_pool *p, int b, int *units_total) {
             s.steps_left = int(std::min<int64_t>(left, 1 << 30));
             s.unit0 = units;
             s.units = int((s.threads + p->block - 1) / p->block);
-            s.qs = qscale_of_exponent(p->qexp);
+            s.qs = qscale_of_exponent(r.qexp);
             s.status = r.status;
             fastdiv_init(unsigned(s.ncx), &s.mx, &s.sx);
             fastdiv_init(unsigned(r.ny), &s.my, &s.sy);
@@ -249,7 +252,7 @@ lbm_status pull_to(lbm_pool *p, Request &r, double *rho, double *u, lbm_mem mem)
     a.nz = r.nz;
     a.P = r.C;
     a.rho0 = r.rho0;
-    a.qs = qscale_of_exponent(p->qexp);
+    a.qs = qscale_of_exponent(r.qexp);
     a.f = nullptr;
     cudaError_t e;
     if (mem == LBM_MEM_DEVICE) {
@@ -338,6 +341,7 @@ lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, 
     p->K = K;
     p->st = st;
     p->qexp = -15;  // fixed-point range 1
+    p->qauto = false;
     p->D = D;
     p->Q = Q;
     p->maxc = maxc;
@@ -428,32 +432,66 @@ lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, doubl
     a.nz = r.nz;
     a.P = r.C;
     a.rho0 = rho0;
-    a.qs = qscale_of_exponent(p->qexp);
     a.status = r.status;
-    if (mem == LBM_MEM_DEVICE) {
-        a.rho = rho;
-        a.u = u;
-        a.ustride = r.C;
-        a.c0 = 0;
-        a.count = r.C;
-        e = p->ks->init(a, p->io);
-    } else {
+    // one pass of the init kernel, from device memory or staged through the idle buffer
+    auto init_pass = [&](const InitArgs &args) -> cudaError_t {
+        InitArgs b = args;
+        if (mem == LBM_MEM_DEVICE) {
+            b.rho = rho;
+            b.u = u;
+            b.ustride = r.C;
+            b.c0 = 0;
+            b.count = r.C;
+            return p->ks->init(b, p->io);
+        }
+        cudaError_t err = cudaSuccess;
         double *stage = static_cast<double *>(r.buf[1]);
         const long long per = (long long)(half / (sizeof(double) * (1 + p->D)));
-        for (long long c0 = 0; c0 < r.C && e == cudaSuccess; c0 += per) {
+        for (long long c0 = 0; c0 < r.C && err == cudaSuccess; c0 += per) {
             const long long n = std::min(per, r.C - c0);
-            e = cudaMemcpyAsync(stage, rho + c0, n * sizeof(double), cudaMemcpyHostToDevice, p->io);
-            for (int d = 0; d < p->D && e == cudaSuccess; ++d)
-                e = cudaMemcpyAsync(stage + (1 + d) * n, u + (long long)d * r.C + c0, n * sizeof(double),
-                                    cudaMemcpyHostToDevice, p->io);
-            a.rho = stage;
-            a.u = stage + n;
-            a.ustride = n;
-            a.c0 = c0;
-            a.count = n;
-            if (e == cudaSuccess) e = p->ks->init(a, p->io);
+            err = cudaMemcpyAsync(stage, rho + c0, n * sizeof(double), cudaMemcpyHostToDevice, p->io);
+            for (int d = 0; d < p->D && err == cudaSuccess; ++d)
+                err = cudaMemcpyAsync(stage + (1 + d) * n, u + (long long)d * r.C + c0, n * sizeof(double),
+                                      cudaMemcpyHostToDevice, p->io);
+            b.rho = stage;
+            b.u = stage + n;
+            b.ustride = n;
+            b.c0 = c0;
+            b.count = n;
+            if (err == cudaSuccess) err = p->ks->init(b, p->io);
         }
+        return err;
+    };
+    r.qexp = p->qexp;
+    if (p->st == LBM_STORE_Q16 && p->qauto) {
+        // this request's range: the smallest power of two >= 1.25 max|h| of its f^eq, measured
+        // into the second word of its status block
+        unsigned int *hm = r.status + 1;
+        e = cudaMemsetAsync(hm, 0, sizeof(unsigned int), p->io);
+        InitArgs m = a;
+        m.hmax = hm;
+        if (e == cudaSuccess) e = init_pass(m);
+        unsigned int bits = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, hm, sizeof(bits), cudaMemcpyDeviceToHost, p->io);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->io);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(r.init_event);
+            p->arena.release(r.off, r.bytes);
+            return set_cuda_error(e, "pool: range measurement");
+        }
+        float h = 0.f;
+        memcpy(&h, &bits, sizeof(h));
+        int e2 = -8;
+        while (e2 < 8 && ldexp(1.0, e2) < 1.25 * double(h)) ++e2;
+        if (!isfinite(h) || ldexp(1.0, e2) < 1.25 * double(h)) {
+            cudaEventDestroy(r.init_event);
+            p->arena.release(r.off, r.bytes);
+            return set_error(LBM_ERR_RANGE, "pool: f^eq does not fit any fixed-point range up to 2^8");
+        }
+        r.qexp = e2 - 15;
     }
+    a.qs = qscale_of_exponent(r.qexp);
+    e = init_pass(a);
     if (e == cudaSuccess) e = cudaEventRecord(r.init_event, p->io);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->io);  // host inputs consumed before returning
     if (e != cudaSuccess) {
@@ -671,12 +709,17 @@ lbm_status lbm_pool_set_storage_range(lbm_pool *p, double range) {
     if (!p) return set_error(LBM_ERR_INVALID_ARG, "pool is NULL");
     std::lock_guard<std::mutex> lock(p->mu);
     if (p->st != LBM_STORE_Q16) return set_error(LBM_ERR_UNSUPPORTED, "only the fixed-point storage has a range");
+    if (!p->reqs.empty()) return set_error(LBM_ERR_BUSY, "pool: the range can change only while no request is resident");
+    if (range == 0.0) {  // automatic: each request's own range, chosen at admission
+        p->qauto = true;
+        return LBM_OK;
+    }
     int e2 = 0;
     const double m = frexp(range, &e2);  // range = m 2^e2, m in [1/2, 1)
     if (!(range > 0.0) || !isfinite(range) || m != 0.5 || e2 - 1 < -8 || e2 - 1 > 8)
-        return set_error(LBM_ERR_INVALID_ARG, "range must be a power of two in [2^-8, 2^8]");
-    if (!p->reqs.empty()) return set_error(LBM_ERR_BUSY, "pool: the range can change only while no request is resident");
+        return set_error(LBM_ERR_INVALID_ARG, "range must be a power of two in [2^-8, 2^8], or 0");
     p->qexp = (e2 - 1) - 15;
+    p->qauto = false;
     return LBM_OK;
 }
 
@@ -684,7 +727,17 @@ lbm_status lbm_pool_get_storage_range(const lbm_pool *p, double *range) {
     if (!p || !range) return set_error(LBM_ERR_INVALID_ARG, "pool and range are required");
     if (p->st != LBM_STORE_Q16) return set_error(LBM_ERR_UNSUPPORTED, "only the fixed-point storage has a range");
     std::lock_guard<std::mutex> lock(p->mu);
-    *range = ldexp(1.0, p->qexp + 15);
+    *range = p->qauto ? 0.0 : ldexp(1.0, p->qexp + 15);
+    return LBM_OK;
+}
+
+lbm_status lbm_pool_request_range(const lbm_pool *p, int64_t id, double *range) {
+    if (!p || !range) return set_error(LBM_ERR_INVALID_ARG, "pool and range are required");
+    if (p->st != LBM_STORE_Q16) return set_error(LBM_ERR_UNSUPPORTED, "only the fixed-point storage has a range");
+    std::lock_guard<std::mutex> lock(p->mu);
+    auto it = p->reqs.find(id);
+    if (it == p->reqs.end()) return set_error(LBM_ERR_NOT_FOUND, "unknown request id");
+    *range = ldexp(1.0, it->second.qexp + 15);
     return LBM_OK;
 }
 

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("lbm_pool_stats", _c.c_int, [_P, _c.POINTER(_c.c_size_t), _IP, _IP]),
     ("lbm_pool_set_storage_range", _c.c_int, [_P, _c.c_double]),
     ("lbm_pool_get_storage_range", _c.c_int, [_P, _DP]),
+    ("lbm_pool_request_range", _c.c_int, [_P, _c.c_int64, _DP]),
     ("lbm_pool_set_kernel", _c.c_int, [_P, _c.c_int, _c.c_int]),
     ("lbm_pool_get_kernel", _c.c_int, [_P, _IP, _IP]),
     ("lbm_pool_autotune", _c.c_int, [_P, _c.c_int, _DP]),
@@ -433,6 +434,12 @@ def lbm_pool_set_storage_range(h, R):
 def lbm_pool_get_storage_range(h):
     r = ctypes.c_double()
     _check(lib().lbm_pool_get_storage_range(h, ctypes.byref(r)))
+    return r.value
+
+
+def lbm_pool_request_range(h, rid):
+    r = ctypes.c_double()
+    _check(lib().lbm_pool_request_range(h, int(rid), ctypes.byref(r)))
     return r.value
 
 

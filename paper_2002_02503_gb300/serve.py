@@ -201,14 +201,15 @@ def batched_rate(n=40, steps=200, storage="f32", K=3, chunk=50, salt=5, autotune
             "ms_per_step": ms / steps, "kernel": {"cells_per_thread": cpt, "block": block}}
 
 
-def served_accuracy(n=24, salt=7, forms=(("f32", None), ("f16", None), ("bf16", None), ("q16", 0.5))):
+def served_accuracy(n=24, salt=7, forms=(("f32", None), ("f16", None), ("bf16", None), ("q16", 0.5), ("q16", 0.0))):
     """Accuracy of served results per storage form: n requests drawn like the trace, all offered at
     once, served by a pool of each form; u compared with the FP32 single-lattice solver on the same
     request (which matches the FP64 oracle within 1e-5).  Two measures per form: max|du| / max|u| on
     the requests whose flow still holds at least a tenth of its initial amplitude u0 (many requests
     decay by orders of magnitude over their steps, and then any rounding is large next to u), and
-    max|du| / u0 on every request.  The fixed-point range 1/2 holds the trace's flows (|h| below
-    about 0.3 for u0 <= 0.08)."""
+    max|du| / u0 on every request.  The fixed-point pools run with one range, 1/2 (it holds the
+    trace's flows: |h| below about 0.3 for u0 <= 0.08), and with each request's own range chosen
+    at admission (range 0)."""
     trace = [dict(r, arrival=0.0) for r in make_trace(n, salt=salt)]
     keep = {r["i"] for r in trace}
     _, ref = serve_plain(trace, keep=keep)
@@ -219,7 +220,7 @@ def served_accuracy(n=24, salt=7, forms=(("f32", None), ("f16", None), ("bf16", 
         _, res = serve_pool(trace, storage=storage, keep=keep, storage_range=R)
         rel = [float(np.max(np.abs(res[i][1] - ref[i][1])) / np.max(np.abs(ref[i][1]))) for i in live]
         by_u0 = [float(np.max(np.abs(res[r["i"]][1] - ref[r["i"]][1])) / r["u0"]) for r in trace]
-        key = storage if R is None else "%s (range %g)" % (storage, R)
+        key = storage if R is None else ("%s (range auto)" % storage if R == 0.0 else "%s (range %g)" % (storage, R))
         out[key] = {"max_rel_u_live": max(rel) if rel else None,
                     "median_rel_u_live": float(np.median(rel)) if rel else None,
                     "max_du_over_u0": max(by_u0)}

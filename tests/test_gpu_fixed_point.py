@@ -403,3 +403,25 @@ def test_automatic_range(u0, want):
     s.set_fields(rho, u)
     assert lbm.lbm_get_storage_range(s.handle) == 1.0
     s.close()
+
+
+def test_pool_automatic_range_per_request():
+    """A fixed-point pool with range 0 gives each request the smallest power of two >= 1.25 max|h|
+    of its own f^eq; results match the oracle within the 16-bit bound."""
+    pool = lbm.Pool("D3Q19", 2, "q16", 1 << 28, 8, storage_range=0.0)
+    assert lbm.lbm_pool_get_storage_range(pool.handle) == 0.0
+    reqs = []
+    for side, u0, want in ((20, 0.05, 0.25), (17, 0.005, 2.0 ** -5)):
+        d = (side,) * 3
+        rho, u = fields.taylor_green_3d(d, u0, 1.0 / 3.0)
+        rid = pool.submit(d, 0.6, rho, u, 30)
+        assert lbm.lbm_pool_request_range(pool.handle, rid) == want
+        reqs.append((d, rho, u, rid))
+    while not all(pool.poll(r[3])[0] for r in reqs):
+        pool.advance(10)
+        pool.sync()
+    for d, rho, u, rid in reqs:
+        rr, uu = pool.result(rid, int(np.prod(d)))
+        _, r_ref, u_ref = oracle_reference("D3Q19", 2, 0.6, d, rho, u, 30)
+        assert rel_u(uu, u_ref) < TOL_U16
+    pool.close()
