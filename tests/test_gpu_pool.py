@@ -205,10 +205,12 @@ def test_cells_per_thread_of_the_batched_step():
 
 def test_served_accuracy_by_storage_form():
     """Requests drawn like the serving trace, served by pools of each storage form, against the FP32
-    single-lattice solver.  The FP32 pool agrees within the FP32 tolerance.  The 16-bit forms are
-    measured and reported (their error grows as a request's flow decays, since rounding then
-    weighs more next to u); the check on them is a sanity bound of 1e-2 of the initial amplitude,
-    an order above what they reach, which catches a wrong range or a mixed-up result."""
+    single-lattice solver.  The FP32 pool agrees within the FP32 tolerance, and the fixed-point
+    pool with each request's own range (range 0) within the 16-bit bound.  FP16 and the
+    fixed-point pool with one range for all are measured and reported (their error grows as a
+    request's flow decays, since rounding then weighs more next to u); the check on them is a
+    sanity bound of 1e-2 of the initial amplitude, which catches a wrong range or a mixed-up
+    result."""
     acc = serve.served_accuracy(n=8, salt=24)  # six of the eight flows stay live
     print(acc)
     assert acc["live_requests"] >= 4
@@ -216,6 +218,9 @@ def test_served_accuracy_by_storage_form():
     assert acc["f32"]["max_du_over_u0"] < TOL_F32
     for form in ("f16", "q16 (range 0.5)"):
         assert acc[form]["max_du_over_u0"] < 1e-2, form
+    # with each request's own range the fixed-point pool holds the 16-bit bound
+    assert acc["q16 (range auto)"]["max_rel_u_live"] < 1e-3
+    assert acc["q16 (range auto)"]["max_du_over_u0"] < 1e-3
 
 
 def test_cancelled_request_leaves_the_others_unchanged():
