@@ -495,6 +495,7 @@ def run_ours(a):
                 trace = serve.make_trace(a.serve, rate=a.serve_rate)
                 pool_stats, _ = serve.serve_pool(trace)
                 pool16_stats, _ = serve.serve_pool(trace, storage="f16")
+                poolq_stats, _ = serve.serve_pool(trace, storage="q16", storage_range=0.0)
                 plain_stats, _ = serve.serve_plain(trace)
                 # capacity: the same requests all arriving at once
                 burst = [dict(r, arrival=0.0) for r in trace]
@@ -504,7 +505,8 @@ def run_ours(a):
                 extras["serving"] = {
                     "workload": "%d D3Q19 Taylor-Green solves, side log-uniform 32-128, tau U[0.52,1], "
                                 "u0 U[0.01,0.08], 100-2000 steps, Poisson %g/s, FP32, K=3" % (a.serve, a.serve_rate),
-                    "pool": pool_stats, "pool_f16_storage": pool16_stats, "plain_fifo": plain_stats,
+                    "pool": pool_stats, "pool_f16_storage": pool16_stats,
+                    "pool_q16_storage_per_request_range": poolq_stats, "plain_fifo": plain_stats,
                     "capacity_all_at_once": {"pool": burst_pool, "plain_fifo": burst_plain}}
         out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
