@@ -500,6 +500,7 @@ def run_ours(a):
                 # capacity: the same requests all arriving at once
                 burst = [dict(r, arrival=0.0) for r in trace]
                 burst_pool, _ = serve.serve_pool(burst)
+                burst_poolq, _ = serve.serve_pool(burst, storage="q16", storage_range=0.0)
                 burst_plain, _ = serve.serve_plain(burst)
                 extras["serving_accuracy"] = serve.served_accuracy()
                 extras["serving"] = {
@@ -507,7 +508,8 @@ def run_ours(a):
                                 "u0 U[0.01,0.08], 100-2000 steps, Poisson %g/s, FP32, K=3" % (a.serve, a.serve_rate),
                     "pool": pool_stats, "pool_f16_storage": pool16_stats,
                     "pool_q16_storage_per_request_range": poolq_stats, "plain_fifo": plain_stats,
-                    "capacity_all_at_once": {"pool": burst_pool, "plain_fifo": burst_plain}}
+                    "capacity_all_at_once": {"pool": burst_pool, "pool_q16_storage_per_request_range": burst_poolq,
+                                             "plain_fifo": burst_plain}}
         out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": DTYPE_NAME[a.storage], "data": "synthetic (Taylor-Green initial field)",
