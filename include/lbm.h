@@ -188,6 +188,17 @@ lbm_status lbm_set_energy_flux(lbm_solver *s, double theta);
 lbm_status lbm_set_storage_range(lbm_solver *s, double range);
 lbm_status lbm_get_storage_range(const lbm_solver *s, double *range);
 
+/* Reference shift of the fixed-point storage (LBM_STORE_Q16): the stored value of velocity i
+ * becomes h_i - href_i, with href_i = rho0 (s_i + (s_i^2 - |U|^2/T0) / 2), s_i = c_i.U / T0,
+ * the scaled equilibrium at the reference velocity U (rounded to the grid, so decode adds
+ * back exactly what encode takes off; the codec costs the same instructions).  For a flow
+ * near a uniform U -- a wave on a background flow -- the stored values, and with them the
+ * automatic range and the rounding step, shrink by the background's share.  U = {0, 0, 0}
+ * (the default) turns it off; |U| <= 1/2.  Set it before lbm_set_fields; the range is
+ * raised if needed so that every shift stays below 2^22 grid steps.  LBM_ERR_UNSUPPORTED
+ * for the floating forms. */
+lbm_status lbm_set_storage_reference(lbm_solver *s, const double U[3]);
+
 /* Autotuner: times every built kernel configuration for this solver on its own
  * buffers (reads the current state, writes only the idle buffer, so the state is
  * unchanged) over `iters` launches each and keeps the fastest.  best_us, if not

@@ -168,6 +168,9 @@ struct lbm_solver {
     double theta;  // energy-flux weight (Eq. pq); 0 = the paper's Sec. 3 collision
     int qexp;      // fixed-point storage: grid step 2^qexp (range 2^(qexp + 15))
     bool qauto;    // fixed-point storage: choose the range at each lbm_set_fields
+    bool qref_on;  // fixed-point storage: values stored relative to the equilibrium at qref_u
+    double qref_u[3];
+    double qref_h[kQMax];  // that equilibrium as scaled shifted values, per velocity
     double graph_theta;
     // Captured graphs of kGraphSteps consecutive steps, one per starting buffer; rebuilt
     // when the kernel configuration changes.  They cut the per-step launch cost, which
@@ -178,6 +181,21 @@ struct lbm_solver {
 };
 
 namespace {
+
+// Codec constants of the solver's storage: grid step and reference shift.
+QScale solver_qscale(const lbm_solver *s) {
+    return qscale_of_exponent(s->qexp, s->qref_on ? s->qref_h : nullptr, s->li.Q);
+}
+
+// Smallest grid exponent the reference shift allows: k_i = ref_i / 2^e must stay below 2^22.
+int min_qexp_for_reference(const lbm_solver *s) {
+    if (!s->qref_on) return -1000;
+    double m = 0.0;
+    for (int i = 0; i < s->li.Q; ++i) m = std::max(m, fabs(s->qref_h[i]));
+    int e = -40;
+    while (e < 30 && ldexp(m, -e) >= 4194304.0) ++e;  // 2^22
+    return e;
+}
 
 StepArgs step_args(const lbm_solver *s, int from) {
     StepArgs a = {};
@@ -192,7 +210,7 @@ StepArgs step_args(const lbm_solver *s, int from) {
     a.status = s->status;
     a.grid_limit = 0;
     a.theta = s->theta;
-    a.qs = qscale_of_exponent(s->qexp);
+    a.qs = solver_qscale(s);
     return a;
 }
 
@@ -343,6 +361,7 @@ lbm_status lbm_create(lbm_lattice lat, const int64_t dims[3], double tau, int K,
     s->model = LBM_COLLISION_FILTERED_GI;
     s->qexp = -15;  // fixed-point range 1
     s->qauto = false;
+    s->qref_on = false;
     s->variant = 0;
     s->block = 256;
     s->V = 1;
@@ -440,7 +459,7 @@ lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm
         memcpy(&h, &bits, sizeof(h));
         if (!isfinite(h)) return fail(LBM_ERR_RANGE, "set_fields: f^eq is not finite");
         int e2 = -8;
-        while (e2 < 8 && ldexp(1.0, e2) < 1.25 * double(h)) ++e2;
+        while (e2 < 8 && (ldexp(1.0, e2) < 1.25 * double(h) || e2 - 15 < min_qexp_for_reference(s))) ++e2;
         if (ldexp(1.0, e2) < 1.25 * double(h))
             return fail(LBM_ERR_RANGE, "set_fields: f^eq needs a range above 2^8 (max |h| = %g)", double(h));
         if (e2 - 15 != s->qexp) {
@@ -448,7 +467,7 @@ lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm
             s->qexp = e2 - 15;
         }
     }
-    a.qs = qscale_of_exponent(s->qexp);
+    a.qs = solver_qscale(s);
     if (lbm_status r = init_pass(s, rho, u, mem, a)) return r;
     LBM_CUDA(cudaStreamSynchronize(s->stream), "set_fields: synchronize");
     s->cur = 0;
@@ -542,7 +561,7 @@ static lbm_status pull_out(lbm_solver *s, double *rho, double *u, double *f, lbm
     a.nz = s->nz;
     a.P = s->C;
     a.rho0 = s->rho0;
-    a.qs = qscale_of_exponent(s->qexp);
+    a.qs = solver_qscale(s);
     pull_fn fn = f ? s->ks->pull_f : s->ks->moments;
     if (mem == LBM_MEM_DEVICE) {
         a.rho = rho;
@@ -619,7 +638,7 @@ static lbm_status reduce_to_host(lbm_solver *s, reduce_fn fn, ReduceArgs &a, int
     a.partials = s->partials;
     a.out = s->red_out;
     a.blocks = kReduceBlocks;
-    a.qs = qscale_of_exponent(s->qexp);
+    a.qs = solver_qscale(s);
     LBM_CUDA(fn(a, s->stream), "reduction kernel");
     LBM_CUDA(cudaMemcpyAsync(out, s->red_out, nvals * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
              "copy reduction");
@@ -760,11 +779,41 @@ lbm_status lbm_set_storage_range(lbm_solver *s, double range) {
     if (!(range > 0.0) || !isfinite(range) || m != 0.5 || e2 - 1 < -8 || e2 - 1 > 8)
         return fail(LBM_ERR_INVALID_ARG, "range must be a power of two in [2^-8, 2^8] (got %g)", range);
     const int qexp = (e2 - 1) - 15;
+    if (qexp < min_qexp_for_reference(s))
+        return fail(LBM_ERR_INVALID_ARG, "range too fine for the reference shift (needs |shift| < 2^22 steps)");
     s->qauto = false;
     if (qexp != s->qexp) {
         drop_step_graphs(s);  // the grid step is baked into captured launches
         s->qexp = qexp;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_storage_reference(lbm_solver *s, const double U[3]) {
+    if (lbm_status r = check_solver(s)) return r;
+    if (!U) return fail(LBM_ERR_INVALID_ARG, "U is NULL");
+    if (s->st != LBM_STORE_Q16) return fail(LBM_ERR_UNSUPPORTED, "only the fixed-point storage has a reference shift");
+    double u2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(U[a])) return fail(LBM_ERR_INVALID_ARG, "U must be finite");
+        u2 += U[a] * U[a];
+    }
+    if (u2 > 0.25) return fail(LBM_ERR_INVALID_ARG, "|U| must be <= 1/2");
+    int c[kQMax * 3];
+    double T0 = 0.0;
+    lbm_lattice_info(s->lat, nullptr, nullptr, c, nullptr, &T0, nullptr);
+    s->qref_on = u2 > 0.0;
+    for (int a = 0; a < 3; ++a) s->qref_u[a] = U[a];
+    // (f^eq_i(rho0, U) - w_i rho0) / w_i with the second-order equilibrium: any fixed values
+    // serve (the codec adds back exactly what it takes off); these are close to a flow near U
+    for (int i = 0; i < s->li.Q; ++i) {
+        double cu = 0.0;
+        for (int a = 0; a < s->li.D; ++a) cu += c[3 * i + a] * U[a];
+        const double sc = cu / T0, v2 = u2 / T0;
+        s->qref_h[i] = s->qref_on ? s->rho0 * (sc + 0.5 * (sc * sc - v2)) : 0.0;
+    }
+    if (!s->qauto && s->qexp < min_qexp_for_reference(s)) s->qexp = min_qexp_for_reference(s);
+    drop_step_graphs(s);  // the codec constants are baked into captured launches
     return LBM_OK;
 }
 

@@ -228,7 +228,8 @@ int build_table(lbm_pool *p, int b, int *units_total) {
             s.steps_left = int(std::min<int64_t>(left, 1 << 30));
             s.unit0 = units;
             s.units = int((s.threads + p->block - 1) / p->block);
-            s.qs = qscale_of_exponent(r.qexp);
+            s.qmul = ldexpf(1.0f, r.qexp);
+            s.qinv = ldexpf(1.0f, -r.qexp);
             s.status = r.status;
             fastdiv_init(unsigned(s.ncx), &s.mx, &s.sx);
             fastdiv_init(unsigned(r.ny), &s.my, &s.sy);

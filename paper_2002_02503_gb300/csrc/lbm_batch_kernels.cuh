@@ -24,7 +24,7 @@ __device__ __forceinline__ void pull_cell_scaled(const typename ST::S *__restric
     for (int i = 0; i < LT::Q; ++i) {
         const long long at = (long long)i * P + (long long)(zs[vel<LT>(i, 2) + M] * ny + ys[vel<LT>(i, 1) + M]) * nx +
                              xs[vel<LT>(i, 0) + M];
-        f[i] = decode<ST>(src[at], qs);
+        f[i] = decode<ST>(src[at], qs, i);
     }
 }
 
@@ -71,8 +71,8 @@ __device__ __forceinline__ void pull_collide_store_pair(const typename ST::S *__
     unsigned int acc = 0u;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        dst[(long long)i * P + c0] = encode<ST>(f0[i], qs, acc);
-        if (second) dst[(long long)i * P + c0 + 1] = encode<ST>(f1[i], qs, acc);
+        dst[(long long)i * P + c0] = encode<ST>(f0[i], qs, i, acc);
+        if (second) dst[(long long)i * P + c0 + 1] = encode<ST>(f1[i], qs, i, acc);
     }
     if constexpr (ST::id == LBM_STORE_Q16) {
         if (range_exceeded(acc) && status) atomicOr(status, kStatusRange);
@@ -160,13 +160,14 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__rest
         const auto *src = static_cast<const typename ST::S *>(sl.buf[cur]);
         auto *dst = static_cast<typename ST::S *>(sl.buf[cur ^ 1]);
         const typename ST::T relax(sl.relax), rho0(sl.rho0), kq(0);
+        const QScale qs = qscale_plain(sl.qmul, sl.qinv);
         if constexpr (MODE == 2) {
             if (t >= total) continue;  // no warp collectives on this path
             const int c0 = 2 * t;
             const int row = fastdiv(c0, sl.mx, sl.sx);  // c0 / nx
             const int z = fastdiv(row, sl.my, sl.sy);
             pull_collide_store_pair<LT, K, ST>(src, dst, sl.nx, sl.ny, sl.nz, sl.P, c0 - row * sl.nx, row - z * sl.ny,
-                                               z, (long long)c0 + 1 < sl.P, relax, rho0, sl.qs, sl.status);
+                                               z, (long long)c0 + 1 < sl.P, relax, rho0, qs, sl.status);
         } else {
             const bool active = t < total;
             if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__rest
             const int z = fastdiv(row, sl.my, sl.sy);
             const int y = row - z * sl.ny;
             pull_collide_store<LT, K, ST, MODE == 1 ? 2 : 1>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk,
-                                                             active, relax, rho0, kq, sl.qs, sl.status);
+                                                             active, relax, rho0, kq, qs, sl.status);
         }
     }
 }

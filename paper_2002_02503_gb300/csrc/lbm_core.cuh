@@ -44,29 +44,31 @@ struct StoreF32 {
     using S = float;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_F32;
-    __device__ __forceinline__ static T dec(S v, const QScale &) { return v; }
-    __device__ __forceinline__ static S enc(T x, const QScale &, unsigned int &) { return x; }
+    __device__ __forceinline__ static T dec(S v, const QScale &, int) { return v; }
+    __device__ __forceinline__ static S enc(T x, const QScale &, int, unsigned int &) { return x; }
 };
 struct StoreF64 {
     using S = double;
     using T = double;
     static constexpr lbm_storage id = LBM_STORE_F64;
-    __device__ __forceinline__ static T dec(S v, const QScale &) { return v; }
-    __device__ __forceinline__ static S enc(T x, const QScale &, unsigned int &) { return x; }
+    __device__ __forceinline__ static T dec(S v, const QScale &, int) { return v; }
+    __device__ __forceinline__ static S enc(T x, const QScale &, int, unsigned int &) { return x; }
 };
 struct StoreF16 {
     using S = __half;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_F16;
-    __device__ __forceinline__ static T dec(S v, const QScale &) { return __half2float(v); }
-    __device__ __forceinline__ static S enc(T x, const QScale &, unsigned int &) { return __float2half_rn(x); }
+    __device__ __forceinline__ static T dec(S v, const QScale &, int) { return __half2float(v); }
+    __device__ __forceinline__ static S enc(T x, const QScale &, int, unsigned int &) { return __float2half_rn(x); }
 };
 struct StoreBF16 {
     using S = __nv_bfloat16;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_BF16;
-    __device__ __forceinline__ static T dec(S v, const QScale &) { return __bfloat162float(v); }
-    __device__ __forceinline__ static S enc(T x, const QScale &, unsigned int &) { return __float2bfloat16_rn(x); }
+    __device__ __forceinline__ static T dec(S v, const QScale &, int) { return __bfloat162float(v); }
+    __device__ __forceinline__ static S enc(T x, const QScale &, int, unsigned int &) {
+        return __float2bfloat16_rn(x);
+    }
 };
 // 16-bit fixed point: h = q 2^e with the integer q in [-32768, 32767], held in offset
 // binary (q + 2^15).  Both directions use the FP32 adder's rounding at magnitude 2^23,
@@ -79,22 +81,21 @@ struct StoreBF16 {
 //           cell (range_exceeded) detects it at one logic operation per value;
 //   decode  the bits 0x4B000000 | (q + 2^15) are the float 2^23 + 2^15 + q, and
 //           fma(that, 2^e, -(2^23 + 2^15) 2^e) = q 2^e exactly.
+// With a reference shift of k_i grid steps for velocity i (QScale), the stored code is
+// q - k_i + 2^15: both constants carry -k_i, so the codec costs the same instructions.
 struct StoreQ16 {
     using S = unsigned short;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_Q16;
     static constexpr float kBias = 8421376.0f;  // 2^23 + 2^15
     static constexpr unsigned int kExp = 0x4B000000u;
-    __device__ __forceinline__ static T dec(S v, const QScale &q) {
-        return fmaf(__uint_as_float(kExp | unsigned(v)), q.mul, q.off);
+    __device__ __forceinline__ static T dec(S v, const QScale &q, int i) {
+        return fmaf(__uint_as_float(kExp | unsigned(v)), q.mul, q.dec[i]);
     }
-    __device__ __forceinline__ static unsigned int enc_bits(T x, const QScale &q, unsigned int &acc) {
-        const unsigned int b = __float_as_uint(fmaf(x, q.inv, kBias));
+    __device__ __forceinline__ static S enc(T x, const QScale &q, int i, unsigned int &acc) {
+        const unsigned int b = __float_as_uint(fmaf(x, q.inv, q.enc[i]));
         acc |= b ^ kExp;
-        return b;
-    }
-    __device__ __forceinline__ static S enc(T x, const QScale &q, unsigned int &acc) {
-        return static_cast<S>(enc_bits(x, q, acc));
+        return static_cast<S>(b);
     }
 };
 // True when an encode since acc = 0 met a value outside the fixed-point range.
@@ -105,7 +106,7 @@ __device__ __forceinline__ bool range_exceeded(unsigned int acc) { return (acc >
 // accumulates the fixed-point form's range check into acc (range_exceeded).
 template <class ST, int V>
 __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typename ST::T (&out)[V],
-                                           const QScale &q) {
+                                           const QScale &q, int i) {
     if constexpr (ST::id == LBM_STORE_F16 && V % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
@@ -123,7 +124,7 @@ __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typen
     } else if constexpr (ST::id == LBM_STORE_Q16 && V % 2 == 0) {
         // two codes per 32-bit word: one byte permute builds each float's bits, one paired
         // FMA scales both
-        const float2 mul = make_float2(q.mul, q.mul), off = make_float2(q.off, q.off);
+        const float2 mul = make_float2(q.mul, q.mul), off = make_float2(q.dec[i], q.dec[i]);
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
             const unsigned int w = unsigned(raw[j]) | (unsigned(raw[j + 1]) << 16);
@@ -135,13 +136,13 @@ __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typen
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < V; ++j) out[j] = ST::dec(raw[j], q);
+        for (int j = 0; j < V; ++j) out[j] = ST::dec(raw[j], q, i);
     }
 }
 
 template <class ST, int V>
 __device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typename ST::S (&raw)[V],
-                                           const QScale &q, unsigned int &acc) {
+                                           const QScale &q, int i, unsigned int &acc) {
     if constexpr (ST::id == LBM_STORE_F16 && V % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
@@ -158,7 +159,7 @@ __device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typena
         }
     } else if constexpr (ST::id == LBM_STORE_Q16 && V % 2 == 0) {
         // one paired FMA encodes two values; the low halves of both encodings pack into one word
-        const float2 inv = make_float2(q.inv, q.inv), bias = make_float2(StoreQ16::kBias, StoreQ16::kBias);
+        const float2 inv = make_float2(q.inv, q.inv), bias = make_float2(q.enc[i], q.enc[i]);
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
             const float2 v = __ffma2_rn(make_float2(in[j], in[j + 1]), inv, bias);
@@ -170,18 +171,33 @@ __device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typena
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < V; ++j) raw[j] = ST::enc(in[j], q, acc);
+        for (int j = 0; j < V; ++j) raw[j] = ST::enc(in[j], q, i, acc);
     }
 }
 
-// Scaled value h of one stored value, and back.
+// Scaled value h of one stored value of velocity i, and back.
 template <class ST>
-__device__ __forceinline__ typename ST::T decode(typename ST::S v, const QScale &q) {
-    return ST::dec(v, q);
+__device__ __forceinline__ typename ST::T decode(typename ST::S v, const QScale &q, int i) {
+    return ST::dec(v, q, i);
 }
 template <class ST>
-__device__ __forceinline__ typename ST::S encode(typename ST::T x, const QScale &q, unsigned int &acc) {
-    return ST::enc(x, q, acc);
+__device__ __forceinline__ typename ST::S encode(typename ST::T x, const QScale &q, int i, unsigned int &acc) {
+    return ST::enc(x, q, i, acc);
+}
+
+// The codec constants of a grid step 2^e = mul with no reference shift (built in registers;
+// with i known at compile time the arrays fold to constants).
+__device__ __forceinline__ QScale qscale_plain(float mul, float inv) {
+    QScale q;
+    q.mul = mul;
+    q.inv = inv;
+#pragma unroll
+    for (int i = 0; i < kQMax; ++i) {
+        q.enc[i] = StoreQ16::kBias;
+        q.dec[i] = -StoreQ16::kBias * mul;
+        q.ref[i] = 0.0f;
+    }
+    return q;
 }
 
 // ------------------------------------------------------------------ paired FP32

@@ -18,17 +18,28 @@ constexpr int kNumV = 4;
 inline int v_index(int V) { return V == 1 ? 0 : V == 2 ? 1 : V == 4 ? 2 : V == 8 ? 3 : -1; }
 inline int v_of_index(int k) { return 1 << k; }
 
-// Grid step of the fixed-point storage (LBM_STORE_Q16) as the three constants the
-// codec uses: mul = 2^e, inv = 2^-e, off = -(2^23 + 2^15) 2^e, all exact in FP32 for
-// |e| <= 30.  The floating storage forms ignore it.
+constexpr int kQMax = 39;  // largest velocity count of the built lattices
+
+// Constants of the fixed-point storage codec (LBM_STORE_Q16); the floating forms ignore them.
+// Grid step 2^e: mul = 2^e, inv = 2^-e.  Per velocity i, a reference shift of k_i whole grid
+// steps (k_i = rint(ref_i / 2^e), ref_i the scaled equilibrium at a reference velocity, 0 by
+// default) enters the codec's two FMA constants: enc[i] = 2^23 + 2^15 - k_i and
+// dec[i] = -(2^23 + 2^15 - k_i) 2^e, both exact in FP32 for |k_i| < 2^22 and |e| <= 30.
+// ref[i] keeps the unrounded shift for the range measurement of lbm_set_fields.
 struct QScale {
-    float mul, inv, off;
+    float mul, inv;
+    float enc[kQMax], dec[kQMax], ref[kQMax];
 };
-inline QScale qscale_of_exponent(int e) {
+inline QScale qscale_of_exponent(int e, const double *ref = nullptr, int Q = 0) {
     QScale q;
     q.mul = ldexpf(1.0f, e);
     q.inv = ldexpf(1.0f, -e);
-    q.off = -ldexpf(8421376.0f, e);
+    for (int i = 0; i < kQMax; ++i) {
+        const double k = (ref && i < Q) ? rint(ldexp(ref[i], -e)) : 0.0;
+        q.enc[i] = float(8421376.0 - k);
+        q.dec[i] = -ldexpf(float(8421376.0 - k), e);
+        q.ref[i] = (ref && i < Q) ? float(ref[i]) : 0.0f;
+    }
     return q;
 }
 
@@ -105,7 +116,7 @@ struct BatchSlot {
     int unit0;         // first work unit of this slot (table sorted by unit0)
     int units;         // work units of this slot
     unsigned int mx, sx, my, sy;  // division by ncx (modes 0, 1) or nx (mode 2) and by ny (fastdiv_init)
-    QScale qs;                    // fixed-point grid step (LBM_STORE_Q16 only)
+    float qmul, qinv;             // fixed-point grid step 2^e and 2^-e (LBM_STORE_Q16 only; no reference shift)
     unsigned int *status;         // this request's status word (kStatusRange)
 };
 

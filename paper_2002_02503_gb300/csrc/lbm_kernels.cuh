@@ -116,7 +116,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         for (int i = 0; i < Q; ++i) {
             const int cx = vel<LT>(i, 0), cy = vel<LT>(i, 1), cz = vel<LT>(i, 2);
             const S *row = src + (long long)i * P + (long long)(zs[cz + M] * ny + ys[cy + M]) * nx;
-            f[i][0] = decode<ST>(row[xs[cx + M]], qs);
+            f[i][0] = decode<ST>(row[xs[cx + M]], qs, i);
         }
     } else {
 #pragma unroll
@@ -126,7 +126,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         S raw[V];
         load_vec<S, V>(row + x0, raw);
         T v[V];
-        decode_vec<ST, V>(raw, v, qs);
+        decode_vec<ST, V>(raw, v, qs, i);
         if (cx == 0) {
 #pragma unroll
             for (int j = 0; j < V; ++j) f[i][j] = v[j];
@@ -142,7 +142,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
                     // source lane lane+dl holds chunk+dl of the same row unless at a warp or row edge
                     const int sl = lane + dl;
                     T sh = __shfl_sync(kFull, v[ei], sl < 0 ? 0 : (sl > 31 ? 31 : sl));
-                    if (!ok[dl + kMaxDl]) sh = decode<ST>(row[wrap1(x0 + e, nx)], qs);
+                    if (!ok[dl + kMaxDl]) sh = decode<ST>(row[wrap1(x0 + e, nx)], qs, i);
                     f[i][j] = sh;
                 }
             }
@@ -187,7 +187,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             S raw[V];
-            encode_vec<ST, V>(f[i], raw, qs, acc);
+            encode_vec<ST, V>(f[i], raw, qs, i, acc);
             store_vec<S, V>(out + (long long)i * P, raw);
         }
     }
@@ -260,7 +260,7 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
         equilibrium_shifted<LT, K, T>(T(r), T(r - rho0), uu, g);
         if (hmax) {  // measuring pass (automatic fixed-point range): nothing is stored
 #pragma unroll
-            for (int i = 0; i < LT::Q; ++i) hbits = max(hbits, __float_as_uint(fabsf(float(g[i]))));
+            for (int i = 0; i < LT::Q; ++i) hbits = max(hbits, __float_as_uint(fabsf(float(g[i]) - qs.ref[i])));
             continue;
         }
 #pragma unroll
@@ -268,7 +268,7 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
             const int xs = wrapn(x - vel<LT>(i, 0), nx);
             const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
             const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
-            dst[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs] = encode<ST>(T(g[i]), qs, acc);
+            dst[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs] = encode<ST>(T(g[i]), qs, i, acc);
         }
     }
     if constexpr (ST::id == LBM_STORE_Q16) {
@@ -304,7 +304,7 @@ __device__ __forceinline__ void pull_cell(const typename ST::S *__restrict__ src
         const int xs = wrapn(x - vel<LT>(i, 0), nx);
         const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
         const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
-        gt[i] = weight<LT>(i) * double(decode<ST>(src[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs], qs));
+        gt[i] = weight<LT>(i) * double(decode<ST>(src[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs], qs, i));
     }
 }
 
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kReduceThreads) conservation_kernel(const type
     long long n = 0;
     for (long long k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
 #pragma unroll
-        for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST>(src[(long long)i * P + k], qs));
+        for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST>(src[(long long)i * P + k], qs, i));
         ++n;
     }
     v[0] = double(n) * rho0;

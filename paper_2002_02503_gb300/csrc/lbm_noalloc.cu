@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kNoallocThreads) plane_sums_kernel(const typen
     long long n = 0;
     for (long long k = threadIdx.x; k < plane_cells; k += blockDim.x) {
 #pragma unroll
-        for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST>(src[(long long)i * P + base + k], QScale{}));
+        for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST>(src[(long long)i * P + base + k], QScale{}, i));
         ++n;
     }
     double v[4] = {double(n) * rho0, 0.0, 0.0, 0.0};

@@ -218,12 +218,12 @@ __global__ void __launch_bounds__(kStagedThreads) step_staged_kernel(const typen
             const S *base = st + size_t(cr[j]) * nx;
             T g[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) g[i] = decode<ST>(base[size_t(i) * R * nx + xs[vel<LT>(i, 0) + M]], QScale{});
+            for (int i = 0; i < Q; ++i) g[i] = decode<ST>(base[size_t(i) * R * nx + xs[vel<LT>(i, 0) + M]], QScale{}, i);
             collide<LT, K, T>(g, relax, rho0);
             S *out = dst + (long long)row * nx + x;
             unsigned int acc = 0u;  // floating storage only: no range to leave
 #pragma unroll
-            for (int i = 0; i < Q; ++i) out[(long long)i * P] = encode<ST>(g[i], QScale{}, acc);
+            for (int i = 0; i < Q; ++i) out[(long long)i * P] = encode<ST>(g[i], QScale{}, i, acc);
         }
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[s])) : "memory");

@@ -47,6 +47,7 @@ SIGNATURES = [
     ("lbm_set_energy_flux", _c.c_int, [_P, _c.c_double]),
     ("lbm_set_storage_range", _c.c_int, [_P, _c.c_double]),
     ("lbm_get_storage_range", _c.c_int, [_P, _DP]),
+    ("lbm_set_storage_reference", _c.c_int, [_P, _DP]),
     ("lbm_autotune", _c.c_int, [_P, _c.c_int, _DP]),
     ("lbm_conservation_noalloc", _c.c_int, [_c.c_int, _c.c_int, _I64P, _c.c_double, _P, _P, _c.c_int, _P]),
     ("lbm_destroy", _c.c_int, [_P]),
@@ -243,6 +244,11 @@ def lbm_set_storage_range(h, R):
     _check(lib().lbm_set_storage_range(h, float(R)))
 
 
+def lbm_set_storage_reference(h, U):
+    arr = (ctypes.c_double * 3)(*[float(x) for x in (list(U) + [0.0, 0.0, 0.0])[:3]])
+    _check(lib().lbm_set_storage_reference(h, arr))
+
+
 def lbm_get_storage_range(h):
     r = ctypes.c_double()
     _check(lib().lbm_get_storage_range(h, ctypes.byref(r)))
@@ -276,10 +282,11 @@ class Solver:
     """Owns a solver handle plus its device workspace (a torch uint8 tensor).
 
     ``stream`` is a ``torch.cuda.Stream`` (default: the current stream).  ``storage_range``
-    sets the range of the fixed-point storage ("q16"; a power of two, default 1)."""
+    sets the range of the fixed-point storage ("q16"; a power of two, default 1, 0 = automatic)
+    and ``storage_reference`` its reference velocity (the shift of the stored values)."""
 
     def __init__(self, lattice, dims, tau, K, storage="f32", rho0=1.0, stream=None, device=None,
-                 storage_range=None):
+                 storage_range=None, storage_reference=None):
         import torch
 
         self.lattice = lattice
@@ -297,6 +304,8 @@ class Solver:
                                  self.stream.cuda_stream)
         if storage_range is not None:
             lbm_set_storage_range(self.handle, storage_range)
+        if storage_reference is not None:
+            lbm_set_storage_reference(self.handle, storage_reference)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

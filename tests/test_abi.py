@@ -104,6 +104,7 @@ def test_null_solver_is_rejected(L):
     assert lbm.lib().lbm_get_storage_range(None, None) == lbm.LBM_ERR_INVALID_ARG
     assert lbm.lib().lbm_pool_get_storage_range(None, None) == lbm.LBM_ERR_INVALID_ARG
     assert lbm.lib().lbm_pool_request_range(None, 0, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lbm.lib().lbm_set_storage_reference(None, None) == lbm.LBM_ERR_INVALID_ARG
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_step(None, 1)
     assert e.value.status == lbm.LBM_ERR_INVALID_ARG
