@@ -191,7 +191,9 @@ lbm_status lbm_get_storage_range(const lbm_solver *s, double *range);
 /* Reference shift of the fixed-point storage (LBM_STORE_Q16): the stored value of velocity i
  * becomes h_i - href_i, with href_i = rho0 (s_i + (s_i^2 - |U|^2/T0) / 2), s_i = c_i.U / T0,
  * the scaled equilibrium at the reference velocity U (rounded to the grid, so decode adds
- * back exactly what encode takes off; the codec costs the same instructions).  For a flow
+ * back exactly what encode takes off).  The shifted codec holds one constant per velocity, so
+ * it runs its own kernels, used only while a shift is set; unshifted solvers keep the
+ * kernels with one constant for every velocity.  For a flow
  * near a uniform U -- a wave on a background flow -- the stored values, and with them the
  * automatic range and the rounding step, shrink by the background's share.  U = {0, 0, 0}
  * (the default) turns it off; |U| <= 1/2.  Set it before lbm_set_fields; the range is
@@ -204,7 +206,8 @@ lbm_status lbm_set_storage_reference(lbm_solver *s, const double U[3]);
  * unchanged) over `iters` launches each and keeps the fastest.  best_us, if not
  * NULL, receives the average step time of the chosen configuration.  With the
  * environment variable LBM_AUTOTUNE_CACHE naming a file, a choice stored there for the
- * same device, lattice, K, storage, dims and collision mode is applied without timing
+ * same device, lattice, K, storage (and reference shift on or off), dims and collision mode
+ * is applied without timing
  * (best_us then reports the stored time), and a new choice is appended to the file. */
 lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us);
 

@@ -162,7 +162,8 @@ struct lbm_solver {
     unsigned int *status;
     cudaStream_t stream;
     long long t;
-    const KernelSet *ks;
+    const KernelSet *ks;       // the kernels the solver runs: ks_base, or its shifted companion
+    const KernelSet *ks_base;  // the kernels of its (lattice, K, storage)
     int variant, V, block;
     lbm_collision model;
     double theta;  // energy-flux weight (Eq. pq); 0 = the paper's Sec. 3 collision
@@ -358,6 +359,7 @@ lbm_status lbm_create(lbm_lattice lat, const int64_t dims[3], double tau, int K,
     s->stream = static_cast<cudaStream_t>(stream);
     s->t = 0;
     s->ks = ks;
+    s->ks_base = ks;
     s->model = LBM_COLLISION_FILTERED_GI;
     s->qexp = -15;  // fixed-point range 1
     s->qauto = false;
@@ -444,6 +446,7 @@ lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm
     a.status = s->status;
     // the state is replaced: events recorded for the old one no longer apply
     LBM_CUDA(cudaMemsetAsync(s->status, 0, sizeof(unsigned int), s->stream), "set_fields: status word");
+    a.qs = solver_qscale(s);  // the measuring pass below needs its reference shift
     if (s->st == LBM_STORE_Q16 && s->qauto) {
         // automatic range: measure the largest |h| of f^eq, then take the smallest power of two
         // R >= 1.25 max|h| (headroom for the flow to develop; an exit is still reported)
@@ -802,6 +805,7 @@ lbm_status lbm_set_storage_reference(lbm_solver *s, const double U[3]) {
     int c[kQMax * 3];
     double T0 = 0.0;
     lbm_lattice_info(s->lat, nullptr, nullptr, c, nullptr, &T0, nullptr);
+    if (u2 > 0.0 && !s->ks_base->shifted) return fail(LBM_ERR_UNSUPPORTED, "shifted fixed-point kernels not built");
     s->qref_on = u2 > 0.0;
     for (int a = 0; a < 3; ++a) s->qref_u[a] = U[a];
     // (f^eq_i(rho0, U) - w_i rho0) / w_i with the second-order equilibrium: any fixed values
@@ -813,7 +817,8 @@ lbm_status lbm_set_storage_reference(lbm_solver *s, const double U[3]) {
         s->qref_h[i] = s->qref_on ? s->rho0 * (sc + 0.5 * (sc * sc - v2)) : 0.0;
     }
     if (!s->qauto && s->qexp < min_qexp_for_reference(s)) s->qexp = min_qexp_for_reference(s);
-    drop_step_graphs(s);  // the codec constants are baked into captured launches
+    s->ks = s->qref_on ? s->ks_base->shifted : s->ks_base;
+    drop_step_graphs(s);  // the codec constants and kernels are baked into captured launches
     return LBM_OK;
 }
 
@@ -847,8 +852,8 @@ std::string tune_key(const lbm_solver *s) {
     for (char &c : name)
         if (c == ' ') c = '_';
     char buf[256];
-    snprintf(buf, sizeof(buf), "%s|L%d|K%d|S%d|%dx%dx%d|M%d|T%d", name.c_str(), int(s->lat), s->K, int(s->st), s->nx,
-             s->ny, s->nz, int(s->model), s->theta != 0.0 ? 1 : 0);
+    snprintf(buf, sizeof(buf), "%s|L%d|K%d|S%d%s|%dx%dx%d|M%d|T%d", name.c_str(), int(s->lat), s->K, int(s->st),
+             s->qref_on ? "R" : "", s->nx, s->ny, s->nz, int(s->model), s->theta != 0.0 ? 1 : 0);
     return buf;
 }
 

@@ -83,20 +83,38 @@ struct StoreBF16 {
 //           fma(that, 2^e, -(2^23 + 2^15) 2^e) = q 2^e exactly.
 // With a reference shift of k_i grid steps for velocity i (QScale), the stored code is
 // q - k_i + 2^15: both constants carry -k_i, so the codec costs the same instructions.
-struct StoreQ16 {
+template <bool SHIFT>
+struct StoreQ16Codec {
     using S = unsigned short;
     using T = float;
     static constexpr lbm_storage id = LBM_STORE_Q16;
+    static constexpr bool shifted = SHIFT;
     static constexpr float kBias = 8421376.0f;  // 2^23 + 2^15
     static constexpr unsigned int kExp = 0x4B000000u;
+    // the FMA constants of velocity i: uniform without a reference shift (hoisted out of the
+    // velocity loops), per velocity with one
+    __device__ __forceinline__ static float dec_off(const QScale &q, int i) { return SHIFT ? q.dec[i] : q.off; }
+    __device__ __forceinline__ static float enc_off(const QScale &q, int i) { return SHIFT ? q.enc[i] : kBias; }
     __device__ __forceinline__ static T dec(S v, const QScale &q, int i) {
-        return fmaf(__uint_as_float(kExp | unsigned(v)), q.mul, q.dec[i]);
+        return fmaf(__uint_as_float(kExp | unsigned(v)), q.mul, dec_off(q, i));
     }
     __device__ __forceinline__ static S enc(T x, const QScale &q, int i, unsigned int &acc) {
-        const unsigned int b = __float_as_uint(fmaf(x, q.inv, q.enc[i]));
+        const unsigned int b = __float_as_uint(fmaf(x, q.inv, enc_off(q, i)));
         acc |= b ^ kExp;
         return static_cast<S>(b);
     }
+};
+using StoreQ16 = StoreQ16Codec<false>;
+using StoreQ16S = StoreQ16Codec<true>;  // with the per-velocity reference shift
+
+// True for the fixed-point codec with the reference shift.
+template <class ST>
+struct ShiftedOf {
+    static constexpr bool value = false;
+};
+template <bool S>
+struct ShiftedOf<StoreQ16Codec<S>> {
+    static constexpr bool value = S;
 };
 // True when an encode since acc = 0 met a value outside the fixed-point range.
 __device__ __forceinline__ bool range_exceeded(unsigned int acc) { return (acc >> 16) != 0u; }
@@ -124,7 +142,7 @@ __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typen
     } else if constexpr (ST::id == LBM_STORE_Q16 && V % 2 == 0) {
         // two codes per 32-bit word: one byte permute builds each float's bits, one paired
         // FMA scales both
-        const float2 mul = make_float2(q.mul, q.mul), off = make_float2(q.dec[i], q.dec[i]);
+        const float2 mul = make_float2(q.mul, q.mul), off = make_float2(ST::dec_off(q, i), ST::dec_off(q, i));
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
             const unsigned int w = unsigned(raw[j]) | (unsigned(raw[j + 1]) << 16);
@@ -159,7 +177,7 @@ __device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typena
         }
     } else if constexpr (ST::id == LBM_STORE_Q16 && V % 2 == 0) {
         // one paired FMA encodes two values; the low halves of both encodings pack into one word
-        const float2 inv = make_float2(q.inv, q.inv), bias = make_float2(q.enc[i], q.enc[i]);
+        const float2 inv = make_float2(q.inv, q.inv), bias = make_float2(ST::enc_off(q, i), ST::enc_off(q, i));
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
             const float2 v = __ffma2_rn(make_float2(in[j], in[j + 1]), inv, bias);
@@ -191,6 +209,7 @@ __device__ __forceinline__ QScale qscale_plain(float mul, float inv) {
     QScale q;
     q.mul = mul;
     q.inv = inv;
+    q.off = -StoreQ16::kBias * mul;
 #pragma unroll
     for (int i = 0; i < kQMax; ++i) {
         q.enc[i] = StoreQ16::kBias;

@@ -27,13 +27,14 @@ constexpr int kQMax = 39;  // largest velocity count of the built lattices
 // dec[i] = -(2^23 + 2^15 - k_i) 2^e, both exact in FP32 for |k_i| < 2^22 and |e| <= 30.
 // ref[i] keeps the unrounded shift for the range measurement of lbm_set_fields.
 struct QScale {
-    float mul, inv;
+    float mul, inv, off;  // off = -(2^23 + 2^15) 2^e: the decode constant with no shift
     float enc[kQMax], dec[kQMax], ref[kQMax];
 };
 inline QScale qscale_of_exponent(int e, const double *ref = nullptr, int Q = 0) {
     QScale q;
     q.mul = ldexpf(1.0f, e);
     q.inv = ldexpf(1.0f, -e);
+    q.off = -ldexpf(8421376.0f, e);
     for (int i = 0; i < kQMax; ++i) {
         const double k = (ref && i < Q) ? rint(ldexp(ref[i], -e)) : 0.0;
         q.enc[i] = float(8421376.0 - k);
@@ -157,6 +158,9 @@ struct KernelSet {
     step_fn theta;           // filtered collision with the energy-flux term (K >= 3), V = 1
     bool (*staged_applies)(int nx);  // variant 1 needs nx * sizeof(storage) % 16 == 0 and a fitting tile
     step_fn pair;            // variant 2: flat cell pairs (two cells of the flat index per thread), any nx
+    // fixed-point storage: the same kernels with a per-velocity reference shift in the codec
+    // (its extra constants cost instructions, so the plain set keeps uniform ones); else null
+    const struct KernelSet *shifted;
 };
 
 // Defined in the instantiation units, one per lattice.

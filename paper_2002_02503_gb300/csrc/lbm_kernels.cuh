@@ -534,6 +534,29 @@ constexpr step_fn theta_if_built() {
 }
 
 template <class LT, int K, class ST>
+const KernelSet *make_kernel_set();
+
+// The fixed-point form's companion set with the reference shift (no batched step: pools run
+// without one); null for the other forms.
+template <class LT, int K, class ST>
+const KernelSet *shifted_set_if_built() {
+    if constexpr (ST::id == LBM_STORE_Q16 && !ShiftedOf<ST>::value) return make_kernel_set<LT, K, StoreQ16S>();
+    else return nullptr;
+}
+
+template <class LT, int K, class ST>
+constexpr batch_fn batch_if_built() {
+    if constexpr (ShiftedOf<ST>::value) return nullptr;
+    else return &launch_batch<LT, K, ST>;
+}
+
+template <class LT, int K, class ST>
+constexpr int (*batch_occupancy_if_built())(int, int) {
+    if constexpr (ShiftedOf<ST>::value) return nullptr;
+    else return &batch_occupancy<LT, K, ST>;
+}
+
+template <class LT, int K, class ST>
 const KernelSet *make_kernel_set() {
     static const KernelSet ks = {
         {direct_if_built<LT, K, ST, 1>(), direct_if_built<LT, K, ST, 2>(), direct_if_built<LT, K, ST, 4>(),
@@ -545,12 +568,13 @@ const KernelSet *make_kernel_set() {
         &launch_pull_f<LT, ST>,
         &launch_conservation<LT, ST>,
         &launch_mode<LT, ST>,
-        &launch_batch<LT, K, ST>,
-        &batch_occupancy<LT, K, ST>,
+        batch_if_built<LT, K, ST>(),
+        batch_occupancy_if_built<LT, K, ST>(),
         &launch_step_direct<LT, K, ST, 1, true>,
         theta_if_built<LT, K, ST>(),
         staged_check_if_built<LT, ST>(),
         &launch_step_pair<LT, K, ST>,
+        shifted_set_if_built<LT, K, ST>(),
     };
     return &ks;
 }

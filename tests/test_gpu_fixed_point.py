@@ -448,7 +448,9 @@ def test_decode_with_reference_shift_is_exact():
     k = np.rint(_href(info, U) / step)  # the shift in whole grid steps
     h = (g.astype(np.float64) - 32768.0 + k[:, None]) * step
     w = info["w"][:, None]
-    np.testing.assert_array_equal(f, _pull(info, dims, w * h + w * 1.0))
+    # h decodes exactly; w h + w rho0 may round once (fused) or twice, hence the few ulp --
+    # far below the one-step (~1e-6) error a wrong shift would make
+    np.testing.assert_allclose(f, _pull(info, dims, w * h + w * 1.0), rtol=4e-16, atol=0)
 
 
 @pytest.mark.parametrize("name,K", [("D3Q27", 3), ("D3Q39", 4)])
