@@ -154,19 +154,33 @@ PER_MODE = [
     ("D3Q39", (192, 192, 192), 5, "f32", 0.6, 0.05, "filtered", 0.0),
     ("D3Q15", (256, 256, 256), 3, "f32", 0.6, 0.05, "filtered", 0.0),
     ("D3Q19", (256, 256, 256), 3, "f32", 0.6, 0.05, "bgk", 0.0),
+    # fixed point on the shear waves of the Galilean-invariance workloads (0.01 on U_x = 0.1),
+    # automatic range, without and with the reference shift at the background velocity
+    ("D3Q27", (192, 192, 192), 3, "q16", 0.6, 0.1, "filtered", 0.0, "shear"),
+    ("D3Q27", (192, 192, 192), 3, "q16", 0.6, 0.1, "filtered", 0.0, "shear_ref"),
+    ("D3Q39", (192, 192, 192), 4, "q16", 0.6, 0.1, "filtered", 0.0, "shear"),
+    ("D3Q39", (192, 192, 192), 4, "q16", 0.6, 0.1, "filtered", 0.0, "shear_ref"),
 ]
 
 
-def measure_lattice(lattice, dims, K, storage, tau, u0, steps, stream, model="filtered", theta=0.0):
+def measure_lattice(lattice, dims, K, storage, tau, u0, steps, stream, model="filtered", theta=0.0, field=None):
     """Autotuned MLUPS and HBM fraction of one configuration (CUDA events on the solver stream).
-    model / theta: the collision operator (BGK comparison, energy-flux weight)."""
+    model / theta: the collision operator (BGK comparison, energy-flux weight).  field: None for
+    a Taylor-Green vortex of amplitude u0; "shear" for a 0.01 shear wave on the background
+    U_x = u0 with the automatic fixed-point range; "shear_ref" the same with the fixed-point
+    values stored relative to the equilibrium at the background."""
     import torch
 
     from paper_2002_02503_gb300 import fields, lbm
 
-    rho, u = fields.taylor_green_3d(dims, u0, LATTICE_T0[lattice])
+    if field is None:
+        rho, u = fields.taylor_green_3d(dims, u0, LATTICE_T0[lattice])
+        q_range, ref = Q16_RANGE, None
+    else:
+        rho, u = fields.shear_wave(dims, 0.01, 3, 1, 0, background=(u0, 0.0, 0.0))
+        q_range, ref = 0.0, ((u0, 0.0, 0.0) if field == "shear_ref" else None)
     s = lbm.Solver(lattice, dims, tau, K, storage, stream=stream,
-                   storage_range=Q16_RANGE if storage == "q16" else None)
+                   storage_range=q_range if storage == "q16" else None, storage_reference=ref)
     lbm.lbm_set_collision(s.handle, model)
     lbm.lbm_set_energy_flux(s.handle, theta)
     s.set_fields(rho, u)
@@ -189,6 +203,8 @@ def measure_lattice(lattice, dims, K, storage, tau, u0, steps, stream, model="fi
     peak, _ = measured_peak()
     mlups = C * steps / (ms / 1e3) / 1e6
     mode = "" if model == "filtered" and theta == 0.0 else (" BGK" if model == "bgk" else " theta=%g" % theta)
+    if field is not None:
+        mode += " shear wave on U_x=%g%s" % (u0, ", reference shift" if field == "shear_ref" else "")
     return {"workload": "%s %dx%dx%d %s K=%d%s" % (lattice, dims[0], dims[1], dims[2], storage, K, mode),
             "MLUPS": mlups, "bytes_per_update": bpu, "achieved_GBs": mlups * 1e6 * bpu / 1e9,
             "frac_of_measured_hbm": mlups * 1e6 * bpu / 1e9 / peak, "ms_per_step": ms / steps,
@@ -478,7 +494,7 @@ def run_ours(a):
                 "traffic": recorded_traffic(a, variant, cpt), "peak_kind": peak_kind,
                 "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                 "algorithmic_bytes_per_launch": bpu * C,
-                "kernel": "step_%s" % ("direct" if variant == 0 else "staged")}
+                "kernel": "step_%s" % {0: "direct", 1: "staged", 2: "pair"}.get(variant, "direct")}
         cpu = None
         if not a.no_cpu_baseline:
             cpu = oracle_sample(a, a.cpu_seconds)
@@ -489,7 +505,8 @@ def run_ours(a):
         if not a.no_extras:
             with torch.cuda.stream(stream):
                 extras["per_lattice"] = [measure_lattice(*cfg, a.extra_steps, stream) for cfg in PER_LATTICE]
-                extras["per_mode"] = [measure_lattice(*cfg[:6], a.extra_steps, stream, model=cfg[6], theta=cfg[7])
+                extras["per_mode"] = [measure_lattice(*cfg[:6], a.extra_steps, stream, model=cfg[6], theta=cfg[7],
+                                                      field=cfg[8] if len(cfg) > 8 else None)
                                       for cfg in PER_MODE]
             from paper_2002_02503_gb300 import serve
 
