@@ -222,25 +222,28 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
     step_direct_body<LT, K, ST, V, BGK, THETA>(src, dst, nx, ny, ncx, P, relax, rho0, kq, qs, status);
 }
 
-// The same step capped at 96 registers, for the one configuration where the cap pays: the
-// fixed-point codec with four cells per thread on D3Q19 at K = 2 compiles to ~108 registers,
-// four 128-thread CTAs per SM; at 96 (no spills) five fit, and the step runs ~4% faster.
-// (A cap is not applied elsewhere: even a no-op cap changes the register allocation.  The
-// qualifier excludes __launch_bounds__; the launcher keeps blocks at <= 256 threads.)
-template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false>
-__global__ void __maxnreg__(96) step_direct_kernel_r96(const typename ST::S *__restrict__ src,
-                                                                              typename ST::S *__restrict__ dst,
-                                                                              int nx, int ny, int ncx, long long P,
-                                                                              typename ST::T relax,
-                                                                              typename ST::T rho0, typename ST::T kq,
-                                                                              QScale qs,
-                                                                              unsigned int *__restrict__ status) {
-    step_direct_body<LT, K, ST, V, BGK, THETA>(src, dst, nx, ny, ncx, P, relax, rho0, kq, qs, status);
+// The same step with a register cap, for the configurations where a cap pays (the cap that
+// takes one more CTA per SM without spills, chosen by measurement):
+//  - fixed point, four cells per thread, D3Q19, K = 2: ~108 registers, four 128-thread CTAs
+//    per SM; at 96 five fit and the step runs 8% faster;
+//  - fixed point, two cells per thread, D3Q39, K = 4: 138 registers, three CTAs; at 128 four.
+// A cap is not applied elsewhere: even a no-op cap changes the register allocation.  The
+// qualifier excludes __launch_bounds__; the launcher keeps blocks at <= 256 threads.
+template <class LT, int K, class ST, int V, bool BGK, bool THETA>
+constexpr int step_direct_cap() {
+    if constexpr (ST::id != LBM_STORE_Q16 || BGK || THETA) return 0;
+    else if constexpr (LT::Q == 19 && K == 2 && V == 4) return 96;
+    else if constexpr (LT::Q == 39 && K == 4 && V == 2 && !ShiftedOf<ST>::value) return 128;
+    else return 0;
 }
 
-template <class LT, int K, class ST, int V, bool BGK, bool THETA>
-constexpr bool step_direct_capped() {
-    return ST::id == LBM_STORE_Q16 && V == 4 && K == 2 && LT::Q == 19 && !BGK && !THETA;
+template <int REGS, class LT, int K, class ST, int V, bool BGK = false, bool THETA = false>
+__global__ void __maxnreg__(REGS) step_direct_kernel_capped(const typename ST::S *__restrict__ src,
+                                                            typename ST::S *__restrict__ dst, int nx, int ny,
+                                                            int ncx, long long P, typename ST::T relax,
+                                                            typename ST::T rho0, typename ST::T kq, QScale qs,
+                                                            unsigned int *__restrict__ status) {
+    step_direct_body<LT, K, ST, V, BGK, THETA>(src, dst, nx, ny, ncx, P, relax, rho0, kq, qs, status);
 }
 
 template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false>
@@ -256,8 +259,9 @@ cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream
     dim3 grid((unsigned)gx, (unsigned)a.nz);
     // (1 - 1/tau) theta / (6 T0^3): weight of the energy-flux part (Eq. pq)
     const double kq = a.relax * a.theta / (6.0 * LT::T0 * LT::T0 * LT::T0);
-    if constexpr (step_direct_capped<LT, K, ST, V, BGK, THETA>())
-        step_direct_kernel_r96<LT, K, ST, V, BGK, THETA><<<grid, block, 0, stream>>>(
+    constexpr int kCap = step_direct_cap<LT, K, ST, V, BGK, THETA>();
+    if constexpr (kCap > 0)
+        step_direct_kernel_capped<kCap, LT, K, ST, V, BGK, THETA><<<grid, block, 0, stream>>>(
             static_cast<const typename ST::S *>(a.src), static_cast<typename ST::S *>(a.dst), a.nx, a.ny, ncx, a.P,
             T(a.relax), T(a.rho0), T(kq), a.qs, a.status);
     else
