@@ -196,7 +196,7 @@ lbm_status lbm_get_storage_range(const lbm_solver *s, double *range);
  * kernels with one constant for every velocity.  For a flow
  * near a uniform U -- a wave on a background flow -- the stored values, and with them the
  * automatic range and the rounding step, shrink by the background's share.  U = {0, 0, 0}
- * (the default) turns it off; |U| <= 1/2.  Set it before lbm_set_fields; the range is
+ * (the default) turns it off; |U| <= 1/2; on D2Q9 U[2] is ignored.  Set it before lbm_set_fields; the range is
  * raised if needed so that every shift stays below 2^22 grid steps.  LBM_ERR_UNSUPPORTED
  * for the floating forms. */
 lbm_status lbm_set_storage_reference(lbm_solver *s, const double U[3]);

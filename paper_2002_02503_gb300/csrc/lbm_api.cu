@@ -799,7 +799,7 @@ lbm_status lbm_set_storage_reference(lbm_solver *s, const double U[3]) {
     double u2 = 0.0;
     for (int a = 0; a < 3; ++a) {
         if (!isfinite(U[a])) return fail(LBM_ERR_INVALID_ARG, "U must be finite");
-        u2 += U[a] * U[a];
+        if (a < s->li.D) u2 += U[a] * U[a];  // components beyond the lattice's dimension are ignored
     }
     if (u2 > 0.25) return fail(LBM_ERR_INVALID_ARG, "|U| must be <= 1/2");
     int c[kQMax * 3];
@@ -807,7 +807,7 @@ lbm_status lbm_set_storage_reference(lbm_solver *s, const double U[3]) {
     lbm_lattice_info(s->lat, nullptr, nullptr, c, nullptr, &T0, nullptr);
     if (u2 > 0.0 && !s->ks_base->shifted) return fail(LBM_ERR_UNSUPPORTED, "shifted fixed-point kernels not built");
     s->qref_on = u2 > 0.0;
-    for (int a = 0; a < 3; ++a) s->qref_u[a] = U[a];
+    for (int a = 0; a < 3; ++a) s->qref_u[a] = a < s->li.D ? U[a] : 0.0;
     // (f^eq_i(rho0, U) - w_i rho0) / w_i with the second-order equilibrium: any fixed values
     // serve (the codec adds back exactly what it takes off); these are close to a flow near U
     for (int i = 0; i < s->li.Q; ++i) {

@@ -214,6 +214,31 @@ def test_every_cells_per_thread_agrees(V):
     assert np.max(np.abs(raws[0].astype(np.int64) - raws[1].astype(np.int64))) <= 16
 
 
+@pytest.mark.parametrize("name,K,V", [("D3Q19", 2, 4), ("D3Q39", 4, 2)])
+@pytest.mark.parametrize("shift", [False, True])
+def test_register_capped_configurations_match_oracle(name, K, V, shift):
+    """The fixed-point steps that run under a register cap (D3Q19 K = 2 with four cells per
+    thread, D3Q39 K = 4 with two), forced, without and with a reference shift: within the
+    16-bit bound of the FP64 oracle after 100 steps."""
+    dims = DIMS[name]
+    D = lbm.lbm_lattice_info(name)["D"]
+    rho, u = fields.random_smooth_fields(dims, D, config_index=0, salt=53 + K)
+    f_ref, r_ref, u_ref = oracle_reference(name, K, 0.55, dims, rho, u, 100)
+    s = lbm.Solver(name, dims, 0.55, K, "q16", storage_range=0.5,
+                   storage_reference=(0.02, -0.01, 0.01) if shift else None)
+    lbm.lbm_set_kernel(s.handle, 0, V, 128)
+    assert lbm.lbm_get_kernel(s.handle) == (0, V, 128)
+    s.set_fields(rho, u)
+    s.step(100)
+    r, uu = s.moments()
+    f = s.f()
+    s.close()
+    eu = rel_u(uu, u_ref)
+    print("%s K=%d V=%d shift=%s q16 rel u %.3e" % (name, K, V, shift, eu))
+    assert eu < TOL_U16
+    assert rel_f(f, to_lib_order(name, f_ref)) < TOL_U16
+
+
 def test_bgk_and_energy_flux_run_on_fixed_point():
     name, K, dims = "D3Q19", 3, DIMS["D3Q19"]
     rho, u = fields.random_smooth_fields(dims, 3, config_index=0, salt=42)
