@@ -135,8 +135,8 @@ __device__ __forceinline__ int fastdiv(int n, unsigned int m, unsigned int s) {
 }
 
 template <class LT, int K, class ST, int MODE>
-__global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__restrict__ slots,
-                                                         const int *__restrict__ header, int step_index) {
+__device__ __forceinline__ void batch_step_body(const BatchSlot *__restrict__ slots, const int *__restrict__ header,
+                                                int step_index) {
     const int nslots = header[1];
     const int u_begin = header[2 + MODE], u_end = header[5 + MODE];
     // grid-stride over units (neighbouring CTAs work on neighbouring rows at the same time);
@@ -181,18 +181,51 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__rest
     }
 }
 
+template <class LT, int K, class ST, int MODE>
+__global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__restrict__ slots,
+                                                         const int *__restrict__ header, int step_index) {
+    batch_step_body<LT, K, ST, MODE>(slots, header, step_index);
+}
+
+// Register cap of a mode's kernel (0 = none; a no-op cap would still change the allocation).
+// Measured on 40 resident D3Q19 lattices, K = 3: the FP16 flat-pair kernel (MODE 2) at 80
+// registers instead of 96 (six 128-thread CTAs per SM instead of five, a 4-byte spill) lifts
+// the pool 1.8%; the FP32 one at 96 or 88 instead of 118, and FP16 at 72, lose.
+template <class LT, int K, class ST, int MODE>
+constexpr int batch_cap() {
+    if constexpr (MODE == 2 && LT::Q == 19 && K == 3 && ST::id == LBM_STORE_F16) return 80;
+    else return 0;
+}
+
+// The same kernel under a register cap (the qualifier excludes __launch_bounds__; blocks
+// stay at <= 256 threads).
+template <int REGS, class LT, int K, class ST, int MODE>
+__global__ void __maxnreg__(REGS) batch_step_kernel_capped(const BatchSlot *__restrict__ slots,
+                                                           const int *__restrict__ header, int step_index) {
+    batch_step_body<LT, K, ST, MODE>(slots, header, step_index);
+}
+
+using BatchKernel = void (*)(const BatchSlot *, const int *, int);
+
+template <class LT, int K, class ST, int MODE>
+BatchKernel batch_kernel() {
+    constexpr int cap = batch_cap<LT, K, ST, MODE>();
+    if constexpr (cap > 0) return batch_step_kernel_capped<cap, LT, K, ST, MODE>;
+    else return batch_step_kernel<LT, K, ST, MODE>;
+}
+
 // One step of every slot: the MODE 0 kernel with one cell per thread (cpt = 1), else the
 // MODE 1 and MODE 2 kernels; grids[m] is mode m's persistent grid.
 template <class LT, int K, class ST>
 cudaError_t launch_batch(const BatchSlot *slots, const int *header, int step_index, const int *grids, int block,
                          int cpt, cudaStream_t stream) {
     if (cpt == 2) {
-        batch_step_kernel<LT, K, ST, 1><<<grids[1], block, 0, stream>>>(slots, header, step_index);
+        batch_kernel<LT, K, ST, 1>()<<<grids[1], block, 0, stream>>>(slots, header, step_index);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        batch_step_kernel<LT, K, ST, 2><<<grids[2], block, 0, stream>>>(slots, header, step_index);
+        batch_kernel<LT, K, ST, 2>()<<<grids[2], block, 0, stream>>>(slots, header, step_index);
     } else {
-        batch_step_kernel<LT, K, ST, 0><<<grids[0], block, 0, stream>>>(slots, header, step_index);
+        batch_kernel<LT, K, ST, 0>()<<<grids[0], block, 0, stream>>>(slots, header, step_index);
     }
     return cudaGetLastError();
 }
@@ -200,10 +233,9 @@ cudaError_t launch_batch(const BatchSlot *slots, const int *header, int step_ind
 template <class LT, int K, class ST>
 int batch_occupancy(int block, int mode) {
     int n = 0;
-    cudaError_t e;
-    if (mode == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 2>, block, 0);
-    else if (mode == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 1>, block, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LT, K, ST, 0>, block, 0);
+    const BatchKernel k = mode == 2 ? batch_kernel<LT, K, ST, 2>()
+                                    : (mode == 1 ? batch_kernel<LT, K, ST, 1>() : batch_kernel<LT, K, ST, 0>());
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0);
     return e == cudaSuccess ? n : 0;
 }
 
