@@ -226,12 +226,15 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
 // takes one more CTA per SM without spills, chosen by measurement):
 //  - fixed point, four cells per thread, D3Q19, K = 2: ~108 registers, four 128-thread CTAs
 //    per SM; at 96 five fit and the step runs 8% faster;
-//  - fixed point, two cells per thread, D3Q39, K = 4: 138 registers, three CTAs; at 128 four.
+//  - fixed point, two cells per thread, D3Q39, K = 4: 138 registers, three CTAs; at 128 four;
+//  - FP32 energy-flux step, D3Q39, K = 4: 128 registers, four CTAs; at 96 five despite a
+//    56-byte spill, 1.6% faster (at 104, with four CTAs still, 2% slower).
 // A cap is not applied elsewhere: even a no-op cap changes the register allocation.  The
 // qualifier excludes __launch_bounds__; the launcher keeps blocks at <= 256 threads.
 template <class LT, int K, class ST, int V, bool BGK, bool THETA>
 constexpr int step_direct_cap() {
-    if constexpr (ST::id != LBM_STORE_Q16 || BGK || THETA) return 0;
+    if constexpr (THETA && LT::Q == 39 && K == 4 && V == 1 && ST::id == LBM_STORE_F32) return 96;
+    else if constexpr (ST::id != LBM_STORE_Q16 || BGK || THETA) return 0;
     else if constexpr (LT::Q == 19 && K == 2 && V == 4) return 96;
     else if constexpr (LT::Q == 39 && K == 4 && V == 2 && !ShiftedOf<ST>::value) return 128;
     else return 0;
