@@ -141,7 +141,8 @@ lbm_status lbm_mode_amplitude(lbm_solver *s, const int64_t k[3], int component, 
  * the step counter.  get synchronises and, like the other synchronising calls, first
  * reports a pending status (LBM_ERR_RANGE, LBM_ERR_TIMEOUT) instead of saving a state known
  * to be invalid; set replaces the state and clears any pending status of the old one (so
- * does lbm_set_fields).  A fixed-point checkpoint restores under the range it was taken with. */
+ * does lbm_set_fields).  A fixed-point checkpoint restores under the range and reference shift
+ * it was taken with (the stored codes carry neither). */
 lbm_status lbm_get_distributions(lbm_solver *s, void *dst, size_t bytes, lbm_mem mem, int64_t *t);
 lbm_status lbm_set_distributions(lbm_solver *s, const void *src, size_t bytes, lbm_mem mem, int64_t t);
 
@@ -190,15 +191,17 @@ lbm_status lbm_get_storage_range(const lbm_solver *s, double *range);
 
 /* Reference shift of the fixed-point storage (LBM_STORE_Q16): the stored value of velocity i
  * becomes h_i - href_i, with href_i = rho0 (s_i + (s_i^2 - |U|^2/T0) / 2), s_i = c_i.U / T0,
- * the scaled equilibrium at the reference velocity U (rounded to the grid, so decode adds
- * back exactly what encode takes off).  The shifted codec holds one constant per velocity, so
+ * the scaled equilibrium at the reference velocity U (Eq. hermite truncated at second order;
+ * rounded to the grid, so decode adds back exactly what encode takes off).  The shift is a
+ * storage device with no counterpart in the paper.  The shifted codec holds one constant per velocity, so
  * it runs its own kernels, used only while a shift is set; unshifted solvers keep the
- * kernels with one constant for every velocity.  For a flow
- * near a uniform U -- a wave on a background flow -- the stored values, and with them the
- * automatic range and the rounding step, shrink by the background's share.  U = {0, 0, 0}
- * (the default) turns it off; |U| <= 1/2; on D2Q9 U[2] is ignored.  Set it before lbm_set_fields; the range is
- * raised if needed so that every shift stays below 2^22 grid steps.  LBM_ERR_UNSUPPORTED
- * for the floating forms. */
+ * kernels with one constant for every velocity.  For a flow near a uniform U -- a wave on a
+ * background flow -- the stored values, and with them the automatic range and the rounding
+ * step, shrink by the background's share.  U = {0, 0, 0} (the default) turns it off;
+ * |U| <= 1/2; on D2Q9 U[2] is ignored.  Set it before lbm_set_fields; the range is
+ * raised if needed so that every shift stays below 2^22 grid steps.  LBM_ERR_INVALID_ARG for
+ * a NULL U, a non-finite component or |U| > 1/2; LBM_ERR_UNSUPPORTED for the floating forms;
+ * the solver is unchanged on error. */
 lbm_status lbm_set_storage_reference(lbm_solver *s, const double U[3]);
 
 /* Autotuner: times every built kernel configuration for this solver on its own
