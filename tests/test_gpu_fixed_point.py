@@ -478,6 +478,43 @@ def test_decode_with_reference_shift_is_exact():
     np.testing.assert_allclose(f, _pull(info, dims, w * h + w * 1.0), rtol=4e-16, atol=0)
 
 
+def _decoded(name, dims, R, U, g):
+    s = lbm.Solver(name, dims, 0.6, 3, "q16", storage_range=R)
+    if U is not None:
+        lbm.lbm_set_storage_reference(s.handle, U)
+    lbm.lbm_set_distributions(s.handle, g, 0)
+    f = s.f()
+    s.close()
+    return f
+
+
+def test_reference_shift_arguments():
+    """Invalid references are refused and leave the solver's shift as it was; the floating forms
+    have no shift; on D2Q9 the third component is ignored."""
+    name, dims, R = "D3Q19", (12, 7, 5), 0.25
+    info = lbm.lbm_lattice_info(name)
+    g = np.full((info["Q"], int(np.prod(dims))), 32768, dtype=np.uint16)  # h = 0 before the shift
+    s = lbm.Solver(name, dims, 0.6, 3, "q16", storage_range=R, storage_reference=(0.1, 0.0, 0.0))
+    for bad in ((0.6, 0.0, 0.0), (float("nan"), 0.0, 0.0), (0.0, float("inf"), 0.0), (0.3, 0.3, 0.3)):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_storage_reference(s.handle, bad)
+        assert e.value.status == lbm.LBM_ERR_INVALID_ARG, bad
+    lbm.lbm_set_distributions(s.handle, g, 0)
+    f_after = s.f()
+    s.close()
+    np.testing.assert_array_equal(f_after, _decoded(name, dims, R, (0.1, 0.0, 0.0), g))
+    assert not np.array_equal(f_after, _decoded(name, dims, R, None, g))  # the shift is still on
+    s = lbm.Solver(name, dims, 0.6, 3, "f16")
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_storage_reference(s.handle, (0.1, 0.0, 0.0))
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+    s.close()
+    d2 = (16, 10, 1)
+    g2 = np.random.default_rng(5).integers(0, 65536, size=(9, 160), dtype=np.uint16)
+    np.testing.assert_array_equal(_decoded("D2Q9", d2, R, (0.1, 0.05, 0.4), g2),
+                                  _decoded("D2Q9", d2, R, (0.1, 0.05, 0.0), g2))
+
+
 @pytest.mark.parametrize("name,K", [("D3Q27", 3), ("D3Q39", 4)])
 def test_reference_shift_on_a_background_flow(name, K):
     """A shear wave (0.01) on U_x = 0.1: with the storage shifted by the equilibrium at U, the
