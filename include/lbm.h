@@ -306,9 +306,10 @@ lbm_status lbm_pool_get_storage_range(const lbm_pool *p, double *range);
 lbm_status lbm_pool_request_range(const lbm_pool *p, int64_t id, double *range);
 
 /* Kernel configuration of the batched step.  cells_per_thread: the most cells a thread
- * updates, 1 or 2 (the default); a request whose nx is odd always runs 1, so a request's
- * arithmetic depends on this setting and its own dims only, never on the other residents.
- * Two cells per thread run the collision on the paired FP32 instructions.  block_threads:
+ * updates, 1 or 2 (the default).  With 2, a request runs two x-neighbours per thread (even
+ * nx) or two consecutive cells of the flat index (odd nx), so a request's arithmetic depends
+ * on this setting and its own dims only, never on the other residents.  Two cells per
+ * thread run the collision on the paired FP32 instructions.  block_threads:
  * 128 or 256 (the default).  Zero keeps the current value.  Waits for the launched chunks.
  * LBM_ERR_UNSUPPORTED for other values. */
 lbm_status lbm_pool_set_kernel(lbm_pool *p, int cells_per_thread, int block_threads);
