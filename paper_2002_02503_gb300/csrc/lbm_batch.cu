@@ -107,6 +107,8 @@ struct lbm_pool {
     Arena arena;
     int max_slots;
     cudaStream_t compute, io, capture;
+    cudaStream_t side;             // second stream of the two slot-mode kernels of a step
+    cudaEvent_t fork, join;        // fork to / join from the side stream
     int block;
     int grids[3];  // persistent grid of each slot-mode kernel
     int cpt;  // most cells per thread a slot may run (1 or 2)
@@ -158,7 +160,8 @@ lbm_status get_graph(lbm_pool *p, long long chunk, int b, cudaGraphExec_t *out) 
     if (e != cudaSuccess) return set_cuda_error(e, "pool: begin capture");
     cudaError_t le = cudaSuccess;
     for (long long s = 0; s < chunk && le == cudaSuccess; ++s)
-        le = p->ks->batch(p->d_table[b], p->d_header[b], int(s), p->grids, p->block, p->cpt, p->capture);
+        le = p->ks->batch(p->d_table[b], p->d_header[b], int(s), p->grids, p->block, p->cpt, p->capture, p->side,
+                          p->fork, p->join);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(p->capture, &g);
     if (le != cudaSuccess) {
@@ -370,6 +373,9 @@ lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, 
             e = cudaMallocHost(reinterpret_cast<void **>(&p->h_header[b]), kBatchHeaderInts * sizeof(int));
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
     for (int k = 0; k < kEventRing && e == cudaSuccess; ++k)
         e = cudaEventCreateWithFlags(&p->chunk_events[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -679,10 +685,12 @@ lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us) {
             e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], kBatchHeaderInts * sizeof(int),
                             cudaMemcpyHostToDevice, p->compute);
         for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grids, p->block, p->cpt, p->compute);
+            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grids, p->block, p->cpt, p->compute, p->side,
+                             p->fork, p->join);
         if (e == cudaSuccess) e = cudaEventRecord(e0, p->compute);
         for (int it = 0; it < iters && e == cudaSuccess; ++it)
-            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grids, p->block, p->cpt, p->compute);
+            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grids, p->block, p->cpt, p->compute, p->side,
+                             p->fork, p->join);
         if (e == cudaSuccess) e = cudaEventRecord(e1, p->compute);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -775,6 +783,10 @@ lbm_status lbm_pool_destroy(lbm_pool *p) {
         if (p->h_table[b]) cudaFreeHost(p->h_table[b]);
         if (p->h_header[b]) cudaFreeHost(p->h_header[b]);
     }
+    if (p->side) cudaStreamSynchronize(p->side);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->join) cudaEventDestroy(p->join);
+    if (p->side) cudaStreamDestroy(p->side);
     if (p->capture) cudaStreamDestroy(p->capture);
     delete p;
     return LBM_OK;

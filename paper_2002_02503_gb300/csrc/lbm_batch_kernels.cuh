@@ -215,15 +215,29 @@ BatchKernel batch_kernel() {
 }
 
 // One step of every slot: the MODE 0 kernel with one cell per thread (cpt = 1), else the
-// MODE 1 and MODE 2 kernels; grids[m] is mode m's persistent grid.
+// MODE 1 and MODE 2 kernels; grids[m] is mode m's persistent grid.  The two modes touch
+// disjoint slots, so with a side stream they run side by side: the second kernel's CTAs fill
+// the SMs the first one's last wave leaves idle.
 template <class LT, int K, class ST>
 cudaError_t launch_batch(const BatchSlot *slots, const int *header, int step_index, const int *grids, int block,
-                         int cpt, cudaStream_t stream) {
+                         int cpt, cudaStream_t stream, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
     if (cpt == 2) {
+        const bool split = side && fork && join;
+        cudaError_t e = cudaSuccess;
+        if (split) {
+            e = cudaEventRecord(fork, stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+            if (e != cudaSuccess) return e;
+        }
         batch_kernel<LT, K, ST, 1>()<<<grids[1], block, 0, stream>>>(slots, header, step_index);
-        cudaError_t e = cudaGetLastError();
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        batch_kernel<LT, K, ST, 2>()<<<grids[2], block, 0, stream>>>(slots, header, step_index);
+        batch_kernel<LT, K, ST, 2>()<<<grids[2], block, 0, split ? side : stream>>>(slots, header, step_index);
+        e = cudaGetLastError();
+        if (e != cudaSuccess || !split) return e;
+        e = cudaEventRecord(join, side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, join, 0);
+        return e;
     } else {
         batch_kernel<LT, K, ST, 0>()<<<grids[0], block, 0, stream>>>(slots, header, step_index);
     }

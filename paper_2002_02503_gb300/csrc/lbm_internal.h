@@ -137,8 +137,11 @@ inline void fastdiv_init(unsigned int d, unsigned int *m, unsigned int *s) {
 }
 
 typedef cudaError_t (*step_fn)(const StepArgs &, int block_threads, cudaStream_t);
+// side, fork, join: a second stream and two events; when given, the two slot-mode kernels
+// of cells_per_thread 2 run side by side (fork on the first stream, join back into it).
 typedef cudaError_t (*batch_fn)(const BatchSlot *slots, const int *header, int step_index, const int *grids,
-                                int block, int cells_per_thread, cudaStream_t);
+                                int block, int cells_per_thread, cudaStream_t, cudaStream_t side,
+                                cudaEvent_t fork, cudaEvent_t join);
 typedef cudaError_t (*init_fn)(const InitArgs &, cudaStream_t);
 typedef cudaError_t (*pull_fn)(const PullArgs &, cudaStream_t);
 typedef cudaError_t (*reduce_fn)(const ReduceArgs &, cudaStream_t);
