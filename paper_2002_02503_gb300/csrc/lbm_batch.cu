@@ -4,9 +4,11 @@
 //
 // Execution model
 //   compute stream : per chunk, an H2D copy of the slot table then one graph of
-//                    `chunk` batch-kernel launches (step_index 0..chunk-1).  Each
-//                    launch is one step of every resident lattice that still has
-//                    steps left; the kernel boundary is the step's global barrier.
+//                    `chunk` steps (step_index 0..chunk-1).  Each step is one launch
+//                    per slot mode over every resident lattice of that mode that still
+//                    has steps left (with two cells per thread the two modes' kernels
+//                    are forked onto a side stream and joined, so they overlap); the
+//                    join is the step's global barrier.
 //   io stream      : fields upload + f^eq initialisation of new requests, and the
 //                    pull of rho, u of finished ones, overlapping the chunks.
 // The slot table and its pinned host mirror are double-buffered, so at most two
