@@ -24,6 +24,7 @@
 #include <mutex>
 #include <vector>
 
+#include "lbm_arena.h"
 #include "lbm_internal.h"
 #include "lbm_trace.h"
 
@@ -34,52 +35,6 @@ namespace {
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 constexpr int kEventRing = 64;
-
-struct Arena {
-    char *base = nullptr;
-    size_t bytes = 0;
-    std::map<size_t, size_t> free_;  // offset -> size, coalesced
-
-    void init(char *b, size_t n) {
-        base = b;
-        bytes = n;
-        free_.clear();
-        if (n) free_[0] = n;
-    }
-    bool alloc(size_t n, size_t *off) {
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= n) {
-                *off = it->first;
-                const size_t rest = it->second - n;
-                const size_t roff = it->first + n;
-                free_.erase(it);
-                if (rest) free_[roff] = rest;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t n) {
-        auto it = free_.emplace(off, n).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t free_bytes() const {
-        size_t s = 0;
-        for (auto &kv : free_) s += kv.second;
-        return s;
-    }
-};
 
 struct Request {
     int64_t id;
