@@ -177,7 +177,10 @@ lbm_status lbm_set_collision(lbm_solver *s, lbm_collision model);
  * runs one cell per thread.  LBM_ERR_UNSUPPORTED for K = 2. */
 lbm_status lbm_set_energy_flux(lbm_solver *s, double theta);
 
-/* Range R of the fixed-point storage (LBM_STORE_Q16): -R <= h_i < R, grid step R / 2^15.
+/* Range R of the fixed-point storage (LBM_STORE_Q16): -R <= h_i < R, grid step d = R / 2^15.
+ * A value is stored as its nearest grid point (ties to an even code); one whose nearest point
+ * does not fit -- at or above R - d/2, or below -R - d/4 (where FP32 rounds at d/2) -- is
+ * reported as out of range.
  * R must be a power of two in [2^-8, 2^8], or 0 for an automatic range: each later
  * lbm_set_fields first measures max |h| of the initial f^eq on the device and takes the
  * smallest power of two R >= 1.25 max |h| (read it back with lbm_get_storage_range); a later
