@@ -26,6 +26,8 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+from paper_2002_02503_gb300 import fields  # noqa: E402  (seeded inputs only)
+
 LATTICE_Q = {"D2Q9": 9, "D3Q15": 15, "D3Q19": 19, "D3Q27": 27, "D3Q39": 39}
 LATTICE_T0 = {"D2Q9": 1.0 / 3.0, "D3Q15": 1.0 / 3.0, "D3Q19": 1.0 / 3.0, "D3Q27": 1.0 / 3.0, "D3Q39": 2.0 / 3.0}
 STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8, "q16": 2}
@@ -56,8 +58,13 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     p.add_argument("--no-extras", action="store_true", help="skip the per-lattice and serving measurements")
-    p.add_argument("--serve", type=int, default=200,
+    p.add_argument("--serve", type=int, default=2000,
                    help="requests of the serving trace (2000 = the full Poisson workload; 0 = skip)")
+    p.add_argument("--capacity-requests", type=int, default=500,
+                   help="requests of the all-at-once capacity runs (the first ones of the trace)")
+    p.add_argument("--no-accuracy", action="store_true",
+                   help="skip the per-config error of each storage form (on by default)")
+    p.add_argument("--no-512", action="store_true", help="accuracy: skip the 512^3 configuration")
     p.add_argument("--serve-rate", type=float, default=50.0)
     p.add_argument("--extra-steps", type=int, default=200)
     p.add_argument("--precision-report", action="store_true",
@@ -246,42 +253,225 @@ def initial_fields(a):
 
 
 # ------------------------------------------------------------------ CPU oracle timing
-def oracle_sample(a, seconds):
-    """Time the FP64 oracle on a sub-lattice of the workload (same lattice, K, tau)."""
+def host_ram_bytes():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        return 0
+
+
+def oracle_sample(a, seconds, min_steps=10):
+    """Time the FP64 oracle on the workload itself (same lattice, dims, K, tau, fields), at least
+    min_steps steps on all host cores, plus one step on a single core.  Falls back to a
+    sub-lattice, and says so, only when the oracle's two FP64 copies of f would not fit in a
+    quarter of the host's memory."""
     import oracle
-    from paper_2002_02503_gb300 import fields
 
     nthreads = oracle.default_threads()
-    side = 64 if a.lattice != "D3Q39" else 48
-    dims = (side, side, side) if a.lattice != "D2Q9" else (256, 256, 1)
+    Q = LATTICE_Q[a.lattice]
+    dims = tuple(a.dims)
+    sub = ""
+    if 2 * Q * 8 * int(np.prod(dims)) > host_ram_bytes() / 4:
+        side = 64 if a.lattice != "D3Q39" else 48
+        dims = (side, side, side) if a.lattice != "D2Q9" else (256, 256, 1)
+        sub = " (sub-lattice: the full size does not fit the host's memory)"
     D = 2 if a.lattice == "D2Q9" else 3
     if D == 3:
         rho, u = fields.taylor_green_3d(dims, a.u0, LATTICE_T0[a.lattice])
     else:
         rho, u = fields.taylor_green_2d(dims, a.u0, LATTICE_T0[a.lattice], D=2)
     f = oracle.init_eq(a.lattice, a.K, dims, rho, u)
+    del rho, u
     C = int(np.prod(dims))
     t0 = time.perf_counter()
     f = oracle.run(a.lattice, a.K, a.tau, dims, f, 1, nthreads)
     one = time.perf_counter() - t0
-    steps = int(max(1, min(200, seconds / max(one, 1e-6))))
+    steps = int(max(min_steps, min(200, seconds / max(one, 1e-6))))
     t0 = time.perf_counter()
-    oracle.run(a.lattice, a.K, a.tau, dims, f, steps, nthreads)
+    f = oracle.run(a.lattice, a.K, a.tau, dims, f, steps, nthreads)
     dt = time.perf_counter() - t0
-    # the same sub-lattice on one core, for a few steps
-    steps1 = int(max(1, min(steps, 0.25 * seconds / max(one * nthreads, 1e-6))))
+    # one step on one core (the same lattice)
     t0 = time.perf_counter()
-    oracle.run(a.lattice, a.K, a.tau, dims, f, steps1, 1)
+    oracle.run(a.lattice, a.K, a.tau, dims, f, 1, 1)
     dt1 = time.perf_counter() - t0
+    del f
     return {"value": C * steps / dt / 1e6, "unit": "MLUPS", "cores": nthreads, "kind": "oracle",
-            "sample": "%s K=%d tau=%g Taylor-Green sub-lattice %dx%dx%d, %d steps, %.1f s" % (
-                a.lattice, a.K, a.tau, dims[0], dims[1], dims[2], steps, dt),
-            "single_core": {"value": C * steps1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
-                            "sample": "the same sub-lattice, %d steps, %.1f s" % (steps1, dt1)}}
+            "sample": "%s K=%d tau=%g Taylor-Green %dx%dx%d%s, %d steps on %d threads, %.1f s" % (
+                a.lattice, a.K, a.tau, dims[0], dims[1], dims[2], sub, steps, nthreads, dt),
+            "single_core": {"value": C / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
+                            "sample": "one step of the same lattice, %.1f s" % dt1}}
+
+
+# The accuracy anchor: the FP64 oracle on a 64^3 lattice of the 16-bit Taylor-Green workload
+# (D3Q19, u0 = 0.05, tau = 0.52, K = 2, 500 steps), against which every storage form of the GPU
+# path is compared directly; the larger configurations compare with the library's FP64 path.
+ANCHOR = ("D3Q19", (64, 64, 64), 2, 0.52, 0.05, 500)
+
+
+def oracle_anchor():
+    """(rho, u) of the FP64 oracle after ANCHOR's steps, with its wall time."""
+    import oracle
+
+    lat, dims, K, tau, u0, steps = ANCHOR
+    rho, u = fields.taylor_green_3d(dims, u0, LATTICE_T0[lat])
+    t0 = time.perf_counter()
+    f = oracle.run(lat, K, tau, dims, oracle.init_eq(lat, K, dims, rho, u), steps)
+    r, uu = oracle.moments(lat, dims, f)
+    return {"rho": r, "u": uu, "seconds": time.perf_counter() - t0}
+
+
+def cpu_baseline_leg(a, seconds):
+    """The oracle's part of the run: its timing on the workload, and the anchor of the accuracy
+    report (None when the accuracy report is off)."""
+    cpu = None if a.no_cpu_baseline else oracle_sample(a, seconds)
+    anchor = None if a.no_accuracy else oracle_anchor()
+    return cpu, anchor
+
+
+# ------------------------------------------------------------------ accuracy of the storage forms
+ACCURACY_FORMS = ("f32", "f16", "bf16", "q16")
+# (key, dims, tau, steps): the stated Taylor-Green configurations (D3Q19, u0 = 0.05, K = 2)
+ACCURACY_CONFIGS = [("256^3 tau=0.55 1000 steps", (256, 256, 256), 0.55, 1000),
+                    ("512^3 tau=0.52 500 steps", (512, 512, 512), 0.52, 500)]
+U16_BOUND = 1e-3  # relative error on u the 16-bit forms are held to
+
+
+def _errors(r, uu, r_ref, u_ref):
+    return (float(np.max(np.abs(uu - u_ref)) / np.max(np.abs(u_ref))),
+            float(np.max(np.abs(r - r_ref) / r_ref)))
+
+
+def _run_form(dims, tau, steps, storage, rho, u, stream):
+    import torch
+
+    from paper_2002_02503_gb300 import lbm
+
+    s = lbm.Solver("D3Q19", dims, tau, 2, storage, stream=stream,
+                   storage_range=Q16_RANGE if storage == "q16" else None)
+    s.set_fields(rho, u)
+    s.step(steps)
+    r, uu = s.moments()
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return r, uu
+
+
+def accuracy_report(stream, anchor, with_512=True):
+    """Relative error on u (max|du| / max|u|) and rho (max |drho| / rho) of every storage form:
+    at the stated Taylor-Green configurations against the library's FP64 path (the oracle is too
+    slow there), and at the 64^3 anchor against the FP64 oracle itself, which also gives the FP64
+    path's own distance from the oracle -- the link of the chain."""
+    rel_u, rel_rho = {}, {}
+    for key, dims, tau, steps in ACCURACY_CONFIGS:
+        if dims[0] == 512 and not with_512:
+            continue
+        rho, u = fields.taylor_green_3d(dims, 0.05, LATTICE_T0["D3Q19"])
+        r_ref, u_ref = _run_form(dims, tau, steps, "f64", rho, u, stream)
+        rel_u[key], rel_rho[key] = {}, {}
+        for storage in ACCURACY_FORMS:
+            r, uu = _run_form(dims, tau, steps, storage, rho, u, stream)
+            eu, er = _errors(r, uu, r_ref, u_ref)
+            rel_u[key][storage], rel_rho[key][storage] = float("%.2g" % eu), float("%.2g" % er)
+            del r, uu
+        del rho, u, r_ref, u_ref
+    if anchor is not None:
+        lat, dims, K, tau, u0, steps = ANCHOR
+        key = "64^3 tau=0.52 500 steps vs oracle"
+        rho, u = fields.taylor_green_3d(dims, u0, LATTICE_T0[lat])
+        rel_u[key], rel_rho[key] = {}, {}
+        for storage in ("f64",) + ACCURACY_FORMS:
+            r, uu = _run_form(dims, tau, steps, storage, rho, u, stream)
+            eu, er = _errors(r, uu, anchor["rho"], anchor["u"])
+            rel_u[key][storage], rel_rho[key][storage] = float("%.2g" % eu), float("%.2g" % er)
+    stated = [k for k, _, _, _ in ACCURACY_CONFIGS if k in rel_u]
+    meets = sorted(f for f in ACCURACY_FORMS if all(rel_u[k][f] <= U16_BOUND for k in stated))
+    return {"vs": "FP64 path of the library; the 64^3 row: the FP64 oracle", "bound_rel_u": U16_BOUND,
+            "within_bound_at_stated_sizes": meets, "rel_u": rel_u, "rel_rho": rel_rho}
 
 
 # ------------------------------------------------------------------ clocks
-class ClockSampler:
+class NvmlClockSampler:
+    """SM clock, power and clock-event reasons of one GPU, read through NVML (the library
+    nvidia-smi queries) about every millisecond while ``active`` is set, so that even a timed
+    region of a few milliseconds is covered.  Read-only queries: no setting is changed."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, torch_index):
+        import ctypes
+
+        self.ct = ctypes
+        self.rows = []
+        self.active = False
+        self.ok = False
+        self._stop = False
+        try:
+            self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return
+        if self.nv.nvmlInit_v2() != 0:
+            return
+        self.h = ctypes.c_void_p()
+        found = False
+        try:
+            import torch
+
+            uid = str(torch.cuda.get_device_properties(torch_index).uuid)
+            uid = uid if uid.startswith("GPU-") else "GPU-" + uid
+            found = self.nv.nvmlDeviceGetHandleByUUID(uid.encode(), ctypes.byref(self.h)) == 0
+        except (AttributeError, RuntimeError):
+            found = False
+        if not found:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            ids = [v for v in vis.split(",") if v.strip().isdigit()]
+            phys = int(ids[torch_index]) if torch_index < len(ids) else torch_index
+            found = self.nv.nvmlDeviceGetHandleByIndex_v2(phys, ctypes.byref(self.h)) == 0
+        if not found:
+            return
+        self.reasons_fn = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(self.nv, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if self.nv.nvmlDeviceGetMaxClockInfo(
+            self.h, self.NVML_CLOCK_SM, ctypes.byref(mx)) == 0 else None
+        self.ok = True
+
+    def start(self):
+        if not self.ok:
+            return
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def _run(self):
+        ct = self.ct
+        mhz, reasons, mw = ct.c_uint(), ct.c_ulonglong(), ct.c_uint()
+        while not self._stop:
+            if self.active:
+                if self.nv.nvmlDeviceGetClockInfo(self.h, self.NVML_CLOCK_SM, ct.byref(mhz)) == 0:
+                    r = reasons.value if self.reasons_fn and self.reasons_fn(self.h, ct.byref(reasons)) == 0 else 0
+                    p = mw.value / 1000.0 if self.nv.nvmlDeviceGetPowerUsage(self.h, ct.byref(mw)) == 0 else None
+                    self.rows.append((float(mhz.value), int(r), p))
+                time.sleep(0.0005)
+            else:
+                time.sleep(0.002)
+
+    def stop(self):
+        self._stop = True
+        if self.ok and getattr(self, "thread", None) is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm = [r[0] for r in self.rows]
+        reasons = sorted({n for r in self.rows for bit, n in self.REASONS.items() if r[1] & bit})
+        power = [r[2] for r in self.rows if r[2] is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz if self.ok else None,
+                "reasons": reasons, "samples": len(sm), "power_w_max": max(power) if power else None,
+                "source": "NVML, polled about every 1 ms during the timed region"}
+
+
+class SmiClockSampler:
+    """The same record from nvidia-smi every 100 ms: the fallback where NVML cannot be loaded."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -331,7 +521,12 @@ class ClockSampler:
                 if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi every 100 ms during the timed region"}
+
+
+def clock_sampler(index):
+    s = NvmlClockSampler(index)
+    return s if s.ok else SmiClockSampler(index)
 
 
 # ------------------------------------------------------------------ roofline helpers
@@ -393,7 +588,7 @@ def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    cpu = oracle_sample(a, a.cpu_seconds)
+    cpu = oracle_sample(a, a.cpu_seconds, min_steps=min(10, max(1, a.steps)))
     out = {"metric": "MLUPS", "value": cpu["value"], "unit": "MLUPS", "n_gpus": a.gpus, "steps": a.steps,
            "warmup": a.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic (Taylor-Green initial field)", "impl": "reference",
@@ -442,7 +637,7 @@ def run_ours(a):
         s.step(a.warmup)
         barrier()
 
-        clocks = ClockSampler(dev)
+        clocks = clock_sampler(dev)
         clocks.start()
         time.sleep(0.3)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -495,9 +690,7 @@ def run_ours(a):
                 "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                 "algorithmic_bytes_per_launch": bpu * C,
                 "kernel": "step_%s" % {0: "direct", 1: "staged", 2: "pair"}.get(variant, "direct")}
-        cpu = None
-        if not a.no_cpu_baseline:
-            cpu = oracle_sample(a, a.cpu_seconds)
+        cpu, anchor = cpu_baseline_leg(a, a.cpu_seconds)
         extras = {}
         if a.precision_report:
             with torch.cuda.stream(stream):
@@ -517,14 +710,12 @@ def run_ours(a):
                 r["frac_of_measured_hbm"] = r["MLUPS"] * 1e6 * r["bytes_per_update"] / 1e9 / peak
                 extras["batched"].append(r)
             if a.serve > 0:
-
                 trace = serve.make_trace(a.serve, rate=a.serve_rate)
                 pool_stats, _ = serve.serve_pool(trace)
-                pool16_stats, _ = serve.serve_pool(trace, storage="f16")
                 poolq_stats, _ = serve.serve_pool(trace, storage="q16", storage_range=0.0)
                 plain_stats, _ = serve.serve_plain(trace)
-                # capacity: the same requests all arriving at once
-                burst = [dict(r, arrival=0.0) for r in trace]
+                # capacity: the first requests of the trace, all arriving at once
+                burst = [dict(r, arrival=0.0) for r in trace[:a.capacity_requests]]
                 burst_pool, _ = serve.serve_pool(burst)
                 burst_poolq, _ = serve.serve_pool(burst, storage="q16", storage_range=0.0)
                 burst_plain, _ = serve.serve_plain(burst)
@@ -532,10 +723,13 @@ def run_ours(a):
                 extras["serving"] = {
                     "workload": "%d D3Q19 Taylor-Green solves, side log-uniform 32-128, tau U[0.52,1], "
                                 "u0 U[0.01,0.08], 100-2000 steps, Poisson %g/s, FP32, K=3" % (a.serve, a.serve_rate),
-                    "pool": pool_stats, "pool_f16_storage": pool16_stats,
-                    "pool_q16_storage_per_request_range": poolq_stats, "plain_fifo": plain_stats,
-                    "capacity_all_at_once": {"pool": burst_pool, "pool_q16_storage_per_request_range": burst_poolq,
+                    "pool": pool_stats, "pool_q16_storage_per_request_range": poolq_stats, "plain_fifo": plain_stats,
+                    "capacity_all_at_once": {"requests": len(burst), "pool": burst_pool,
+                                             "pool_q16_storage_per_request_range": burst_poolq,
                                              "plain_fifo": burst_plain}}
+        if not a.no_accuracy:
+            with torch.cuda.stream(stream):
+                extras["accuracy"] = accuracy_report(stream, anchor, with_512=not a.no_512)
         out = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": DTYPE_NAME[a.storage], "data": "synthetic (Taylor-Green initial field)",
@@ -544,7 +738,24 @@ def run_ours(a):
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps,
                "clocks": clocks.summary(),
                "conservation": {"mass": cons[0], "momentum": list(cons[1:])}}
+        # compact summaries last, where a truncated tail of the line still shows them
+        accuracy = extras.pop("accuracy", None)
         out.update(extras)
+        if "serving" in extras:
+            sv = extras["serving"]
+            out["serving_summary"] = {
+                k: {"solves_per_s": round(v["solves_per_s"], 1), "p50_s": round(v["p50_latency_s"], 3),
+                    "p99_s": round(v["p99_latency_s"], 3)}
+                for k, v in (("pool_f32", sv["pool"]), ("pool_q16", sv["pool_q16_storage_per_request_range"]),
+                             ("fifo_f32", sv["plain_fifo"]))}
+            out["serving_summary"]["requests"] = a.serve
+        gi = next((r for r in extras.get("per_lattice", []) if r["workload"].startswith("D3Q19 256x256x256 f32 K=3")),
+                  None)
+        if gi is not None:
+            out["headline_gi"] = {"workload": "D3Q19 256^3 FP32 Taylor-Green tau=0.55, K=3 (Eq. filter-1st)",
+                                  "MLUPS": round(gi["MLUPS"], 1), "frac": round(gi["frac_of_measured_hbm"], 3)}
+        if accuracy is not None:
+            out["accuracy"] = accuracy
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -227,12 +227,22 @@ lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us);
  * counterpart to this call: it is a deployment convenience.
  *   distributions  device pointer to Q*nx*ny*nz stored values in the layout
  *                  lbm_get_distributions produces (any solver's raw state)
+ *   dims           the same limits as lbm_create (nz == 1 for D2Q9, each side
+ *                  >= the largest velocity component), and nz <= 4096
  *   out            four doubles, host or device memory as out_mem says; a host
- *                  output makes the call synchronise the stream
- * Scratch: a fixed device array inside the library (about 128 KiB per GPU that
- * loads it, held until the process exits) with room for nz <= 4096 z-planes;
- * larger nz is rejected with LBM_ERR_INVALID_ARG.  The first call on a device
- * looks up that array's device address, so make it before any stream capture.
+ *                  output makes the call synchronise the stream and return
+ *                  LBM_ERR_NONFINITE when a sum is not finite; a device output
+ *                  is left for the caller to read later, so that check is not
+ *                  made (the same state can then return LBM_OK)
+ * Scratch: a fixed device array inside the library (about 128 KiB per GPU,
+ * held until the process exits) with room for nz <= 4096 z-planes; larger nz
+ * is rejected with LBM_ERR_INVALID_ARG.  Under CUDA's lazy module loading (the
+ * default) that array is committed on a device at the first call there, not
+ * when the library is loaded: a caller whose device memory another allocator
+ * will reserve should make one call early.  The first call on a device also
+ * looks up the array's device address, so make it before any stream capture;
+ * later calls outside capture look it up again, so a device reset between
+ * calls does not leave a stale address.
  * All calls share the array: calls whose GPU work overlaps race on it and must
  * be serialised by the caller. */
 lbm_status lbm_conservation_noalloc(lbm_lattice lattice, lbm_storage storage, const int64_t dims[3], double rho0,

@@ -11,11 +11,18 @@
 //
 // Its scratch (one FP64 partial sum per z-plane and value, plus the final four
 // sums) lives in the file-scope device array below, of a fixed size.  Every GPU
-// that loads the library holds this array (about 128 KiB) until the process
-// exits.  Host code must not pass the array's name to a kernel: on the host the
-// name is only a stand-in, not a device address.  The device address is looked
-// up with cudaGetSymbolAddress once per device, on the first call made while
-// that device is current; make that first call before any stream capture.
+// on which the library's kernels are loaded holds this array (about 128 KiB)
+// until the process exits.  Under CUDA's lazy module loading (the default since
+// CUDA 12.2) that memory is committed at the first call on each device, not when
+// the library is loaded, so a caller whose device memory another allocator will
+// reserve should make one call early.  Host code must not pass the array's name
+// to a kernel: on the host the name is only a stand-in, not a device address.
+// The device address comes from cudaGetSymbolAddress with the device current.
+// The first call on a device does this set-up; make it before any stream
+// capture.  Later calls look the address up again (a cheap host query), so that
+// a device reset between calls, after which the module and its array may be
+// loaded at a new address, is harmless; a call on a capturing stream reuses the
+// address found by the last call on that device.
 //
 // All calls share the one array, and it keeps the contents of the last call.
 // Each call first writes every slot it later reads (nothing accumulates across
@@ -35,22 +42,29 @@ namespace lbm {
 namespace {
 
 constexpr int kNoallocMaxPlanes = 4096;  // largest nz this entry point accepts
-constexpr int kNoallocThreads = 256;
+constexpr int kNoallocThreads = kReduceThreads;
 constexpr int kMaxDevices = 64;
+// block_reduce_store sizes its shared array for kReduceThreads threads per block
+static_assert(kNoallocThreads == kReduceThreads, "plane_sums_kernel runs the shared block reduction");
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocMaxPlanes * 4 + 4];
 
 std::mutex g_addr_mutex;
 double *g_addr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device (looked up once per device).
-cudaError_t scratch_address(double **out) {
+// Device address of the scratch array on the current device.  Outside stream capture it is
+// looked up on every call (a device reset may move the array); on a capturing stream the
+// address found by the last call on this device is reused.
+cudaError_t scratch_address(cudaStream_t stream, double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
@@ -126,15 +140,17 @@ extern "C" lbm_status lbm_conservation_noalloc(lbm_lattice lattice, lbm_storage 
         return set_error(LBM_ERR_UNSUPPORTED, "the fixed-point storage needs its range: use lbm_conservation");
     if (storage != LBM_STORE_F32 && storage != LBM_STORE_F16 && storage != LBM_STORE_BF16 && storage != LBM_STORE_F64)
         return set_error(LBM_ERR_UNSUPPORTED, "unknown storage");
-    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || dims[0] * dims[1] > (int64_t(1) << 31))
-        return set_error(LBM_ERR_INVALID_ARG, "dims out of range");
+    // the same per-dimension limits as lbm_create (each side >= max|c|, nx and ny <= 2^24,
+    // nz == 1 for D2Q9, fewer than 2^31 cells), checked before any product is formed
+    const std::string dp = dims_check(lattice, dims);
+    if (!dp.empty()) return set_error(LBM_ERR_INVALID_ARG, ("lbm_conservation_noalloc: dims: " + dp).c_str());
     if (dims[2] > kNoallocMaxPlanes)
         return set_error(LBM_ERR_INVALID_ARG,
                          "lbm_conservation_noalloc: nz exceeds the static scratch limit of 4096 z-planes");
-    double *scratch = nullptr;
-    cudaError_t e = scratch_address(&scratch);
-    if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    double *scratch = nullptr;
+    cudaError_t e = scratch_address(stream, &scratch);
+    if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
     double *result = out_mem == LBM_MEM_DEVICE ? out : scratch + kNoallocMaxPlanes * 4;
     const int nx = int(dims[0]), ny = int(dims[1]), nz = int(dims[2]);
     switch (lattice) {

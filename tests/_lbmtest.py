@@ -10,7 +10,13 @@ from paper_2002_02503_gb300 import lbm
 
 TOL_F32 = 1e-5   # max relative error of FP32 fields against the FP64 oracle after 100 steps
 TOL_F64 = 1e-12
-TOL_U16 = 1e-3   # relative error on u for shifted 16-bit storage
+TOL_U16 = 1e-3   # relative error on u for shifted 16-bit storage: the accuracy target of the 16-bit forms
+# Implementation parity of the 16-bit floating forms on short runs (tens of steps, white-noise or
+# smooth seeded fields) against the FP64 oracle: a few units of the storage's own rounding of the
+# scaled value h (2^-11 for FP16, 2^-8 for BF16, |h| up to ~0.3) over the decayed max|u|.  These
+# check that the kernels compute the method; they are not the accuracy target, which the
+# stated-size runs of test_gpu_storage_accuracy.py hold the storage forms to.
+TOL_ROUND = {"f16": 2e-3, "bf16": 2e-2}
 
 DIMS = {  # ragged sizes: several thread blocks per plane and a partial last block
     "D2Q9": (72, 44, 1),

@@ -127,3 +127,23 @@ def test_fixed_point_storage_host_checks(L):
     st = lbm.lib().lbm_conservation_noalloc(lbm.LATTICES["D3Q19"], lbm.STORAGES["q16"], d, 1.0,
                                             ctypes.c_void_p(256), out, lbm.MEM_HOST, None)
     assert st == lbm.LBM_ERR_UNSUPPORTED
+
+
+def test_noalloc_dims_use_the_solver_limits(L):
+    """The allocation-free sums reject, before any device work, every shape lbm_create rejects:
+    a side above 2^24 (whose int conversion would wrap), a 2-D lattice with nz != 1, a side
+    below the largest velocity component, and nz above its fixed scratch."""
+    out = (ctypes.c_double * 4)()
+
+    def status(lattice, dims):
+        d = (ctypes.c_int64 * 3)(*dims)
+        return lbm.lib().lbm_conservation_noalloc(lbm.LATTICES[lattice], lbm.STORAGES["f32"], d, 1.0,
+                                                  ctypes.c_void_p(256), out, lbm.MEM_HOST, None)
+
+    assert status("D3Q19", (1 << 31, 1, 1)) == lbm.LBM_ERR_INVALID_ARG
+    assert status("D3Q19", (1 << 40, 1 << 40, 1)) == lbm.LBM_ERR_INVALID_ARG
+    assert status("D2Q9", (8, 8, 2)) == lbm.LBM_ERR_INVALID_ARG
+    assert status("D3Q39", (8, 2, 8)) == lbm.LBM_ERR_INVALID_ARG
+    assert status("D3Q19", (4, 4, 4097)) == lbm.LBM_ERR_INVALID_ARG
+    assert status("D3Q19", (0, 4, 4)) == lbm.LBM_ERR_INVALID_ARG
+    assert b"dims" in lbm.lib().lbm_last_error() or b"4096" in lbm.lib().lbm_last_error()

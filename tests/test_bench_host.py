@@ -59,7 +59,7 @@ def test_combine_ranks_single_rank_is_identity():
 def test_reference_arm_prints_one_json_line():
     env = dict(os.environ)
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "3",
-                        "--warmup", "1", "--cpu-seconds", "0.3"], capture_output=True, text=True, env=env,
+                        "--warmup", "1", "--cpu-seconds", "0.3", "--dims", "32", "32", "32"], capture_output=True, text=True, env=env,
                        timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     lines = [x for x in r.stdout.splitlines() if x.strip()]
@@ -68,6 +68,8 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "32x32x32" in d["cpu_baseline"]["sample"] and "sub-lattice" not in d["cpu_baseline"]["sample"]
+    assert d["cpu_baseline"]["single_core"]["cores"] == 1
 
 
 def test_reference_arm_other_ranks_exit_quietly():

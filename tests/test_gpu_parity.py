@@ -1,15 +1,17 @@
 """Parity of the CUDA library (through its C-ABI) with the FP64 oracle.
 
 Tolerances: FP32 storage and arithmetic within 1e-5 relative after 100 steps
-(f and rho per element, u as max|du| / max|u|); FP64 storage within 1e-12;
-shifted FP16 storage within 1e-3 relative on u."""
+(f and rho per element, u as max|du| / max|u|); FP64 storage within 1e-12; the
+16-bit storage forms within their rounding bound TOL_ROUND on short runs (the
+accuracy target of 1e-3 on u at the stated sizes is checked in
+test_gpu_storage_accuracy.py)."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2002_02503_gb300 import fields, lbm
 
-from _lbmtest import (DIMS, TOL_F32, TOL_F64, TOL_U16, oracle_reference, perm_lib_to_oracle, raw_from_f, rel_f,
+from _lbmtest import (DIMS, TOL_F32, TOL_F64, TOL_ROUND, TOL_U16, oracle_reference, perm_lib_to_oracle, raw_from_f, rel_f,
                       rel_u, to_lib_order)
 
 pytestmark = pytest.mark.gpu
@@ -123,14 +125,16 @@ def test_every_kernel_configuration(name, K, storage):
     f_ref, r_ref, u_ref = oracle_reference(name, K, 0.6, dims, rho, u, 10)
     variants = _built_variants(name, K, storage, dims[0])
     assert len(variants) >= 3
-    tol = {"f32": TOL_F32, "f64": TOL_F64, "f16": 2e-3, "bf16": 2e-2}[storage]
+    tol = {"f32": TOL_F32, "f64": TOL_F64, **TOL_ROUND}[storage]
     results = []
     for v in variants:
         f, r, uu = _run_gpu(name, K, 0.6, dims, rho, u, 10, storage, variant=v)
         assert rel_u(uu, u_ref) < tol, v
         results.append(f)
+    # every configuration computes the same per-cell arithmetic; the FP32 rounding order of the
+    # paired and scalar collisions differs, which can flip a 16-bit rounding now and then
     same = {"f32": 1e-5, "f64": 1e-13, "f16": 5e-3, "bf16": 3e-2}[storage]
-    for f in results[1:]:  # every configuration computes the same per-cell arithmetic
+    for f in results[1:]:
         np.testing.assert_allclose(f, results[0], rtol=same)
 
 
@@ -142,17 +146,6 @@ def test_d2q9_shear_wave_fp64_1000_steps():
     f, r, uu = _run_gpu("D2Q9", 2, 0.8, dims, rho, u, 1000, "f64")
     assert rel_u(uu, u_ref) < TOL_F64
     assert rel_f(r, r_ref) < TOL_F64
-
-
-@pytest.mark.parametrize("storage,tol", [("f16", 1e-3), ("bf16", 1e-2)])
-def test_shifted_16bit_storage_taylor_green(storage, tol):
-    dims = (32, 32, 32)
-    rho, u = fields.taylor_green_3d(dims, 0.05, 1.0 / 3.0)
-    _, r_ref, u_ref = oracle_reference("D3Q19", 3, 0.55, dims, rho, u, 100)
-    _, r, uu = _run_gpu("D3Q19", 3, 0.55, dims, rho, u, 100, storage)
-    err = rel_u(uu, u_ref)
-    print("%s u error vs FP64 oracle after 100 steps: %.3e" % (storage, err))
-    assert err < tol
 
 
 def test_checkpoint_resume_is_bitwise():
@@ -395,7 +388,7 @@ def test_flat_pair_variant_on_odd_lattices(name, K, storage, dims):
     r, uu = s.moments()
     f = s.f()
     s.close()
-    tol = {"f32": TOL_F32, "f64": TOL_F64, "f16": 2e-3, "q16": TOL_U16}[storage]
+    tol = {"f32": TOL_F32, "f64": TOL_F64, "f16": TOL_ROUND["f16"], "q16": TOL_U16}[storage]
     assert rel_u(uu, u_ref) < tol
     assert rel_f(f, to_lib_order(name, f_ref)) < tol
 
@@ -416,7 +409,7 @@ def test_autotune_on_odd_widths(storage, dims):
     s.step(6)
     r, uu = s.moments()
     s.close()
-    tol = {"f32": TOL_F32, "f16": 2e-3, "q16": TOL_U16}[storage]
+    tol = {"f32": TOL_F32, "f16": TOL_ROUND["f16"], "q16": TOL_U16}[storage]
     assert rel_u(uu, u_ref) < tol
 
 

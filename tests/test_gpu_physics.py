@@ -22,7 +22,7 @@ import pytest
 import oracle
 from paper_2002_02503_gb300 import fields, lbm
 
-from _lbmtest import TOL_F32, rel_f, rel_u
+from _lbmtest import TOL_F32, TOL_U16, rel_f, rel_u
 
 pytestmark = pytest.mark.gpu
 
@@ -111,10 +111,7 @@ def taylor_green_reference():
     return dims, rho, u, r_ref, u_ref
 
 
-@pytest.mark.parametrize("storage,tol", [("f32", TOL_F32), ("f16", 1e-3), ("bf16", 1e-1), ("q16", 3e-4)])
-def test_storage_precision_taylor_green_500_steps(taylor_green_reference, storage, tol):
-    """Error of each storage form after 500 steps against the FP64 oracle.  The fixed-point form
-    runs with range 1/4 (|h| reaches about 0.16 in this flow)."""
+def _storage_error(taylor_green_reference, storage):
     dims, rho, u, r_ref, u_ref = taylor_green_reference
     s = lbm.Solver("D3Q19", dims, 0.52, 2, storage, storage_range=0.25 if storage == "q16" else None)
     s.set_fields(rho, u)
@@ -124,4 +121,25 @@ def test_storage_precision_taylor_green_500_steps(taylor_green_reference, storag
     eu, er = rel_u(uu, u_ref), rel_f(r, r_ref)
     print("D3Q19 64^3 Taylor-Green tau=0.52 K=2, %s storage, 500 steps: rel u error %.3e, rel rho error %.3e" % (
         storage, eu, er))
-    assert eu < tol
+    return eu
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", TOL_F32), ("f16", TOL_U16), ("q16", 3e-4)])
+def test_storage_precision_taylor_green_500_steps(taylor_green_reference, storage, tol):
+    """Error of each storage form after 500 steps against the FP64 oracle on 64^3 (the 16-bit
+    workload, tau = 0.52, at a size the oracle finishes in seconds; the stated sizes are checked
+    in test_gpu_storage_accuracy.py, where FP16 misses the target).  The fixed-point form runs
+    with range 1/4 (|h| reaches about 0.16 in this flow)."""
+    assert _storage_error(taylor_green_reference, storage) < tol
+
+
+@pytest.mark.xfail(strict=True, reason="BF16 storage misses the 1e-3 bound on u already at 64^3 (measured 4.9e-2)")
+def test_bf16_storage_meets_u_bound_at_64(taylor_green_reference):
+    """The 16-bit target (1e-3 on u) for BF16 storage: recorded as failing -- an 8-bit significand
+    rounds the momentum-carrying values at ~4e-4 each step."""
+    assert _storage_error(taylor_green_reference, "bf16") < TOL_U16
+
+
+def test_bf16_storage_error_regression_at_64(taylor_green_reference):
+    """BF16's measured miss at 64^3 (4.9e-2) must not grow."""
+    assert _storage_error(taylor_green_reference, "bf16") < 1.25 * 4.9e-2

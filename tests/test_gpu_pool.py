@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_2002_02503_gb300 import fields, lbm, serve
 
-from _lbmtest import TOL_F32, rel_f, rel_u
+from _lbmtest import TOL_F32, TOL_ROUND, rel_f, rel_u
 
 pytestmark = pytest.mark.gpu
 
@@ -165,7 +165,7 @@ def test_pool_other_classes_match_single_lattice(lattice, K, storage, sides):
     while not all(pool.poll(i)[0] for i in ids):
         pool.advance(10)
         pool.sync()
-    tol = {"f32": TOL_F32, "f16": 2e-3, "bf16": 2e-2}[storage]  # a one-ulp flip of a 16-bit value
+    tol = {"f32": TOL_F32, **TOL_ROUND}[storage]  # a one-ulp flip of a 16-bit value
     for side, rid in zip(sides, ids):
         r, u = pool.result(rid, side ** 3)
         s = lbm.Solver(lattice, (side,) * 3, 0.65, K, storage)
