@@ -30,9 +30,18 @@ from paper_2002_02503_gb300 import fields  # noqa: E402  (seeded inputs only)
 
 LATTICE_Q = {"D2Q9": 9, "D3Q15": 15, "D3Q19": 19, "D3Q27": 27, "D3Q39": 39}
 LATTICE_T0 = {"D2Q9": 1.0 / 3.0, "D3Q15": 1.0 / 3.0, "D3Q19": 1.0 / 3.0, "D3Q27": 1.0 / 3.0, "D3Q39": 2.0 / 3.0}
-STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8, "q16": 2}
+STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8, "q16": 2, "f16r": 2, "bf16r": 2}
 DTYPE_NAME = {"f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)", "f64": "f64",
-              "q16": "f32 (16-bit fixed-point storage)"}
+              "q16": "f32 (16-bit fixed-point storage)", "f16r": "f32 (f16 storage, per-cell reference velocity)",
+              "bf16r": "f32 (bf16 storage, per-cell reference velocity)"}
+LATTICE_D = {"D2Q9": 2, "D3Q15": 3, "D3Q19": 3, "D3Q27": 3, "D3Q39": 3}
+
+
+def bytes_per_update(lattice, storage):
+    """Algorithmic bytes of one cell update: every stored plane read once and written once (the
+    reference-velocity forms store D planes beside the Q distribution planes)."""
+    planes = LATTICE_Q[lattice] + (LATTICE_D[lattice] if storage in ("f16r", "bf16r") else 0)
+    return 2 * planes * STORE_BYTES[storage]
 NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal (the measured copy peak is the roofline's denominator)
 Q16_RANGE = 0.25  # fixed-point range for the Taylor-Green workloads (u0 = 0.05: |h| up to about 0.16)
 KERNEL_SOURCES = ["lbm_core.cuh", "lbm_kernels.cuh", "lbm_lattice.cuh"]
@@ -151,6 +160,8 @@ PER_LATTICE = [
     ("D3Q19", (512, 512, 512), 2, "f16", 0.52, 0.05),
     ("D3Q19", (512, 512, 512), 2, "bf16", 0.52, 0.05),
     ("D3Q19", (512, 512, 512), 2, "q16", 0.52, 0.05),
+    ("D3Q19", (512, 512, 512), 2, "f16r", 0.52, 0.05),
+    ("D3Q19", (256, 256, 256), 2, "f16r", 0.55, 0.05),
 ]
 
 # The extensions of the method (energy-flux term, K = 5, D3Q15, the BGK comparison operator):
@@ -206,7 +217,7 @@ def measure_lattice(lattice, dims, K, storage, tau, u0, steps, stream, model="fi
     del s
     torch.cuda.empty_cache()
     C = int(np.prod(dims))
-    bpu = 2 * LATTICE_Q[lattice] * STORE_BYTES[storage]
+    bpu = bytes_per_update(lattice, storage)
     peak, _ = measured_peak()
     mlups = C * steps / (ms / 1e3) / 1e6
     mode = "" if model == "filtered" and theta == 0.0 else (" BGK" if model == "bgk" else " theta=%g" % theta)
@@ -227,7 +238,7 @@ def config_of(a, extra=None):
     c = {"workload": workload_name(a), "lattice": a.lattice, "dims": list(a.dims), "K": a.K, "tau": a.tau,
          "u0": a.u0, "storage": a.storage, "parallelism": "replicas",
          "l2": "inputs larger than L2: %.2f GB of distributions per step" % (
-             2 * LATTICE_Q[a.lattice] * STORE_BYTES[a.storage] * int(np.prod(a.dims)) / 1e9)}
+             bytes_per_update(a.lattice, a.storage) * int(np.prod(a.dims)) / 1e9)}
     if a.storage == "q16":
         c["storage_range"] = a.storage_range
     if extra:
@@ -329,7 +340,7 @@ def cpu_baseline_leg(a, seconds):
 
 
 # ------------------------------------------------------------------ accuracy of the storage forms
-ACCURACY_FORMS = ("f32", "f16", "bf16", "q16")
+ACCURACY_FORMS = ("f32", "f16", "bf16", "q16", "f16r", "bf16r")
 # (key, dims, tau, steps): the stated Taylor-Green configurations (D3Q19, u0 = 0.05, K = 2)
 ACCURACY_CONFIGS = [("256^3 tau=0.55 1000 steps", (256, 256, 256), 0.55, 1000),
                     ("512^3 tau=0.52 500 steps", (512, 512, 512), 0.52, 500)]
@@ -681,7 +692,7 @@ def run_ours(a):
         e2e["value"] = e2e_job
     value = job_mlups(C, a.steps, world, t_max)
     if rank == 0:
-        bpu = 2 * Q * STORE_BYTES[a.storage]
+        bpu = bytes_per_update(a.lattice, a.storage)
         per_launch_s = (ms / 1e3) / a.steps
         achieved = bpu * C / per_launch_s / 1e9
         peak, peak_kind = measured_peak()
@@ -754,6 +765,16 @@ def run_ours(a):
         if gi is not None:
             out["headline_gi"] = {"workload": "D3Q19 256^3 FP32 Taylor-Green tau=0.55, K=3 (Eq. filter-1st)",
                                   "MLUPS": round(gi["MLUPS"], 1), "frac": round(gi["frac_of_measured_hbm"], 3)}
+        # each storage form at 512^3 (tau = 0.52, K = 2): rate, HBM fraction and error on u after
+        # 500 steps, against the bound the 16-bit forms are held to
+        rates = {r["workload"].split()[2]: r for r in extras.get("per_lattice", [])
+                 if r["workload"].startswith("D3Q19 512x512x512")}
+        if rates:
+            err = (accuracy or {}).get("rel_u", {}).get("512^3 tau=0.52 500 steps", {})
+            out["storage_summary"] = {
+                k: {"MLUPS": round(v["MLUPS"]), "frac": round(v["frac_of_measured_hbm"], 3),
+                    "x_f32": round(v["MLUPS"] / rates["f32"]["MLUPS"], 2) if "f32" in rates else None,
+                    "rel_u_500": err.get(k)} for k, v in rates.items()}
         if accuracy is not None:
             out["accuracy"] = accuracy
         print(json.dumps(out), flush=True)

@@ -51,8 +51,11 @@ typedef enum {
     LBM_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
     LBM_ERR_BUSY = 7,          /* no free slot or memory in a pool right now */
     LBM_ERR_NOT_FOUND = 8,     /* unknown request id */
-    LBM_ERR_RANGE = 9          /* a value left the range of the fixed-point storage (or was not
+    LBM_ERR_RANGE = 9,         /* a value left the range of the fixed-point storage (or was not
                                   finite); the stored state is no longer valid */
+    LBM_ERR_BOUNDS = 10        /* only in the bounds-check build (lbm_bounds_checked() == 1): a
+                                  kernel computed an index outside its buffer; the access was
+                                  skipped, the stored state is not valid */
 } lbm_status;
 
 /* Velocity sets.  D2Q9, D3Q15, D3Q19: isotropy class 2N = 4, T0 = 1/3 (Sec. 2
@@ -71,13 +74,27 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2, LBM_D3Q39 = 3, LBM_D3
  * and the next synchronising call returns LBM_ERR_RANGE.  Q16 runs on the register
  * pull step (variant 0, every cells_per_thread, BGK and the energy-flux term) and in
  * pools (lbm_pool_set_storage_range); the staged variant and lbm_conservation_noalloc
- * reject it (LBM_ERR_UNSUPPORTED). */
+ * reject it (LBM_ERR_UNSUPPORTED).
+ * LBM_STORE_F16_REF and LBM_STORE_BF16_REF store, beside the Q distribution planes, D
+ * planes of a per-cell reference velocity a = u / T0 (the cell's velocity after its
+ * collision, rounded to the storage type), and in place of h_i the residual
+ * h_i - r_i, r_i = s + s^2/2 with s = c_i . a, rounded to FP16 or BF16.  The reader adds
+ * r_i of the cell that wrote the value back in FP32, so only the residual is rounded: its
+ * size is that of (rho - rho0), rho |u|^2 / (2 T0), the higher orders and the
+ * non-equilibrium part, not of c_i . u / T0, and the rounding error shrinks by the same
+ * factor.  Per cell update they move
+ * 2 (Q + D) x 2 bytes (D3Q19: 88 against 76 for FP16 and 152 for FP32).  They run on
+ * the register-pull step (variant 0, every cells_per_thread, BGK and the energy-flux
+ * term); the staged and flat-pair variants, pools and lbm_conservation_noalloc reject
+ * them (LBM_ERR_UNSUPPORTED). */
 typedef enum {
     LBM_STORE_F32 = 0,
     LBM_STORE_F16 = 1,
     LBM_STORE_BF16 = 2,
     LBM_STORE_F64 = 3,
-    LBM_STORE_Q16 = 4
+    LBM_STORE_Q16 = 4,
+    LBM_STORE_F16_REF = 5,
+    LBM_STORE_BF16_REF = 6
 } lbm_storage;
 
 typedef enum { LBM_MEM_HOST = 0, LBM_MEM_DEVICE = 1 } lbm_mem;
@@ -90,8 +107,9 @@ typedef struct lbm_solver lbm_solver; /* opaque; owned by the library */
 lbm_status lbm_lattice_info(lbm_lattice lattice, int *D, int *Q, int *c, double *w, double *T0, int *kmax);
 
 /* Bytes of device workspace lbm_create needs: two distribution buffers of
- * Q*C values of the storage type (pull streaming ping-pongs between them) plus
- * a small reduction area.  Returns 0 for invalid arguments. */
+ * Q*C values of the storage type (Q+D planes of C values for the forms with a
+ * reference velocity; pull streaming ping-pongs between them) plus a small
+ * reduction area.  Returns 0 for invalid arguments. */
 size_t lbm_workspace_bytes(lbm_lattice lattice, const int64_t dims[3], lbm_storage storage);
 
 /* Create a solver for a periodic lattice (Eq. lbe, Eq. lbe-reg).
@@ -137,8 +155,9 @@ lbm_status lbm_conservation(lbm_solver *s, double out[4]);
  * accumulated in FP64.  Host output; synchronises. */
 lbm_status lbm_mode_amplitude(lbm_solver *s, const int64_t k[3], int component, double out[2]);
 
-/* Checkpoint: the raw stored distributions (bytes = Q*C*sizeof(storage)) and
- * the step counter.  get synchronises and, like the other synchronising calls, first
+/* Checkpoint: the raw stored distributions (bytes = Q*C*sizeof(storage); (Q+D)*C*2
+ * for the forms with a reference velocity, whose planes follow the Q distribution
+ * planes) and the step counter.  get synchronises and, like the other synchronising calls, first
  * reports a pending status (LBM_ERR_RANGE, LBM_ERR_TIMEOUT) instead of saving a state known
  * to be invalid; set replaces the state and clears any pending status of the old one (so
  * does lbm_set_fields).  A fixed-point checkpoint restores under the range and reference shift
@@ -248,6 +267,23 @@ lbm_status lbm_autotune(lbm_solver *s, int iters, double *best_us);
 lbm_status lbm_conservation_noalloc(lbm_lattice lattice, lbm_storage storage, const int64_t dims[3], double rho0,
                                    const void *distributions, double out[4], lbm_mem out_mem, void *cuda_stream);
 
+/* 1 when this library is the bounds-check build (compiled with LBM_DEBUG_BOUNDS, a
+ * separate file): every kernel then checks each load and store index against the buffer
+ * or velocity plane it addresses, skips an access outside it and records the event, and
+ * the next synchronising call returns LBM_ERR_BOUNDS.  0 in the normal build.  The paper
+ * has no counterpart: it is a check of the library's own indexing. */
+int lbm_bounds_checked(void);
+
+/* Host walk of the register-pull step's index arithmetic (no device work, any build): for
+ * every thread of one launch with cells_per_thread V (1, 2, 4, 8; V must divide nx) on
+ * dims, the offsets its loads and stores compute inside a velocity plane, each checked
+ * against a plane of P elements with the same test the bounds-check build's kernels apply.
+ * Returns how many accesses fall outside (0 for a consistent P = nx*ny*nz) and sets
+ * *accesses (if not NULL) to the number checked; -1 for invalid arguments.  The paper has
+ * no counterpart: it is a check of the library's own indexing. */
+int64_t lbm_bounds_walk(lbm_lattice lattice, int cells_per_thread, const int64_t dims[3], int64_t P,
+                        int64_t *accesses);
+
 /* Release the solver (not the workspace).  Synchronises its stream. */
 lbm_status lbm_destroy(lbm_solver *s);
 
@@ -263,7 +299,8 @@ lbm_status lbm_destroy(lbm_solver *s);
 typedef struct lbm_pool lbm_pool;
 
 /* Device bytes one request of these dims occupies in a pool's arena: its two
- * distribution buffers and a 256-byte status word. */
+ * distribution buffers and a 256-byte status word.  0 for invalid arguments and for
+ * the storage forms pools do not run (the reference-velocity forms). */
 size_t lbm_pool_request_bytes(lbm_lattice lattice, const int64_t dims[3], lbm_storage storage);
 
 /* arena: caller-owned device memory (256-byte aligned) that the pool carves

@@ -86,8 +86,15 @@ size_t storage_size(lbm_storage st) {
     case LBM_STORE_BF16: return 2;
     case LBM_STORE_F64: return 8;
     case LBM_STORE_Q16: return 2;
+    case LBM_STORE_F16_REF: return 2;
+    case LBM_STORE_BF16_REF: return 2;
     }
     return 0;
+}
+
+// Stored planes of C values per buffer: Q distributions, plus D reference-velocity planes.
+size_t planes_of(const LatInfo &li, lbm_storage st) {
+    return size_t(li.Q) + (has_reference_planes(st) ? size_t(li.D) : 0);
 }
 
 const KernelSet *kernels_for(lbm_lattice lat, int K, lbm_storage st) {
@@ -256,6 +263,8 @@ lbm_status check_device_status(lbm_solver *s) {
     if (e != cudaSuccess) return cuda_fail(e, "status word");
     if (v != 0) {
         cudaMemsetAsync(s->status, 0, sizeof(unsigned int), s->stream);
+        if (v & kStatusBounds)
+            return fail(LBM_ERR_BOUNDS, "an index fell outside its buffer (bounds-check build; status 0x%x)", v);
         if (v & kStatusTimeout)
             return fail(LBM_ERR_TIMEOUT, "a bounded wait in the staged step expired (status 0x%x)", v);
         return fail(LBM_ERR_RANGE, "a value left the fixed-point storage range +-2^%d (status 0x%x)", s->qexp + 15, v);
@@ -279,6 +288,7 @@ const char *lbm_status_string(lbm_status st) {
     case LBM_ERR_BUSY: return "busy";
     case LBM_ERR_NOT_FOUND: return "not found";
     case LBM_ERR_RANGE: return "value outside the storage range";
+    case LBM_ERR_BOUNDS: return "index outside its buffer (bounds-check build)";
     }
     return "unknown status";
 }
@@ -307,7 +317,7 @@ size_t lbm_workspace_bytes(lbm_lattice lat, const int64_t dims[3], lbm_storage s
     if (!lattice_info(lat, &li) || storage_size(st) == 0) return 0;
     if (!dims_problem(li, dims).empty()) return 0;
     const size_t C = size_t(dims[0]) * size_t(dims[1]) * size_t(dims[2]);
-    const size_t buf = align_up(C * size_t(li.Q) * storage_size(st));
+    const size_t buf = align_up(C * planes_of(li, st) * storage_size(st));
     return 2 * buf + align_up(kPartialBytes) + kAlign + kAlign;
 }
 
@@ -348,7 +358,7 @@ lbm_status lbm_create(lbm_lattice lat, const int64_t dims[3], double tau, int K,
     s->relax = 1.0 - 1.0 / tau;
     s->ws = static_cast<char *>(ws);
     s->ws_bytes = ws_bytes;
-    s->buf_bytes = size_t(s->C) * size_t(li.Q) * s->ssize;
+    s->buf_bytes = size_t(s->C) * planes_of(li, st) * s->ssize;
     const size_t bufa = align_up(s->buf_bytes);
     s->buf[0] = s->ws;
     s->buf[1] = s->ws + bufa;
@@ -471,6 +481,12 @@ lbm_status lbm_set_fields(lbm_solver *s, const double *rho, const double *u, lbm
         }
     }
     a.qs = solver_qscale(s);
+    if (has_reference_planes(s->st)) {
+        // the reference planes first (each cell's own), then the values relative to them
+        a.phase = 0;
+        if (lbm_status r = init_pass(s, rho, u, mem, a)) return r;
+        a.phase = 1;
+    }
     if (lbm_status r = init_pass(s, rho, u, mem, a)) return r;
     LBM_CUDA(cudaStreamSynchronize(s->stream), "set_fields: synchronize");
     s->cur = 0;
@@ -565,6 +581,7 @@ static lbm_status pull_out(lbm_solver *s, double *rho, double *u, double *f, lbm
     a.P = s->C;
     a.rho0 = s->rho0;
     a.qs = solver_qscale(s);
+    a.status = s->status;
     pull_fn fn = f ? s->ks->pull_f : s->ks->moments;
     if (mem == LBM_MEM_DEVICE) {
         a.rho = rho;
@@ -612,6 +629,7 @@ static lbm_status pull_out(lbm_solver *s, double *rho, double *u, double *f, lbm
         }
     }
     LBM_CUDA(cudaStreamSynchronize(s->stream), "synchronize");
+    if (kBoundsCheck) return check_device_status(s);  // the pull kernel's own accesses
     return LBM_OK;
 }
 
@@ -642,10 +660,13 @@ static lbm_status reduce_to_host(lbm_solver *s, reduce_fn fn, ReduceArgs &a, int
     a.out = s->red_out;
     a.blocks = kReduceBlocks;
     a.qs = solver_qscale(s);
+    a.status = s->status;
     LBM_CUDA(fn(a, s->stream), "reduction kernel");
     LBM_CUDA(cudaMemcpyAsync(out, s->red_out, nvals * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
              "copy reduction");
     LBM_CUDA(cudaStreamSynchronize(s->stream), "synchronize");
+    if (kBoundsCheck)
+        if (lbm_status st = check_device_status(s)) return st;  // the reduction kernel's own accesses
     for (int q = 0; q < nvals; ++q)
         if (!isfinite(out[q])) return fail(LBM_ERR_NONFINITE, "reduction result %d is not finite", q);
     return LBM_OK;

@@ -215,6 +215,7 @@ lbm_status pull_to(lbm_pool *p, Request &r, double *rho, double *u, lbm_mem mem)
     a.rho0 = r.rho0;
     a.qs = qscale_of_exponent(r.qexp);
     a.f = nullptr;
+    a.status = r.status;
     cudaError_t e;
     if (mem == LBM_MEM_DEVICE) {
         a.rho = rho;
@@ -263,6 +264,10 @@ lbm_status request_status(lbm_pool *p, unsigned int *status) {
     cudaError_t e = cudaMemcpyAsync(&v, status, sizeof(v), cudaMemcpyDeviceToHost, p->io);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->io);
     if (e != cudaSuccess) return set_cuda_error(e, "pool: status word");
+    if (v & kStatusBounds) {
+        cudaMemsetAsync(status, 0, sizeof(unsigned int), p->io);
+        return set_error(LBM_ERR_BOUNDS, "pool: an index of this request fell outside its buffer (bounds-check build)");
+    }
     if (v & kStatusRange) {
         cudaMemsetAsync(status, 0, sizeof(unsigned int), p->io);
         return set_error(LBM_ERR_RANGE, "pool: a value of this request left the fixed-point storage range");
@@ -277,6 +282,7 @@ extern "C" {
 size_t lbm_pool_request_bytes(lbm_lattice lat, const int64_t dims[3], lbm_storage st) {
     int D, Q, maxc, kmax;
     if (!lattice_query(lat, &D, &Q, &maxc, &kmax) || storage_bytes(st) == 0) return 0;
+    if (has_reference_planes(st)) return 0;  // pools do not run the reference-velocity forms
     if (!dims_check(lat, dims).empty()) return 0;
     return request_bytes(Q, storage_bytes(st), (long long)dims[0] * dims[1] * dims[2]);
 }

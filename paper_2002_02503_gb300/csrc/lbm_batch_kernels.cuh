@@ -11,7 +11,7 @@ namespace lbm {
 template <class LT, class ST>
 __device__ __forceinline__ void pull_cell_scaled(const typename ST::S *__restrict__ src, int nx, int ny, int nz,
                                                  long long P, int x, int y, int z, const QScale &qs,
-                                                 typename ST::T (&f)[LT::Q]) {
+                                                 typename ST::T (&f)[LT::Q], unsigned int *status) {
     constexpr int M = LT::MAXC;
     int xs[2 * M + 1], ys[2 * M + 1], zs[2 * M + 1];
 #pragma unroll
@@ -22,9 +22,9 @@ __device__ __forceinline__ void pull_cell_scaled(const typename ST::S *__restric
     }
 #pragma unroll
     for (int i = 0; i < LT::Q; ++i) {
-        const long long at = (long long)i * P + (long long)(zs[vel<LT>(i, 2) + M] * ny + ys[vel<LT>(i, 1) + M]) * nx +
-                             xs[vel<LT>(i, 0) + M];
-        f[i] = decode<ST>(src[at], qs, i);
+        const long long in_plane =
+            (long long)(zs[vel<LT>(i, 2) + M] * ny + ys[vel<LT>(i, 1) + M]) * nx + xs[vel<LT>(i, 0) + M];
+        f[i] = guard(in_plane, 1, P, status) ? decode<ST>(src[(long long)i * P + in_plane], qs, i) : typename ST::T(0);
     }
 }
 
@@ -51,8 +51,8 @@ __device__ __forceinline__ void pull_collide_store_pair(const typename ST::S *__
         }
     }
     T f0[Q], f1[Q];
-    pull_cell_scaled<LT, ST>(src, nx, ny, nz, P, x0, y0, z0, qs, f0);
-    pull_cell_scaled<LT, ST>(src, nx, ny, nz, P, x1, y1, z1, qs, f1);
+    pull_cell_scaled<LT, ST>(src, nx, ny, nz, P, x0, y0, z0, qs, f0, status);
+    pull_cell_scaled<LT, ST>(src, nx, ny, nz, P, x1, y1, z1, qs, f1, status);
     if constexpr (sizeof(T) == 4) {
         F2 g[Q];
 #pragma unroll
@@ -69,6 +69,7 @@ __device__ __forceinline__ void pull_collide_store_pair(const typename ST::S *__
     }
     const long long c0 = x0 + (long long)nx * (y0 + (long long)ny * z0);
     unsigned int acc = 0u;
+    if (!guard(c0, second ? 2 : 1, P, status)) return;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         dst[(long long)i * P + c0] = encode<ST>(f0[i], qs, i, acc);

@@ -116,6 +116,42 @@ template <bool S>
 struct ShiftedOf<StoreQ16Codec<S>> {
     static constexpr bool value = S;
 };
+// Per-cell reference velocity (LBM_STORE_F16_REF, LBM_STORE_BF16_REF): the base 16-bit codec,
+// applied to the residual h_i - r_i with r_i = s + s^2 / 2, s = c_i . a, where a = u / T0 of the
+// cell that wrote the value, rounded to the same 16-bit type and stored in D extra planes after
+// the Q distribution planes.  A reader adds r_i of that cell back in FP32 (ref_value, the same
+// operations on both sides), so only the residual is rounded.  For a flow of speed |u| the
+// momentum part c_i . u / T0 of h_i is the largest term (about 0.15 at |u| = 0.05 on T0 = 1/3
+// lattices) and its square the next; what is left (rho - rho0, rho |u|^2 / (2 T0), higher
+// orders and the non-equilibrium part) is more than an order of magnitude smaller, and so is
+// the rounding step of a 16-bit float.
+template <class Base>
+struct StoreRef : Base {
+    static constexpr lbm_storage id = Base::id == LBM_STORE_F16 ? LBM_STORE_F16_REF : LBM_STORE_BF16_REF;
+    static constexpr lbm_storage codec = Base::id;  // the element codec (vector conversions key on it)
+};
+using StoreF16Ref = StoreRef<StoreF16>;
+using StoreBF16Ref = StoreRef<StoreBF16>;
+
+// Element codec of a storage form (the form itself, or the base of a reference form).
+template <class ST>
+struct CodecOf {
+    static constexpr lbm_storage value = ST::id;
+};
+template <class B>
+struct CodecOf<StoreRef<B>> {
+    static constexpr lbm_storage value = B::id;
+};
+// True for the forms with reference-velocity planes.
+template <class ST>
+struct RefOf {
+    static constexpr bool value = false;
+};
+template <class B>
+struct RefOf<StoreRef<B>> {
+    static constexpr bool value = true;
+};
+
 // True when an encode since acc = 0 met a value outside the fixed-point range.
 __device__ __forceinline__ bool range_exceeded(unsigned int acc) { return (acc >> 16) != 0u; }
 
@@ -125,14 +161,14 @@ __device__ __forceinline__ bool range_exceeded(unsigned int acc) { return (acc >
 template <class ST, int V>
 __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typename ST::T (&out)[V],
                                            const QScale &q, int i) {
-    if constexpr (ST::id == LBM_STORE_F16 && V % 2 == 0) {
+    if constexpr (CodecOf<ST>::value == LBM_STORE_F16 && V % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
             const float2 f = __half22float2(__halves2half2(raw[j], raw[j + 1]));
             out[j] = f.x;
             out[j + 1] = f.y;
         }
-    } else if constexpr (ST::id == LBM_STORE_BF16 && V % 2 == 0) {
+    } else if constexpr (CodecOf<ST>::value == LBM_STORE_BF16 && V % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
             const float2 f = __bfloat1622float2(__halves2bfloat162(raw[j], raw[j + 1]));
@@ -161,14 +197,14 @@ __device__ __forceinline__ void decode_vec(const typename ST::S (&raw)[V], typen
 template <class ST, int V>
 __device__ __forceinline__ void encode_vec(const typename ST::T (&in)[V], typename ST::S (&raw)[V],
                                            const QScale &q, int i, unsigned int &acc) {
-    if constexpr (ST::id == LBM_STORE_F16 && V % 2 == 0) {
+    if constexpr (CodecOf<ST>::value == LBM_STORE_F16 && V % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
             const __half2 h = __floats2half2_rn(in[j], in[j + 1]);
             raw[j] = __low2half(h);
             raw[j + 1] = __high2half(h);
         }
-    } else if constexpr (ST::id == LBM_STORE_BF16 && V % 2 == 0) {
+    } else if constexpr (CodecOf<ST>::value == LBM_STORE_BF16 && V % 2 == 0) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
             const __nv_bfloat162 h = __floats2bfloat162_rn(in[j], in[j + 1]);
@@ -261,6 +297,48 @@ __device__ __forceinline__ F2 &operator-=(F2 &x, F2 y) { return x = x - y; }
 __device__ __forceinline__ F2 &operator+=(F2 &x, const F2P &p) { return x = x + p; }
 __device__ __forceinline__ F2 &operator-=(F2 &x, const F2P &p) { return x = x - p; }
 
+// ------------------------------------------------------------------ reference velocity
+// r_i = s + s^2 / 2 with s = c_i . a, for velocity i of lattice LT and a the reference
+// velocity over T0 of the cell that wrote the value (reference-velocity storage forms).  The
+// writer subtracts it and the reader adds it back, each with this same sequence of
+// correctly rounded operations (explicit intrinsics, so no contraction choice can differ
+// between the two sides); on F2 each lane is rounded as the scalar operation, so one cell's
+// r_i is the same bits on the scalar and the paired path.
+__device__ __forceinline__ float ref_add(float s, int c, float a) {
+    return c == 1 ? __fadd_rn(s, a) : (c == -1 ? __fsub_rn(s, a) : (c != 0 ? __fmaf_rn(float(c), a, s) : s));
+}
+__device__ __forceinline__ F2 ref_add(F2 s, int c, F2 a) {
+    return c == 1 ? s + a : (c == -1 ? s - a : (c != 0 ? F2(double(c)) * a + s : s));
+}
+template <class LT, typename T>
+__device__ __forceinline__ T ref_dot(int i, const T (&a)[3]) {
+    T s = T(-0.0);
+#pragma unroll
+    for (int d = 0; d < LT::D; ++d) s = ref_add(s, vel<LT>(i, d), a[d]);
+    return s;
+}
+__device__ __forceinline__ float ref_of_dot(float s) { return __fmaf_rn(s * 0.5f, s, s); }
+__device__ __forceinline__ F2 ref_of_dot(F2 s) { return F2(s * F2(0.5)) * s + s; }
+template <class LT, typename T>
+__device__ __forceinline__ T ref_value(int i, const T (&a)[3]) {
+    return ref_of_dot(ref_dot<LT>(i, a));
+}
+// r of the pair (+c_p, -c_p) at once: s_- = -s_+ exactly, so r_- = fma(s/2, s, -s) is the
+// value ref_value gives for the -c_p velocity.
+template <class LT, typename T>
+__device__ __forceinline__ void ref_pair(int p, const T (&a)[3], T &r_plus, T &r_minus) {
+    const T s = ref_dot<LT>(2 * p + 1, a);
+    if constexpr (sizeof(T) == 4) {
+        const float h = s * 0.5f;
+        r_plus = __fmaf_rn(h, s, s);
+        r_minus = __fmaf_rn(h, s, -s);
+    } else {
+        const F2 h = F2(s * F2(0.5));
+        r_plus = h * s + s;
+        r_minus = h * s - s;
+    }
+}
+
 // ------------------------------------------------------------------ moments
 // Accumulators start at -0.0: x + (-0.0) == x for every x, so the compiler drops
 // the first addition (it cannot drop x + 0.0, which differs for x = -0.0).
@@ -343,8 +421,9 @@ struct ScalarHermite {
 //   a_0 = Qt(c,c,c) - 3 T0 c.q,  a_1 = -3 (c.(Qt u).c - T0 u.q),  a_2 = 3 c.(Qt u u),
 // a_0, a_2 odd and a_1 even under c -> -c.  Qt = sum w c c c (h - h^eq) - 3 sym(u Pi).
 // kq = (1 - 1/tau) theta / (6 T0^3).
+// us_out, when given, receives u / T0 (the collision conserves rho and u).
 template <class LT, int K, typename T, bool THETA = false>
-__device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0, T kq = T(0)) {
+__device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0, T kq = T(0), T *us_out = nullptr) {
     static_assert(K >= 2 && K <= 5, "truncation order");
     static_assert(!THETA || K >= 3, "the energy-flux series starts at Hermite order 3");
     constexpr int D = LT::D;
@@ -359,6 +438,7 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0, T kq = T
     for (int a = 0; a < D; ++a) {
         u[a] = j[a] * irho;
         us[a] = u[a] * iT0;
+        if (us_out) us_out[a] = us[a];
     }
     // Pi^neq = sum c c g~ - T0 drho I - j u  (Eq. coeff-2; equal to Eq. Pi_def)
     T P[3][3];
@@ -567,7 +647,7 @@ __device__ __forceinline__ void equilibrium_shifted(T rho, T drho, const T (&u)[
 // variables: h' = h^eq + (1 - 1/tau)(h - h^eq).  A comparison baseline: it relaxes
 // every non-equilibrium moment, including those the lattice does not support.
 template <class LT, int K, typename T>
-__device__ __forceinline__ void collide_bgk(T (&g)[LT::Q], T relax, T rho0) {
+__device__ __forceinline__ void collide_bgk(T (&g)[LT::Q], T relax, T rho0, T *us_out = nullptr) {
     constexpr int D = LT::D;
     T drho, j[3], m2[3][3];
     accumulate_moments<LT, T>(g, drho, j, m2);
@@ -575,7 +655,10 @@ __device__ __forceinline__ void collide_bgk(T (&g)[LT::Q], T relax, T rho0) {
     const T irho = T(1) / rho;
     T u[3] = {T(0), T(0), T(0)};
 #pragma unroll
-    for (int a = 0; a < D; ++a) u[a] = j[a] * irho;
+    for (int a = 0; a < D; ++a) {
+        u[a] = j[a] * irho;
+        if (us_out) us_out[a] = u[a] * T(1.0 / LT::T0);
+    }
     T feq[LT::Q];
     equilibrium_shifted<LT, K, T>(rho, drho, u, feq);
 #pragma unroll

@@ -20,6 +20,10 @@ inline int v_of_index(int k) { return 1 << k; }
 
 constexpr int kQMax = 39;  // largest velocity count of the built lattices
 
+// Storage forms that keep a per-cell reference velocity in D planes after the Q distribution
+// planes (LBM_STORE_F16_REF, LBM_STORE_BF16_REF).
+inline bool has_reference_planes(lbm_storage st) { return st == LBM_STORE_F16_REF || st == LBM_STORE_BF16_REF; }
+
 // Constants of the fixed-point storage codec (LBM_STORE_Q16); the floating forms ignore them.
 // Grid step 2^e: mul = 2^e, inv = 2^-e.  Per velocity i, a reference shift of k_i whole grid
 // steps (k_i = rint(ref_i / 2^e), ref_i the scaled equilibrium at a reference velocity, 0 by
@@ -47,6 +51,38 @@ inline QScale qscale_of_exponent(int e, const double *ref = nullptr, int Q = 0) 
 // Bits of the device status word.
 constexpr unsigned int kStatusTimeout = 1u;  // a bounded wait of the staged step expired
 constexpr unsigned int kStatusRange = 2u;    // a value left the fixed-point storage's range
+constexpr unsigned int kStatusBounds = 4u;   // bounds-check build: an index fell outside its buffer
+
+// The bounds-check build (compiled with -DLBM_DEBUG_BOUNDS, a separate library): every kernel
+// checks each computed load and store index against the extent of the buffer (or velocity
+// plane) it addresses; an index outside is recorded in the status word and the access is
+// skipped -- no trap, the context stays usable -- and the next synchronising call returns
+// LBM_ERR_BOUNDS.  In the normal build the checks compile away.
+#ifdef LBM_DEBUG_BOUNDS
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+
+// True when the n elements [first, first + n) lie inside [0, extent).
+__host__ __device__ inline bool span_in(long long first, long long n, long long extent) {
+    return first >= 0 && n >= 0 && first <= extent - n;
+}
+
+#ifdef __CUDACC__
+// Bounds-check build: true when the n elements [first, first + n) lie inside [0, extent);
+// otherwise records kStatusBounds in *status (when given) and returns false, and the caller
+// skips the access.  Constant true in the normal build.
+__device__ __forceinline__ bool guard(long long first, int n, long long extent, unsigned int *status) {
+    if constexpr (!kBoundsCheck) {
+        return true;
+    } else {
+        if (span_in(first, n, extent)) return true;
+        if (status) atomicOr(status, kStatusBounds);
+        return false;
+    }
+}
+#endif
 
 struct StepArgs {
     const void *src;  // stored distributions at t (post-collision of t-1, un-streamed)
@@ -73,6 +109,8 @@ struct InitArgs {
     QScale qs;
     unsigned int *status;  // receives kStatusRange when a value does not fit the fixed-point range
     unsigned int *hmax;    // when set: store nothing, only raise *hmax to the largest |h| (float bits)
+    int phase;             // forms with a reference velocity: 0 writes each cell's reference planes,
+                           // 1 the distributions relative to the references phase 0 wrote
 };
 
 struct PullArgs {
@@ -86,6 +124,7 @@ struct PullArgs {
     long long P;
     double rho0;
     QScale qs;
+    unsigned int *status;  // bounds-check build: receives kStatusBounds
 };
 
 struct ReduceArgs {
@@ -99,6 +138,7 @@ struct ReduceArgs {
     int k[3];              // mode wave vector
     int component;         // mode velocity component
     QScale qs;
+    unsigned int *status;  // bounds-check build: receives kStatusBounds
 };
 
 // One lattice of a batch (device-resident table entry).

@@ -105,54 +105,91 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
     for (int dl = -kMaxDl; dl <= kMaxDl; ++dl)
         ok[dl + kMaxDl] = V > 1 && lane + dl >= 0 && lane + dl <= 31 && chunk + dl >= 0 && chunk + dl < ncx;
 
-    T f[Q][V];
-    if constexpr (V == 1) {
-        // one cell per thread: load the x-shifted element directly (the warp's load is still
-        // one contiguous span; the neighbour warps' loads keep the extra sector in cache)
-        int xs[2 * M + 1];
+    int xs[2 * M + 1];  // wrapped source x of one cell per thread (V = 1)
 #pragma unroll
-        for (int k = -M; k <= M; ++k) xs[k + M] = wrap1(x0 - k, nx);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cx = vel<LT>(i, 0), cy = vel<LT>(i, 1), cz = vel<LT>(i, 2);
-            const S *row = src + (long long)i * P + (long long)(zs[cz + M] * ny + ys[cy + M]) * nx;
-            f[i][0] = decode<ST>(row[xs[cx + M]], qs, i);
-        }
-    } else {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = vel<LT>(i, 0), cy = vel<LT>(i, 1), cz = vel<LT>(i, 2);
-        const S *row = src + (long long)i * P + (long long)(zs[cz + M] * ny + ys[cy + M]) * nx;
-        S raw[V];
-        load_vec<S, V>(row + x0, raw);
-        T v[V];
-        decode_vec<ST, V>(raw, v, qs, i);
-        if (cx == 0) {
-#pragma unroll
-            for (int j = 0; j < V; ++j) f[i][j] = v[j];
+    for (int k = -M; k <= M; ++k) xs[k + M] = wrap1(x0 - k, nx);
+
+    // The V values of one stored plane pulled along velocity (cx, cy, cz): out[j] holds the
+    // plane's value at x0 + j - cx of row (y - cy, z - cz).  ci: the codec's velocity index.
+    auto pull = [&](const S *__restrict__ plane, int cx, int cy, int cz, int ci, T(&out)[V]) {
+        const long long roff = (long long)(zs[cz + M] * ny + ys[cy + M]) * nx;  // row offset in its plane
+        const S *row = plane + roff;
+        if constexpr (V == 1) {
+            // one cell per thread: load the x-shifted element directly (the warp's load is still
+            // one contiguous span; the neighbour warps' loads keep the extra sector in cache)
+            out[0] = guard(roff + xs[cx + M], 1, P, status) ? decode<ST>(row[xs[cx + M]], qs, ci) : T(0);
         } else {
+            S raw[V] = {};
+            if (guard(roff + x0, V, P, status)) load_vec<S, V>(row + x0, raw);
+            T v[V];
+            decode_vec<ST, V>(raw, v, qs, ci);
+            if (cx == 0) {
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-                const int e = j - cx;  // source element relative to x0
-                const int dl = floordiv(e, V);
-                const int ei = e - dl * V;
-                if (dl == 0) {
-                    f[i][j] = v[ei];
+                for (int j = 0; j < V; ++j) out[j] = v[j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const int e = j - cx;  // source element relative to x0
+                    const int dl = floordiv(e, V);
+                    const int ei = e - dl * V;
+                    if (dl == 0) {
+                        out[j] = v[ei];
+                    } else {
+                        // source lane lane+dl holds chunk+dl of the same row unless at a warp or row edge
+                        const int sl = lane + dl;
+                        T sh = __shfl_sync(kFull, v[ei], sl < 0 ? 0 : (sl > 31 ? 31 : sl));
+                        if (!ok[dl + kMaxDl]) {
+                            const int xw = wrap1(x0 + e, nx);
+                            sh = guard(roff + xw, 1, P, status) ? decode<ST>(row[xw], qs, ci) : T(0);
+                        }
+                        out[j] = sh;
+                    }
+                }
+            }
+        }
+    };
+
+    T f[Q][V];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) pull(src + (long long)i * P, vel<LT>(i, 0), vel<LT>(i, 1), vel<LT>(i, 2), i, f[i]);
+    if constexpr (RefOf<ST>::value) {
+        // add back r_i of the cell each value came from (its reference planes, pulled along
+        // the same velocity); two cells per instruction where V allows
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            T a[3][V];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d < LT::D && vel<LT>(i, d) != 0) {
+                    pull(src + (long long)(Q + d) * P, vel<LT>(i, 0), vel<LT>(i, 1), vel<LT>(i, 2), 0, a[d]);
                 } else {
-                    // source lane lane+dl holds chunk+dl of the same row unless at a warp or row edge
-                    const int sl = lane + dl;
-                    T sh = __shfl_sync(kFull, v[ei], sl < 0 ? 0 : (sl > 31 ? 31 : sl));
-                    if (!ok[dl + kMaxDl]) sh = decode<ST>(row[wrap1(x0 + e, nx)], qs, i);
-                    f[i][j] = sh;
+#pragma unroll
+                    for (int j = 0; j < V; ++j) a[d][j] = T(0);
+                }
+            }
+            if constexpr (V % 2 == 0) {
+#pragma unroll
+                for (int j = 0; j < V; j += 2) {
+                    F2 a2[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) a2[d] = F2(make_float2(a[d][j], a[d][j + 1]));
+                    const F2 h = F2(make_float2(f[i][j], f[i][j + 1])) + ref_value<LT>(i, a2);
+                    f[i][j] = h.v.x;
+                    f[i][j + 1] = h.v.y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const T a1[3] = {a[0][j], a[1][j], a[2][j]};
+                    f[i][j] += ref_value<LT>(i, a1);
                 }
             }
         }
     }
-    }
 
-    // FP32 arithmetic with V >= 2: two cells per pass of the collision on the paired FP32
-    // instructions (F2), which halves the instructions the collision issues; the 16-bit
-    // storage forms, whose steps are issue-bound, gain 7-12%
+    constexpr bool kRef = RefOf<ST>::value;
+    unsigned int acc = 0u;
+    S refraw[3][V];  // the rounded reference a = u / T0 of each cell (reference forms only)
     constexpr bool kPaired = V % 2 == 0 && sizeof(T) == 4;
     if constexpr (kPaired) {
 #pragma unroll
@@ -160,8 +197,35 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
             F2 g[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) g[i] = F2(make_float2(f[i][j], f[i][j + 1]));
-            if constexpr (BGK) collide_bgk<LT, K, F2>(g, F2(relax), F2(rho0));
-            else collide<LT, K, F2, THETA>(g, F2(relax), F2(rho0), F2(kq));
+            F2 u2[3];
+            if constexpr (BGK) collide_bgk<LT, K, F2>(g, F2(relax), F2(rho0), kRef ? u2 : nullptr);
+            else collide<LT, K, F2, THETA>(g, F2(relax), F2(rho0), F2(kq), kRef ? u2 : nullptr);
+            if constexpr (kRef) {
+                // the reference a = u / T0 of both cells rounded to the storage type; the values
+                // keep only their residual h_i - r_i
+                F2 a2[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (d < LT::D) {
+                        T v[2] = {u2[d].v.x, u2[d].v.y}, back[2];
+                        S raw2[2];
+                        encode_vec<ST, 2>(v, raw2, qs, 0, acc);
+                        decode_vec<ST, 2>(raw2, back, qs, 0);
+                        a2[d] = F2(make_float2(back[0], back[1]));
+                        refraw[d][j] = raw2[0];
+                        refraw[d][j + 1] = raw2[1];
+                    } else {
+                        a2[d] = F2(0.0);
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < LT::NP; ++p) {
+                    F2 rp, rm;
+                    ref_pair<LT>(p, a2, rp, rm);
+                    g[2 * p + 1] -= rp;
+                    g[2 * p + 2] -= rm;
+                }
+            }
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 f[i][j] = g[i].v.x;
@@ -174,16 +238,43 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
             T g[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) g[i] = f[i][j];
-            if constexpr (BGK) collide_bgk<LT, K, T>(g, relax, rho0);
-            else collide<LT, K, T, THETA>(g, relax, rho0, kq);
+            T u1[3];
+            if constexpr (BGK) collide_bgk<LT, K, T>(g, relax, rho0, kRef ? u1 : nullptr);
+            else collide<LT, K, T, THETA>(g, relax, rho0, kq, kRef ? u1 : nullptr);
+            if constexpr (kRef) {
+                T a1[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (d < LT::D) {
+                        refraw[d][j] = encode<ST>(u1[d], qs, 0, acc);
+                        a1[d] = decode<ST>(refraw[d][j], qs, 0);
+                    } else {
+                        a1[d] = T(0);
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < LT::NP; ++p) {
+                    T rp, rm;
+                    ref_pair<LT>(p, a1, rp, rm);
+                    g[2 * p + 1] -= rp;
+                    g[2 * p + 2] -= rm;
+                }
+            }
 #pragma unroll
             for (int i = 0; i < Q; ++i) f[i][j] = g[i];
         }
     }
 
-    unsigned int acc = 0u;
-    if (active) {
-        S *out = dst + (long long)(z * ny + y) * nx + x0;
+    const long long ooff = (long long)(z * ny + y) * nx + x0;  // offset of the thread's cells in a plane
+    S *out = dst + ooff;
+    const bool store_ok = active && guard(ooff, V, P, status);
+    if constexpr (kRef) {
+        if (store_ok) {
+#pragma unroll
+            for (int d = 0; d < LT::D; ++d) store_vec<S, V>(out + (long long)(Q + d) * P, refraw[d]);
+        }
+    }
+    if (store_ok) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             S raw[V];
@@ -228,12 +319,15 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
 //    per SM; at 96 five fit and the step runs 8% faster;
 //  - fixed point, two cells per thread, D3Q39, K = 4: 138 registers, three CTAs; at 128 four;
 //  - FP32 energy-flux step, D3Q39, K = 4: 128 registers, four CTAs; at 96 five despite a
-//    56-byte spill, 1.6% faster (at 104, with four CTAs still, 2% slower).
+//    56-byte spill, 1.6% faster (at 104, with four CTAs still, 2% slower);
+//  - reference-velocity storage, four cells per thread, D3Q19: 130 registers, three CTAs; at
+//    128 four.
 // A cap is not applied elsewhere: even a no-op cap changes the register allocation.  The
 // qualifier excludes __launch_bounds__; the launcher keeps blocks at <= 256 threads.
 template <class LT, int K, class ST, int V, bool BGK, bool THETA>
 constexpr int step_direct_cap() {
     if constexpr (THETA && LT::Q == 39 && K == 4 && V == 1 && ST::id == LBM_STORE_F32) return 96;
+    else if constexpr (RefOf<ST>::value && LT::Q == 19 && V == 4 && !BGK && !THETA) return 128;
     else if constexpr (ST::id != LBM_STORE_Q16 || BGK || THETA) return 0;
     else if constexpr (LT::Q == 19 && K == 2 && V == 4) return 96;
     else if constexpr (LT::Q == 39 && K == 4 && V == 2 && !ShiftedOf<ST>::value) return 128;
@@ -278,11 +372,14 @@ cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream
 // f_i(x, 0) = f^eq_i(rho(x), u(x)) is computed in the collision's arithmetic type
 // and written to the stored field at x - c_i, so that the first pull of step 0
 // reads it back at x.
+// The forms with a reference velocity take two passes over the cells: phase 0 stores each
+// cell's reference a = u / T0 (rounded) at its own position; phase 1 stores f^eq relative to
+// the reference of the position it is written to.
 template <class LT, int K, class ST>
 __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__restrict__ rho,
                             const double *__restrict__ u, long long ustride, long long c0, long long count, int nx,
                             int ny, int nz, long long P, double rho0, QScale qs,
-                            unsigned int *__restrict__ status, unsigned int *__restrict__ hmax) {
+                            unsigned int *__restrict__ status, unsigned int *__restrict__ hmax, int phase) {
     using S = typename ST::S;
     using T = typename ST::T;
     unsigned int acc = 0u;
@@ -297,6 +394,17 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
         T uu[3] = {T(0), T(0), T(0)};
 #pragma unroll
         for (int a = 0; a < LT::D; ++a) uu[a] = T(u[a * ustride + k]);
+        if constexpr (RefOf<ST>::value) {
+            if (phase == 0) {
+#pragma unroll
+                if (guard(cell, 1, P, status)) {
+#pragma unroll
+                    for (int a = 0; a < LT::D; ++a)
+                        dst[(long long)(LT::Q + a) * P + cell] = encode<ST>(uu[a] * T(1.0 / LT::T0), qs, 0, acc);
+                }
+                continue;
+            }
+        }
         T g[LT::Q];
         equilibrium_shifted<LT, K, T>(T(r), T(r - rho0), uu, g);
         if (hmax) {  // measuring pass (automatic fixed-point range): nothing is stored
@@ -309,7 +417,20 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
             const int xs = wrapn(x - vel<LT>(i, 0), nx);
             const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
             const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
-            dst[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs] = encode<ST>(T(g[i]), qs, i, acc);
+            const long long at = (long long)(zsrc * ny + ysrc) * nx + xs;
+            if (!guard(at, 1, P, status)) continue;
+            T v = g[i];
+            if constexpr (RefOf<ST>::value) {
+                if (i > 0) {
+                    T a[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        a[d] = (d < LT::D && vel<LT>(i, d) != 0) ? decode<ST>(dst[(long long)(LT::Q + d) * P + at], qs, 0)
+                                                                  : T(0);
+                    v -= ref_value<LT>(i, a);
+                }
+            }
+            dst[(long long)i * P + at] = encode<ST>(v, qs, i, acc);
         }
     }
     if constexpr (ST::id == LBM_STORE_Q16) {
@@ -328,7 +449,7 @@ cudaError_t launch_init(const InitArgs &a, cudaStream_t stream) {
     if (blocks > 65535) blocks = 65535;
     init_kernel<LT, K, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<typename ST::S *>(a.dst), a.rho, a.u,
                                                                   a.ustride, a.c0, a.count, a.nx, a.ny, a.nz, a.P,
-                                                                  a.rho0, a.qs, a.status, a.hmax);
+                                                                  a.rho0, a.qs, a.status, a.hmax, a.phase);
     return cudaGetLastError();
 }
 
@@ -336,7 +457,8 @@ cudaError_t launch_init(const InitArgs &a, cudaStream_t stream) {
 // Pre-collision f_i(x, t) = g_i(x - c_i) decoded to FP64; rho and u per Eq. mme.
 template <class LT, class ST>
 __device__ __forceinline__ void pull_cell(const typename ST::S *__restrict__ src, long long cell, int nx, int ny,
-                                          int nz, long long P, const QScale &qs, double (&gt)[LT::Q]) {
+                                          int nz, long long P, const QScale &qs, double (&gt)[LT::Q],
+                                          unsigned int *status) {
     const int x = int(cell % nx);
     const int y = int((cell / nx) % ny);
     const int z = int(cell / ((long long)nx * ny));
@@ -345,7 +467,22 @@ __device__ __forceinline__ void pull_cell(const typename ST::S *__restrict__ src
         const int xs = wrapn(x - vel<LT>(i, 0), nx);
         const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
         const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
-        gt[i] = weight<LT>(i) * double(decode<ST>(src[(long long)i * P + (long long)(zsrc * ny + ysrc) * nx + xs], qs, i));
+        const long long at = (long long)(zsrc * ny + ysrc) * nx + xs;
+        if (!guard(at, 1, P, status)) {
+            gt[i] = 0.0;
+            continue;
+        }
+        typename ST::T h = decode<ST>(src[(long long)i * P + at], qs, i);
+        if constexpr (RefOf<ST>::value) {  // the value's reference, as the step adds it back
+            using T = typename ST::T;
+            T a[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                a[d] = (d < LT::D && vel<LT>(i, d) != 0) ? decode<ST>(src[(long long)(LT::Q + d) * P + at], qs, 0)
+                                                          : T(0);
+            if (i > 0) h += ref_value<LT>(i, a);
+        }
+        gt[i] = weight<LT>(i) * double(h);
     }
 }
 
@@ -353,11 +490,11 @@ template <class LT, class ST>
 __global__ void moments_kernel(const typename ST::S *__restrict__ src, double *__restrict__ rho,
                                double *__restrict__ u, double *__restrict__ f, long long ustride, long long fstride,
                                long long c0, long long count, int nx, int ny, int nz, long long P, double rho0,
-                               QScale qs) {
+                               QScale qs, unsigned int *__restrict__ status) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
          k += (long long)gridDim.x * blockDim.x) {
         double gt[LT::Q];
-        pull_cell<LT, ST>(src, c0 + k, nx, ny, nz, P, qs, gt);
+        pull_cell<LT, ST>(src, c0 + k, nx, ny, nz, P, qs, gt, status);
         if (f) {
 #pragma unroll
             for (int i = 0; i < LT::Q; ++i) f[i * fstride + k] = gt[i] + weight<LT>(i) * rho0;
@@ -387,7 +524,7 @@ cudaError_t launch_moments(const PullArgs &a, cudaStream_t stream) {
     if (blocks > 65535) blocks = 65535;
     moments_kernel<LT, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const typename ST::S *>(a.src), a.rho,
                                                                   a.u, nullptr, a.ustride, a.fstride, a.c0, a.count,
-                                                                  a.nx, a.ny, a.nz, a.P, a.rho0, a.qs);
+                                                                  a.nx, a.ny, a.nz, a.P, a.rho0, a.qs, a.status);
     return cudaGetLastError();
 }
 
@@ -398,7 +535,7 @@ cudaError_t launch_pull_f(const PullArgs &a, cudaStream_t stream) {
     if (blocks > 65535) blocks = 65535;
     moments_kernel<LT, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const typename ST::S *>(a.src), nullptr,
                                                                   nullptr, a.f, a.ustride, a.fstride, a.c0, a.count,
-                                                                  a.nx, a.ny, a.nz, a.P, a.rho0, a.qs);
+                                                                  a.nx, a.ny, a.nz, a.P, a.rho0, a.qs, a.status);
     return cudaGetLastError();
 }
 
@@ -445,7 +582,8 @@ __global__ void final_reduce_kernel(const double *__restrict__ partials, int blo
 template <class LT, class ST>
 __global__ void __launch_bounds__(kReduceThreads) conservation_kernel(const typename ST::S *__restrict__ src,
                                                                       long long P, double rho0, QScale qs,
-                                                                      double *__restrict__ partials) {
+                                                                      double *__restrict__ partials,
+                                                                      unsigned int *__restrict__ status) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const long long per = (P + gridDim.x - 1) / gridDim.x;
     const long long b0 = blockIdx.x * per;
@@ -457,8 +595,22 @@ __global__ void __launch_bounds__(kReduceThreads) conservation_kernel(const type
     for (int i = 0; i < LT::Q; ++i) acc[i] = 0.0;
     long long n = 0;
     for (long long k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
+        if (!guard(k, 1, P, status)) continue;
+        if constexpr (RefOf<ST>::value) {
+            using T = typename ST::T;
+            T a[3];
 #pragma unroll
-        for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST>(src[(long long)i * P + k], qs, i));
+            for (int d = 0; d < 3; ++d) a[d] = d < LT::D ? decode<ST>(src[(long long)(LT::Q + d) * P + k], qs, 0) : T(0);
+#pragma unroll
+            for (int i = 0; i < LT::Q; ++i) {
+                T h = decode<ST>(src[(long long)i * P + k], qs, i);
+                if (i > 0) h += ref_value<LT>(i, a);
+                acc[i] += double(h);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < LT::Q; ++i) acc[i] += double(decode<ST>(src[(long long)i * P + k], qs, i));
+        }
         ++n;
     }
     v[0] = double(n) * rho0;
@@ -480,7 +632,7 @@ __global__ void __launch_bounds__(kReduceThreads) conservation_kernel(const type
 template <class LT, class ST>
 cudaError_t launch_conservation(const ReduceArgs &a, cudaStream_t stream) {
     conservation_kernel<LT, ST><<<a.blocks, kReduceThreads, 0, stream>>>(static_cast<const typename ST::S *>(a.src),
-                                                                         a.P, a.rho0, a.qs, a.partials);
+                                                                         a.P, a.rho0, a.qs, a.partials, a.status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     final_reduce_kernel<4><<<1, 4 * 32, 0, stream>>>(a.partials, a.blocks, a.out);
@@ -492,14 +644,15 @@ template <class LT, class ST>
 __global__ void __launch_bounds__(kReduceThreads) mode_kernel(const typename ST::S *__restrict__ src, int nx, int ny,
                                                               int nz, long long P, double rho0, int kx, int ky,
                                                               int kz, int comp, QScale qs,
-                                                              double *__restrict__ partials) {
+                                                              double *__restrict__ partials,
+                                                              unsigned int *__restrict__ status) {
     double v[2] = {0.0, 0.0};
     const long long per = (P + gridDim.x - 1) / gridDim.x;
     const long long b0 = blockIdx.x * per;
     const long long b1 = b0 + per < P ? b0 + per : P;
     for (long long cell = b0 + threadIdx.x; cell < b1; cell += blockDim.x) {
         double gt[LT::Q];
-        pull_cell<LT, ST>(src, cell, nx, ny, nz, P, qs, gt);
+        pull_cell<LT, ST>(src, cell, nx, ny, nz, P, qs, gt, status);
         double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int i = 0; i < LT::Q; ++i) {
@@ -526,7 +679,7 @@ template <class LT, class ST>
 cudaError_t launch_mode(const ReduceArgs &a, cudaStream_t stream) {
     mode_kernel<LT, ST><<<a.blocks, kReduceThreads, 0, stream>>>(static_cast<const typename ST::S *>(a.src), a.nx,
                                                                  a.ny, a.nz, a.P, a.rho0, a.k[0], a.k[1], a.k[2],
-                                                                 a.component, a.qs, a.partials);
+                                                                 a.component, a.qs, a.partials, a.status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     final_reduce_kernel<2><<<1, 2 * 32, 0, stream>>>(a.partials, a.blocks, a.out);
@@ -549,10 +702,11 @@ constexpr step_fn direct_if_built() {
     else return &launch_step_direct<LT, K, ST, V>;
 }
 
-// FP64 and fixed-point storage run on the register pull only (no staged variant).
+// FP64, fixed-point and reference-velocity storage run on the register pull only (no staged
+// variant).
 template <class ST>
 constexpr bool register_pull_only() {
-    return sizeof(typename ST::S) == 8 || ST::id == LBM_STORE_Q16;
+    return sizeof(typename ST::S) == 8 || ST::id == LBM_STORE_Q16 || RefOf<ST>::value;
 }
 
 template <class LT, int K, class ST>
@@ -585,16 +739,24 @@ const KernelSet *shifted_set_if_built() {
     else return nullptr;
 }
 
+// Pools run neither the shifted fixed-point codec nor the reference-velocity forms.
 template <class LT, int K, class ST>
 constexpr batch_fn batch_if_built() {
-    if constexpr (ShiftedOf<ST>::value) return nullptr;
+    if constexpr (ShiftedOf<ST>::value || RefOf<ST>::value) return nullptr;
     else return &launch_batch<LT, K, ST>;
 }
 
 template <class LT, int K, class ST>
 constexpr int (*batch_occupancy_if_built())(int, int) {
-    if constexpr (ShiftedOf<ST>::value) return nullptr;
+    if constexpr (ShiftedOf<ST>::value || RefOf<ST>::value) return nullptr;
     else return &batch_occupancy<LT, K, ST>;
+}
+
+// The flat-pair variant pulls with per-cell direct loads and has no reference planes.
+template <class LT, int K, class ST>
+constexpr step_fn pair_if_built() {
+    if constexpr (RefOf<ST>::value) return nullptr;
+    else return &launch_step_pair<LT, K, ST>;
 }
 
 template <class LT, int K, class ST>
@@ -614,7 +776,7 @@ const KernelSet *make_kernel_set() {
         &launch_step_direct<LT, K, ST, 1, true>,
         theta_if_built<LT, K, ST>(),
         staged_check_if_built<LT, ST>(),
-        &launch_step_pair<LT, K, ST>,
+        pair_if_built<LT, K, ST>(),
         shifted_set_if_built<LT, K, ST>(),
     };
     return &ks;
@@ -628,6 +790,8 @@ const KernelSet *kernel_set_for_storage(lbm_storage st) {
     case LBM_STORE_BF16: return make_kernel_set<LT, K, StoreBF16>();
     case LBM_STORE_F64: return make_kernel_set<LT, K, StoreF64>();
     case LBM_STORE_Q16: return make_kernel_set<LT, K, StoreQ16>();
+    case LBM_STORE_F16_REF: return make_kernel_set<LT, K, StoreF16Ref>();
+    case LBM_STORE_BF16_REF: return make_kernel_set<LT, K, StoreBF16Ref>();
     }
     return nullptr;
 }

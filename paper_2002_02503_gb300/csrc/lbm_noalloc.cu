@@ -138,6 +138,8 @@ extern "C" lbm_status lbm_conservation_noalloc(lbm_lattice lattice, lbm_storage 
     if (out_mem != LBM_MEM_HOST && out_mem != LBM_MEM_DEVICE) return set_error(LBM_ERR_INVALID_ARG, "bad lbm_mem");
     if (storage == LBM_STORE_Q16)
         return set_error(LBM_ERR_UNSUPPORTED, "the fixed-point storage needs its range: use lbm_conservation");
+    if (has_reference_planes(storage))
+        return set_error(LBM_ERR_UNSUPPORTED, "the reference-velocity storage forms: use lbm_conservation");
     if (storage != LBM_STORE_F32 && storage != LBM_STORE_F16 && storage != LBM_STORE_BF16 && storage != LBM_STORE_F64)
         return set_error(LBM_ERR_UNSUPPORTED, "unknown storage");
     // the same per-dimension limits as lbm_create (each side >= max|c|, nx and ny <= 2^24,

@@ -108,7 +108,8 @@ constexpr int kStagedMaxCpt = 4;  // cells per consumer thread per tile
 template <class LT, class ST>
 __device__ __forceinline__ void issue_tile_warp(const typename ST::S *__restrict__ src, typename ST::S *stage,
                                                 unsigned long long *bar, int tile, int R, int rows, int nx, int ny,
-                                                int nz, long long P, unsigned int extra_tx, int lane) {
+                                                int nz, long long P, unsigned int extra_tx, int lane,
+                                                unsigned int *status) {
     using S = typename ST::S;
     const int r0 = tile * R;
     const int nr = min(R, rows - r0);
@@ -122,7 +123,16 @@ __device__ __forceinline__ void issue_tile_warp(const typename ST::S *__restrict
         int ys = y - vel_rt<LT>(i, 1), zs = z - vel_rt<LT>(i, 2);
         ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);  // dims >= max|c| (host-checked)
         zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
-        bulk_copy_g2s(stage + (size_t(i) * R + r) * nx, src + i * P + (long long)(zs * ny + ys) * nx, row_bytes, bar);
+        long long roff = (long long)(zs * ny + ys) * nx;
+        if constexpr (kBoundsCheck) {
+            // a row outside the plane is recorded and replaced by the plane's first row, so the
+            // stage still receives the bytes its barrier expects
+            if (!span_in(roff, nx, P)) {
+                if (status) atomicOr(status, kStatusBounds);
+                roff = 0;
+            }
+        }
+        bulk_copy_g2s(stage + (size_t(i) * R + r) * nx, src + i * P + roff, row_bytes, bar);
     }
 }
 
@@ -170,7 +180,7 @@ __global__ void __launch_bounds__(kStagedThreads) step_staged_kernel(const typen
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue_tile_warp<LT, ST>(src, stages + s * stage_elems, &full[s], blockIdx.x + k * gridDim.x, R, rows, nx,
-                                    ny, nz, P, k == 0 ? extra_tx : 0u, lane);
+                                    ny, nz, P, k == 0 ? extra_tx : 0u, lane, status);
             ++issued;
         }
         if (!ok && lane == 0) {
@@ -222,6 +232,7 @@ __global__ void __launch_bounds__(kStagedThreads) step_staged_kernel(const typen
             collide<LT, K, T>(g, relax, rho0);
             S *out = dst + (long long)row * nx + x;
             unsigned int acc = 0u;  // floating storage only: no range to leave
+            if (!guard((long long)row * nx + x, 1, P, status)) continue;
 #pragma unroll
             for (int i = 0; i < Q; ++i) out[(long long)i * P] = encode<ST>(g[i], QScale{}, i, acc);
         }

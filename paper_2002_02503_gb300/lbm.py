@@ -11,14 +11,19 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblbm_gb300.so")
+# LBM_BOUNDS_CHECK=1 selects the bounds-check build (every kernel checks its indices; an index
+# outside its buffer is reported as LBM_ERR_BOUNDS); built by build.build(bounds_check=True)
+BOUNDS_CHECK = os.environ.get("LBM_BOUNDS_CHECK", "") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "liblbm_gb300_bounds.so" if BOUNDS_CHECK else "liblbm_gb300.so")
 
 LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
 LBM_ERR_CUDA, LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_BUSY, LBM_ERR_NOT_FOUND = 4, 5, 6, 7, 8
-LBM_ERR_RANGE = 9
+LBM_ERR_RANGE, LBM_ERR_BOUNDS = 9, 10
 LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2, "D3Q39": 3, "D3Q15": 4}
-STORAGES = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3, "q16": 4}
-STORAGE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8, "q16": 2}
+STORAGES = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3, "q16": 4, "f16r": 5, "bf16r": 6}
+STORAGE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8, "q16": 2, "f16r": 2, "bf16r": 2}
+# forms that store D planes of a per-cell reference velocity after the Q distribution planes
+REFERENCE_FORMS = ("f16r", "bf16r")
 MEM_HOST, MEM_DEVICE = 0, 1
 
 # (name, restype, argtypes) of every exported entry point of include/lbm.h
@@ -50,6 +55,8 @@ SIGNATURES = [
     ("lbm_set_storage_reference", _c.c_int, [_P, _DP]),
     ("lbm_autotune", _c.c_int, [_P, _c.c_int, _DP]),
     ("lbm_conservation_noalloc", _c.c_int, [_c.c_int, _c.c_int, _I64P, _c.c_double, _P, _P, _c.c_int, _P]),
+    ("lbm_bounds_checked", _c.c_int, []),
+    ("lbm_bounds_walk", _c.c_int64, [_c.c_int, _c.c_int, _I64P, _c.c_int64, _c.POINTER(_c.c_int64)]),
     ("lbm_destroy", _c.c_int, [_P]),
     ("lbm_pool_request_bytes", _c.c_size_t, [_c.c_int, _I64P, _c.c_int]),
     ("lbm_pool_create", _c.c_int, [_c.c_int, _c.c_int, _c.c_int, _P, _c.c_size_t, _c.c_int, _P, _P, _c.POINTER(_P)]),
@@ -84,7 +91,7 @@ class LbmError(RuntimeError):
 def _status_name(status):
     names = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_UNSUPPORTED", 3: "LBM_ERR_OUT_OF_MEMORY",
              4: "LBM_ERR_CUDA", 5: "LBM_ERR_NONFINITE", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_BUSY",
-             8: "LBM_ERR_NOT_FOUND", 9: "LBM_ERR_RANGE"}
+             8: "LBM_ERR_NOT_FOUND", 9: "LBM_ERR_RANGE", 10: "LBM_ERR_BOUNDS"}
     return names.get(status, "LBM_STATUS_%d" % status)
 
 
@@ -93,8 +100,9 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("liblbm_gb300.so is not built (run __graft_entry__.build()); "
-                               "the CUDA library is the only implementation")
+            raise RuntimeError("%s is not built (run __graft_entry__.build(); the bounds-check build: "
+                               "build.build(bounds_check=True)); the CUDA library is the only implementation"
+                               % os.path.basename(LIB_PATH))
         L = ctypes.CDLL(LIB_PATH)
         for name, res, args in SIGNATURES:
             fn = getattr(L, name)
@@ -273,6 +281,19 @@ def lbm_conservation_noalloc(lattice, storage, dims, rho0, distributions, out, s
                                           ctypes.c_void_p(stream_ptr)))
 
 
+def lbm_bounds_checked():
+    return bool(lib().lbm_bounds_checked())
+
+
+def lbm_bounds_walk(lattice, cells_per_thread, dims, P):
+    """(accesses outside their plane, accesses checked) of one register-pull launch (host only)."""
+    n = ctypes.c_int64()
+    bad = lib().lbm_bounds_walk(_lat(lattice), int(cells_per_thread), _dims(dims), int(P), ctypes.byref(n))
+    if bad < 0:
+        raise LbmError(LBM_ERR_INVALID_ARG, "lbm_bounds_walk: invalid arguments")
+    return int(bad), int(n.value)
+
+
 def lbm_destroy(h):
     _check(lib().lbm_destroy(h))
 
@@ -346,7 +367,8 @@ class Solver:
         return lbm_time(self.handle)
 
     def raw_bytes(self):
-        return self.info["Q"] * self.C * STORAGE_BYTES[self.storage]
+        planes = self.info["Q"] + (self.info["D"] if self.storage in REFERENCE_FORMS else 0)
+        return planes * self.C * STORAGE_BYTES[self.storage]
 
     def autotune(self, iters=10):
         return lbm_autotune(self.handle, iters)

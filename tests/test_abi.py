@@ -147,3 +147,43 @@ def test_noalloc_dims_use_the_solver_limits(L):
     assert status("D3Q19", (4, 4, 4097)) == lbm.LBM_ERR_INVALID_ARG
     assert status("D3Q19", (0, 4, 4)) == lbm.LBM_ERR_INVALID_ARG
     assert b"dims" in lbm.lib().lbm_last_error() or b"4096" in lbm.lib().lbm_last_error()
+
+
+def test_reference_velocity_forms_host_checks(L):
+    """The forms with a per-cell reference velocity: Q + D planes of two bytes per buffer; pools
+    and the allocation-free sums turn them away before any device work."""
+    C = 64 ** 3
+    n = lbm.lbm_workspace_bytes("D3Q19", (64, 64, 64), "f16r")
+    n16 = lbm.lbm_workspace_bytes("D3Q19", (64, 64, 64), "f16")
+    assert n - n16 == 2 * 3 * C * 2
+    assert lbm.lbm_workspace_bytes("D2Q9", (64, 64, 1), "bf16r") - lbm.lbm_workspace_bytes(
+        "D2Q9", (64, 64, 1), "bf16") == 2 * 2 * 64 * 64 * 2
+    d = (ctypes.c_int64 * 3)(64, 64, 64)
+    assert lbm.lib().lbm_pool_request_bytes(lbm.LATTICES["D3Q19"], d, lbm.STORAGES["f16r"]) == 0
+    out = (ctypes.c_double * 4)()
+    st = lbm.lib().lbm_conservation_noalloc(lbm.LATTICES["D3Q19"], lbm.STORAGES["f16r"], d, 1.0,
+                                            ctypes.c_void_p(256), out, lbm.MEM_HOST, None)
+    assert st == lbm.LBM_ERR_UNSUPPORTED
+
+
+def test_bounds_walk_consistent_and_inconsistent_plane_sizes(L):
+    """The guard's arithmetic on the host: for every cells-per-thread and a set of odd and
+    degenerate sizes, no access of a register-pull launch falls outside a consistent plane
+    (P = nx*ny*nz); with a dims/P pair that disagrees (one element short, or the nz of a bigger
+    lattice) the walk counts the accesses the bounds-check build's kernels would skip."""
+    cases = [("D3Q19", (1, 1, 1)), ("D3Q19", (5, 7, 9)), ("D3Q39", (3, 3, 3)), ("D3Q39", (12, 5, 3)),
+             ("D2Q9", (3, 11, 1)), ("D3Q27", (8, 3, 1)), ("D3Q15", (16, 1, 5)), ("D3Q19", (72, 9, 4))]
+    for name, dims in cases:
+        C = int(np.prod(dims))
+        for V in (1, 2, 4, 8):
+            if dims[0] % V:
+                continue
+            bad, n = lbm.lbm_bounds_walk(name, V, dims, C)
+            assert bad == 0 and n > 0, (name, dims, V)
+            bad, n = lbm.lbm_bounds_walk(name, V, dims, C - 1)
+            assert bad > 0, (name, dims, V)  # the last cell's own store at least
+            bigger = (dims[0], dims[1], dims[2] + 1) if name != "D2Q9" else (dims[0], dims[1] + 1, 1)
+            bad, n = lbm.lbm_bounds_walk(name, V, bigger, C)
+            assert bad > 0, (name, dims, V)
+    assert lbm.lib().lbm_bounds_walk(lbm.LATTICES["D3Q19"], 3, (ctypes.c_int64 * 3)(8, 8, 8), 512, None) == -1
+    assert lbm.lbm_bounds_checked() in (False, True)

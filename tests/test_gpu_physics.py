@@ -124,7 +124,8 @@ def _storage_error(taylor_green_reference, storage):
     return eu
 
 
-@pytest.mark.parametrize("storage,tol", [("f32", TOL_F32), ("f16", TOL_U16), ("q16", 3e-4)])
+@pytest.mark.parametrize("storage,tol", [("f32", TOL_F32), ("f16", TOL_U16), ("q16", 3e-4), ("f16r", 2e-4),
+                                         ("bf16r", TOL_U16)])
 def test_storage_precision_taylor_green_500_steps(taylor_green_reference, storage, tol):
     """Error of each storage form after 500 steps against the FP64 oracle on 64^3 (the 16-bit
     workload, tau = 0.52, at a size the oracle finishes in seconds; the stated sizes are checked

@@ -6,14 +6,17 @@ own FP64 path on the same run, which the parity tests tie to the oracle within 1
 64^3 runs of test_gpu_physics.py compare each form with the oracle directly).  Error on u:
 max|du| / max|u| (u crosses zero); on rho: per element.
 
-Results, as measured on a GB300 (u / rho):
-  256^3: FP32 1.2e-5, FP16 9.3e-3, BF16 9.6e-2, 16-bit fixed point (range 1/4) 1.3e-4
-  512^3: FP32 1.1e-5, FP16 7.8e-3, BF16 3.3e-2, 16-bit fixed point (range 1/4) 2.1e-4
-The fixed-point form meets the 1e-3 target on u at both sizes.  FP16 and BF16 storage of the
-scaled shifted value miss it: the values that carry the momentum (|h| ~ 0.15) round at ~6e-5
-(FP16) or ~5e-4 (BF16) per step, and the errors accumulate.  Those misses are recorded as
-expected failures of the target (strict: a form that starts meeting it fails the record), and
-their measured size is held as a regression ceiling."""
+Relative error on u, as measured on a GB300:
+  256^3: FP32 1.2e-5, FP16 9.3e-3, BF16 9.6e-2, 16-bit fixed point (range 1/4) 1.3e-4,
+         FP16 / BF16 with a per-cell reference velocity 2.7e-5 / 3.9e-4
+  512^3: FP32 1.1e-5, FP16 7.8e-3, BF16 3.3e-2, 16-bit fixed point (range 1/4) 2.1e-4,
+         FP16 / BF16 with a per-cell reference velocity 3.1e-5 / 4.6e-4
+The fixed-point form and both reference-velocity forms meet the 1e-3 target on u at both
+sizes.  FP16 and BF16 storage of the scaled shifted value itself miss it: the values that carry
+the momentum (|h| ~ 0.15) round at ~6e-5 (FP16) or ~5e-4 (BF16) per step, and the errors
+accumulate; with the reference velocity only the residual h_i - r_i (|.| ~ 0.006) is rounded.
+The misses are recorded as expected failures of the target (strict: a form that starts
+meeting it fails the record), and their measured size is held as a regression ceiling."""
 import pytest
 
 from paper_2002_02503_gb300 import fields, lbm
@@ -28,7 +31,7 @@ CEILING = {("256", "f16"): 1.25 * 9.3e-3, ("256", "bf16"): 1.25 * 9.6e-2,
            ("512", "f16"): 1.25 * 7.8e-3, ("512", "bf16"): 1.25 * 3.3e-2}
 Q16_RANGE = 0.25
 
-FORMS = ("f32", "f16", "bf16", "q16")
+FORMS = ("f32", "f16", "bf16", "q16", "f16r", "bf16r")
 
 
 @pytest.fixture(scope="module")
@@ -66,6 +69,15 @@ def errors():
 @pytest.mark.parametrize("key", ["256", "512"])
 def test_fixed_point_storage_meets_u_bound(errors, key):
     eu, er = errors[(key, "q16")]
+    assert eu < TOL_U16
+    assert er < TOL_U16
+
+
+@pytest.mark.parametrize("key", ["256", "512"])
+@pytest.mark.parametrize("storage", ["f16r", "bf16r"])
+def test_16bit_float_with_reference_velocity_meets_u_bound(errors, key, storage):
+    """FP16 and BF16 storage of the residual after a per-cell reference velocity."""
+    eu, er = errors[(key, storage)]
     assert eu < TOL_U16
     assert er < TOL_U16
 
