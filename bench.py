@@ -97,8 +97,9 @@ PRECISION_CONFIGS = [
 
 
 def precision_report(stream):
-    """Errors of the FP32, FP16, BF16 and 16-bit fixed-point storage forms (on the shear waves also
-    fixed point shifted by the equilibrium at the background velocity) on each workload of
+    """Errors of the FP32, FP16, BF16, 16-bit fixed-point and reference-velocity FP16/BF16 storage
+    forms (on the shear waves also fixed point shifted by the equilibrium at the background
+    velocity) on each workload of
     PRECISION_CONFIGS, against the same run with FP64 storage and arithmetic (the FP64 oracle is
     too slow for these sizes; the library's FP64 path matches it within 1e-12 on the parity
     cases).  Taylor-Green: max|du| / max|u| and max|drho| / rho.  Shear wave: the same for the
@@ -115,7 +116,7 @@ def precision_report(stream):
         else:
             rho, u = fields.shear_wave(dims, 0.01, 3, 1, 0, background=(amp, 0.0, 0.0))
         out, ref = {}, None
-        forms = ["f64", "f32", "f16", "bf16", "q16"]
+        forms = ["f64", "f32", "f16", "bf16", "q16", "f16r", "bf16r"]
         if kind == "shear":
             forms.append("q16_ref")  # automatic range, values stored relative to f^eq at U
         for storage in forms:
