@@ -299,7 +299,8 @@ lbm_status lbm_destroy(lbm_solver *s);
 typedef struct lbm_pool lbm_pool;
 
 /* Device bytes one request of these dims occupies in a pool's arena: its two
- * distribution buffers and a 256-byte status word.  0 for invalid arguments and for
+ * distribution buffers (Q planes of px*ny*nz values, px = nx rounded up to a multiple of
+ * 4) and a 256-byte status word.  0 for invalid arguments and for
  * the storage forms pools do not run (the reference-velocity forms). */
 size_t lbm_pool_request_bytes(lbm_lattice lattice, const int64_t dims[3], lbm_storage storage);
 
@@ -355,18 +356,19 @@ lbm_status lbm_pool_set_storage_range(lbm_pool *p, double range);
 lbm_status lbm_pool_get_storage_range(const lbm_pool *p, double *range);
 lbm_status lbm_pool_request_range(const lbm_pool *p, int64_t id, double *range);
 
-/* Kernel configuration of the batched step.  cells_per_thread: the most cells a thread
- * updates, 1 or 2 (the default).  With 2, a request runs two x-neighbours per thread (even
- * nx) or two consecutive cells of the flat index (odd nx), so a request's arithmetic depends
- * on this setting and its own dims only, never on the other residents.  Two cells per
- * thread run the collision on the paired FP32 instructions.  block_threads:
- * 128 or 256 (the default).  Zero keeps the current value.  Waits for the launched chunks.
+/* Kernel configuration of the batched step.  cells_per_thread: the x-neighbours a thread
+ * updates, 1, 2 or 4 (the default).  A pool stores each request with its rows padded to a
+ * multiple of 4 cells whose pad cells hold periodic images of the row's first cells, so
+ * every request runs this setting whatever its nx, and a request's arithmetic depends on the
+ * setting and its own dims only, never on the other residents.  Two and four cells per
+ * thread run the collision on the paired FP32 instructions.  block_threads: 128 (the
+ * default) or 256.  Zero keeps the current value.  Waits for the launched chunks.
  * LBM_ERR_UNSUPPORTED for other values. */
 lbm_status lbm_pool_set_kernel(lbm_pool *p, int cells_per_thread, int block_threads);
 lbm_status lbm_pool_get_kernel(const lbm_pool *p, int *cells_per_thread, int *block_threads);
 
-/* Autotuner for the batch kernel: times each built configuration (cells per thread 1 or 2
- * x block 128 or 256) on the current resident set (state unchanged) and keeps the fastest.
+/* Autotuner for the batch kernel: times each built configuration (cells per thread 1, 2 or
+ * 4 x block 128 or 256) on the current resident set (state unchanged) and keeps the fastest.
  * best_us: time per step. */
 lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us);
 

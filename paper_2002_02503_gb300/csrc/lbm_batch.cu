@@ -5,10 +5,12 @@
 // Execution model
 //   compute stream : per chunk, an H2D copy of the slot table then one graph of
 //                    `chunk` steps (step_index 0..chunk-1).  Each step is one launch
-//                    per slot mode over every resident lattice of that mode that still
-//                    has steps left (with two cells per thread the two modes' kernels
-//                    are forked onto a side stream and joined, so they overlap); the
-//                    join is the step's global barrier.
+//                    of the pool's slot-mode kernel (1, 2 or 4 cells per thread) over
+//                    every resident lattice that still has steps left; the launch
+//                    boundary is the step's global barrier.
+// Every request is stored with its rows padded to a multiple of 4 (pool_pitch), the pad
+// cells holding periodic images of the row's first cells, so every request runs the same
+// register-pull mode whatever its nx.
 //   io stream      : fields upload + f^eq initialisation of new requests, and the
 //                    pull of rho, u of finished ones, overlapping the chunks.
 // The slot table and its pinned host mirror are double-buffered, so at most two
@@ -39,7 +41,9 @@ constexpr int kEventRing = 64;
 struct Request {
     int64_t id;
     int nx, ny, nz;
-    long long C;
+    int px;                            // padded row pitch (pool_pitch(nx))
+    long long C;                       // cells nx ny nz
+    long long Cp;                      // stored cells per plane px ny nz
     double relax, rho0;
     int64_t steps_total, steps_sched;  // steps launched so far
     int parity;                        // buffer holding the state after the launched steps
@@ -64,11 +68,9 @@ struct lbm_pool {
     Arena arena;
     int max_slots;
     cudaStream_t compute, io, capture;
-    cudaStream_t side;             // second stream of the two slot-mode kernels of a step
-    cudaEvent_t fork, join;        // fork to / join from the side stream
     int block;
     int grids[3];  // persistent grid of each slot-mode kernel
-    int cpt;  // most cells per thread a slot may run (1 or 2)
+    int cpt;  // cells per thread of every slot (1, 2 or 4)
     int qexp; // fixed-point storage: grid step 2^qexp
     bool qauto;  // fixed-point storage: each request's range chosen from its own f^eq at admission
     // double-buffered slot tables
@@ -99,9 +101,10 @@ lbm_status ensure_completed(lbm_pool *p, long long upto_exclusive, bool wait) {
     return LBM_OK;
 }
 
-// A request's arena block: its two distribution buffers, then its status word.
-size_t buffer_bytes(int Q, size_t ssize, long long C) { return align_up(size_t(C) * Q * ssize); }
-size_t request_bytes(int Q, size_t ssize, long long C) { return 2 * buffer_bytes(Q, ssize, C) + kAlign; }
+// A request's arena block: its two distribution buffers (Q planes of Cp = px ny nz stored
+// cells), then its status word.
+size_t buffer_bytes(int Q, size_t ssize, long long Cp) { return align_up(size_t(Cp) * Q * ssize); }
+size_t request_bytes(int Q, size_t ssize, long long Cp) { return 2 * buffer_bytes(Q, ssize, Cp) + kAlign; }
 
 // Reads (and clears) a request's status word on the io stream; LBM_ERR_RANGE if set.
 lbm_status request_status(lbm_pool *p, unsigned int *status);
@@ -117,8 +120,7 @@ lbm_status get_graph(lbm_pool *p, long long chunk, int b, cudaGraphExec_t *out) 
     if (e != cudaSuccess) return set_cuda_error(e, "pool: begin capture");
     cudaError_t le = cudaSuccess;
     for (long long s = 0; s < chunk && le == cudaSuccess; ++s)
-        le = p->ks->batch(p->d_table[b], p->d_header[b], int(s), p->grids, p->block, p->cpt, p->capture, p->side,
-                          p->fork, p->join);
+        le = p->ks->batch(p->d_table[b], p->d_header[b], int(s), p->grids, p->block, p->cpt, p->capture);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(p->capture, &g);
     if (le != cudaSuccess) {
@@ -158,9 +160,8 @@ lbm_status set_geometry(lbm_pool *p, int block, int cpt) {
     return LBM_OK;
 }
 
-// Slot mode of a request: one cell per thread, or two -- x-neighbours (row vectors) for
-// even nx, flat-index neighbours otherwise.
-int slot_mode(const lbm_pool *p, const Request &r) { return p->cpt == 1 ? 0 : (r.nx % 2 == 0 ? 1 : 2); }
+// Slot mode of the pool: cells per thread 1, 2 or 4 (every request, thanks to the padded pitch).
+int slot_mode(const lbm_pool *p, const Request &) { return p->cpt == 4 ? 2 : (p->cpt == 2 ? 1 : 0); }
 
 // Writes the table of resident requests with steps left into buffer b, grouped by slot mode
 // (each mode's kernel walks its own unit range); returns the slot count.
@@ -178,10 +179,11 @@ int build_table(lbm_pool *p, int b, int *units_total) {
             s.nx = r.nx;
             s.ny = r.ny;
             s.nz = r.nz;
+            s.px = r.px;
             s.mode = m;
-            s.ncx = m == 1 ? r.nx / 2 : r.nx;
-            s.threads = int(m == 0 ? r.C : (r.C + 1) / 2);
-            s.P = r.C;
+            s.ncx = r.px / p->cpt;
+            s.threads = int((long long)s.ncx * r.ny * r.nz);
+            s.P = r.Cp;
             s.relax = r.relax;
             s.rho0 = r.rho0;
             s.parity = r.parity;
@@ -211,7 +213,8 @@ lbm_status pull_to(lbm_pool *p, Request &r, double *rho, double *u, lbm_mem mem)
     a.nx = r.nx;
     a.ny = r.ny;
     a.nz = r.nz;
-    a.P = r.C;
+    a.px = r.px;
+    a.P = r.Cp;
     a.rho0 = r.rho0;
     a.qs = qscale_of_exponent(r.qexp);
     a.f = nullptr;
@@ -228,7 +231,7 @@ lbm_status pull_to(lbm_pool *p, Request &r, double *rho, double *u, lbm_mem mem)
         if (e != cudaSuccess) return set_cuda_error(e, "pool: moments");
     } else {
         double *stage = static_cast<double *>(r.buf[cur ^ 1]);
-        const size_t cap = buffer_bytes(p->Q, p->ssize, r.C);
+        const size_t cap = buffer_bytes(p->Q, p->ssize, r.Cp);
         const int per_cell = (rho ? 1 : 0) + (u ? p->D : 0);
         if (per_cell == 0) return LBM_OK;
         const long long per = (long long)(cap / (sizeof(double) * per_cell));
@@ -284,7 +287,7 @@ size_t lbm_pool_request_bytes(lbm_lattice lat, const int64_t dims[3], lbm_storag
     if (!lattice_query(lat, &D, &Q, &maxc, &kmax) || storage_bytes(st) == 0) return 0;
     if (has_reference_planes(st)) return 0;  // pools do not run the reference-velocity forms
     if (!dims_check(lat, dims).empty()) return 0;
-    return request_bytes(Q, storage_bytes(st), (long long)dims[0] * dims[1] * dims[2]);
+    return request_bytes(Q, storage_bytes(st), (long long)pool_pitch(int(dims[0])) * dims[1] * dims[2]);
 }
 
 lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, size_t arena_bytes, int max_slots,
@@ -336,16 +339,13 @@ lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, 
             e = cudaMallocHost(reinterpret_cast<void **>(&p->h_header[b]), kBatchHeaderInts * sizeof(int));
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
     for (int k = 0; k < kEventRing && e == cudaSuccess; ++k)
         e = cudaEventCreateWithFlags(&p->chunk_events[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         lbm_pool_destroy(p);
         return set_cuda_error(e, "pool: host setup");
     }
-    lbm_status rs = set_geometry(p, 256, 2);
+    lbm_status rs = set_geometry(p, 128, 4);
     if (rs != LBM_OK) {
         lbm_pool_destroy(p);
         return rs;
@@ -370,15 +370,17 @@ lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, doubl
     r.nx = int(dims[0]);
     r.ny = int(dims[1]);
     r.nz = int(dims[2]);
+    r.px = pool_pitch(r.nx);
     r.C = (long long)dims[0] * dims[1] * dims[2];
+    r.Cp = (long long)r.px * dims[1] * dims[2];
     r.relax = 1.0 - 1.0 / tau;
     r.rho0 = rho0;
     r.steps_total = steps;
     r.steps_sched = 0;
     r.parity = 0;
-    r.bytes = request_bytes(p->Q, p->ssize, r.C);
+    r.bytes = request_bytes(p->Q, p->ssize, r.Cp);
     if (!p->arena.alloc(r.bytes, &r.off)) return set_error(LBM_ERR_BUSY, "pool: arena has no room for this request");
-    const size_t half = buffer_bytes(p->Q, p->ssize, r.C);
+    const size_t half = buffer_bytes(p->Q, p->ssize, r.Cp);
     r.buf[0] = p->arena.base + r.off;
     r.buf[1] = p->arena.base + r.off + half;
     r.status = reinterpret_cast<unsigned int *>(p->arena.base + r.off + 2 * half);
@@ -400,7 +402,8 @@ lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, doubl
     a.nx = r.nx;
     a.ny = r.ny;
     a.nz = r.nz;
-    a.P = r.C;
+    a.px = r.px;
+    a.P = r.Cp;
     a.rho0 = rho0;
     a.status = r.status;
     // one pass of the init kernel, from device memory or staged through the idle buffer
@@ -638,8 +641,8 @@ lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us) {
     cudaEventCreate(&e1);
     float best = 1e30f;
     int best_block = p->block, best_cpt = p->cpt;
-    for (int cfg = 0; cfg < 4; ++cfg) {
-        const int cpt = 1 + (cfg >> 1), block = (cfg & 1) ? 256 : 128;
+    for (int cfg = 0; cfg < 6; ++cfg) {
+        const int cpt = 1 << (cfg >> 1), block = (cfg & 1) ? 256 : 128;
         rs = set_geometry(p, block, cpt);
         if (rs != LBM_OK) break;
         build_table(p, b, &units);  // units depend on the block size and the cells per thread
@@ -648,12 +651,10 @@ lbm_status lbm_pool_autotune(lbm_pool *p, int iters, double *best_us) {
             e = cudaMemcpyAsync(p->d_header[b], p->h_header[b], kBatchHeaderInts * sizeof(int),
                             cudaMemcpyHostToDevice, p->compute);
         for (int w = 0; w < 2 && e == cudaSuccess; ++w)
-            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grids, p->block, p->cpt, p->compute, p->side,
-                             p->fork, p->join);
+            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grids, p->block, p->cpt, p->compute);
         if (e == cudaSuccess) e = cudaEventRecord(e0, p->compute);
         for (int it = 0; it < iters && e == cudaSuccess; ++it)
-            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grids, p->block, p->cpt, p->compute, p->side,
-                             p->fork, p->join);
+            e = p->ks->batch(p->d_table[b], p->d_header[b], 0, p->grids, p->block, p->cpt, p->compute);
         if (e == cudaSuccess) e = cudaEventRecord(e1, p->compute);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -718,7 +719,8 @@ lbm_status lbm_pool_set_kernel(lbm_pool *p, int cells_per_thread, int block_thre
     std::lock_guard<std::mutex> lock(p->mu);
     const int cpt = cells_per_thread == 0 ? p->cpt : cells_per_thread;
     const int block = block_threads == 0 ? p->block : block_threads;
-    if (cpt != 1 && cpt != 2) return set_error(LBM_ERR_UNSUPPORTED, "pool: cells_per_thread must be 1 or 2");
+    if (cpt != 1 && cpt != 2 && cpt != 4)
+        return set_error(LBM_ERR_UNSUPPORTED, "pool: cells_per_thread must be 1, 2 or 4");
     if (block != 128 && block != 256) return set_error(LBM_ERR_UNSUPPORTED, "pool: block_threads must be 128 or 256");
     // the launched chunks hold graphs built for the current geometry: let them finish first
     lbm_status rs = ensure_completed(p, p->chunks, true);
@@ -746,10 +748,6 @@ lbm_status lbm_pool_destroy(lbm_pool *p) {
         if (p->h_table[b]) cudaFreeHost(p->h_table[b]);
         if (p->h_header[b]) cudaFreeHost(p->h_header[b]);
     }
-    if (p->side) cudaStreamSynchronize(p->side);
-    if (p->fork) cudaEventDestroy(p->fork);
-    if (p->join) cudaEventDestroy(p->join);
-    if (p->side) cudaStreamDestroy(p->side);
     if (p->capture) cudaStreamDestroy(p->capture);
     delete p;
     return LBM_OK;

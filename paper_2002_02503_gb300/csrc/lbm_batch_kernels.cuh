@@ -120,19 +120,23 @@ cudaError_t launch_step_pair(const StepArgs &a, int block, cudaStream_t stream) 
 
 // ------------------------------------------------------------------ batched step
 // Persistent kernels over the work units of a slot table (one unit = blockDim.x consecutive
-// threads of one lattice).  The table is sorted by the slots' modes, and each mode has its
-// own kernel over its own range of units, so that each is register-allocated for one code
-// path: MODE 0 runs one cell per thread; MODE 1 two x-neighbours per thread (row vectors,
-// even nx); MODE 2 two consecutive cells of the flat index per thread (any nx).  Modes 1 and
-// 2 run the collision on the paired FP32 instructions.  A request's mode depends only on the
-// pool setting and its own nx, never on the other residents.  One launch per mode advances
-// every slot of that mode with step_index < steps_left by one step; the slot's buffers
-// alternate with its parity.  Header: [total units, slots, first unit of modes 0..2, end
-// unit of modes 0..2] (kBatchHeaderInts).  The table lives in device memory, so a captured
-// graph of launches stays valid while the host rewrites the table between chunks.
+// threads of one lattice).  A pool stores every lattice with its rows padded to a pitch of a
+// multiple of 4 whose pad cells hold periodic images (pull_collide_store, PADDED), so each
+// lattice, whatever its nx, runs the register pull with V = 1, 2 or 4 cells per thread (MODE 0,
+// 1, 2) on aligned row vectors: the pool's slot mode is one V for every resident lattice, and
+// one launch of that mode's kernel advances every slot with step_index < steps_left by one
+// step; the slot's buffers alternate with its parity.  A request's results do not depend on
+// the other residents.  Header: [total units, slots, first unit of modes 0..2, end unit of
+// modes 0..2] (kBatchHeaderInts).  The table lives in device memory, so a captured graph of
+// launches stays valid while the host rewrites the table between chunks.
 
 __device__ __forceinline__ int fastdiv(int n, unsigned int m, unsigned int s) {
     return int((__umulhi((unsigned int)n, m) + (unsigned int)n) >> s);
+}
+
+template <int MODE>
+constexpr int batch_cells() {
+    return MODE == 0 ? 1 : (MODE == 1 ? 2 : 4);
 }
 
 template <class LT, int K, class ST, int MODE>
@@ -162,23 +166,14 @@ __device__ __forceinline__ void batch_step_body(const BatchSlot *__restrict__ sl
         auto *dst = static_cast<typename ST::S *>(sl.buf[cur ^ 1]);
         const typename ST::T relax(sl.relax), rho0(sl.rho0), kq(0);
         const QScale qs = qscale_plain(sl.qmul, sl.qinv);
-        if constexpr (MODE == 2) {
-            if (t >= total) continue;  // no warp collectives on this path
-            const int c0 = 2 * t;
-            const int row = fastdiv(c0, sl.mx, sl.sx);  // c0 / nx
-            const int z = fastdiv(row, sl.my, sl.sy);
-            pull_collide_store_pair<LT, K, ST>(src, dst, sl.nx, sl.ny, sl.nz, sl.P, c0 - row * sl.nx, row - z * sl.ny,
-                                               z, (long long)c0 + 1 < sl.P, relax, rho0, qs, sl.status);
-        } else {
-            const bool active = t < total;
-            if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
-            const int row = fastdiv(t, sl.mx, sl.sx);  // t / ncx
-            const int chunk = t - row * sl.ncx;
-            const int z = fastdiv(row, sl.my, sl.sy);
-            const int y = row - z * sl.ny;
-            pull_collide_store<LT, K, ST, MODE == 1 ? 2 : 1>(src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk,
-                                                             active, relax, rho0, kq, qs, sl.status);
-        }
+        const bool active = t < total;
+        if (!active) t = total - 1;  // inactive lanes still take part in the shuffles
+        const int row = fastdiv(t, sl.mx, sl.sx);  // t / ncx
+        const int chunk = t - row * sl.ncx;
+        const int z = fastdiv(row, sl.my, sl.sy);
+        const int y = row - z * sl.ny;
+        pull_collide_store<LT, K, ST, batch_cells<MODE>(), false, false, true>(
+            src, dst, sl.nx, sl.ny, sl.nz, sl.ncx, sl.P, y, z, chunk, active, relax, rho0, kq, qs, sl.status, sl.px);
     }
 }
 
@@ -188,13 +183,11 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__rest
     batch_step_body<LT, K, ST, MODE>(slots, header, step_index);
 }
 
-// Register cap of a mode's kernel (0 = none; a no-op cap would still change the allocation).
-// Measured on 40 resident D3Q19 lattices, K = 3: the FP16 flat-pair kernel (MODE 2) at 80
-// registers instead of 96 (six 128-thread CTAs per SM instead of five, a 4-byte spill) lifts
-// the pool 1.8%; the FP32 one at 96 or 88 instead of 118, and FP16 at 72, lose.
+// Register cap of a mode's kernel (0 = none; a no-op cap would still change the allocation):
+// the four-cell mode takes the single-lattice four-cell step's cap.
 template <class LT, int K, class ST, int MODE>
 constexpr int batch_cap() {
-    if constexpr (MODE == 2 && LT::Q == 19 && K == 3 && ST::id == LBM_STORE_F16) return 80;
+    if constexpr (MODE == 2) return step_direct_cap<LT, K, ST, 4, false, false>();
     else return 0;
 }
 
@@ -215,42 +208,27 @@ BatchKernel batch_kernel() {
     else return batch_step_kernel<LT, K, ST, MODE>;
 }
 
-// One step of every slot: the MODE 0 kernel with one cell per thread (cpt = 1), else the
-// MODE 1 and MODE 2 kernels; grids[m] is mode m's persistent grid.  The two modes touch
-// disjoint slots, so with a side stream they run side by side: the second kernel's CTAs fill
-// the SMs the first one's last wave leaves idle.
+template <class LT, int K, class ST>
+BatchKernel batch_kernel_of_mode(int mode) {
+    return mode == 2 ? batch_kernel<LT, K, ST, 2>() : (mode == 1 ? batch_kernel<LT, K, ST, 1>()
+                                                                  : batch_kernel<LT, K, ST, 0>());
+}
+
+// One step of every slot: the kernel of the pool's mode (cells per thread 1, 2 or 4);
+// grids[m] is mode m's persistent grid.
 template <class LT, int K, class ST>
 cudaError_t launch_batch(const BatchSlot *slots, const int *header, int step_index, const int *grids, int block,
-                         int cpt, cudaStream_t stream, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
-    if (cpt == 2) {
-        const bool split = side && fork && join;
-        cudaError_t e = cudaSuccess;
-        if (split) {
-            e = cudaEventRecord(fork, stream);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
-            if (e != cudaSuccess) return e;
-        }
-        batch_kernel<LT, K, ST, 1>()<<<grids[1], block, 0, stream>>>(slots, header, step_index);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        batch_kernel<LT, K, ST, 2>()<<<grids[2], block, 0, split ? side : stream>>>(slots, header, step_index);
-        e = cudaGetLastError();
-        if (e != cudaSuccess || !split) return e;
-        e = cudaEventRecord(join, side);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, join, 0);
-        return e;
-    } else {
-        batch_kernel<LT, K, ST, 0>()<<<grids[0], block, 0, stream>>>(slots, header, step_index);
-    }
+                         int cpt, cudaStream_t stream) {
+    const int mode = cpt == 4 ? 2 : (cpt == 2 ? 1 : 0);
+    batch_kernel_of_mode<LT, K, ST>(mode)<<<grids[mode], block, 0, stream>>>(slots, header, step_index);
     return cudaGetLastError();
 }
 
 template <class LT, int K, class ST>
 int batch_occupancy(int block, int mode) {
     int n = 0;
-    const BatchKernel k = mode == 2 ? batch_kernel<LT, K, ST, 2>()
-                                    : (mode == 1 ? batch_kernel<LT, K, ST, 1>() : batch_kernel<LT, K, ST, 0>());
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0);
+    const cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel_of_mode<LT, K, ST>(mode), block, 0);
     return e == cudaSuccess ? n : 0;
 }
 

@@ -111,6 +111,8 @@ struct InitArgs {
     unsigned int *hmax;    // when set: store nothing, only raise *hmax to the largest |h| (float bits)
     int phase;             // forms with a reference velocity: 0 writes each cell's reference planes,
                            // 1 the distributions relative to the references phase 0 wrote
+    int px;                // row pitch of the stored field (0 = nx); pools pad rows to a multiple of 4
+                           // and the pad cells x = nx + k hold images of cells k
 };
 
 struct PullArgs {
@@ -125,6 +127,7 @@ struct PullArgs {
     double rho0;
     QScale qs;
     unsigned int *status;  // bounds-check build: receives kStatusBounds
+    int px;                // row pitch of the stored field (0 = nx)
 };
 
 struct ReduceArgs {
@@ -145,18 +148,18 @@ struct ReduceArgs {
 struct BatchSlot {
     void *buf[2];      // the two distribution buffers of this lattice
     int nx, ny, nz;
-    int mode;          // 0: one cell per thread; 1: two x-neighbours per thread (row vectors, even nx);
-                       // 2: two consecutive cells of the flat index per thread (any nx)
-    int ncx;           // nx / V in modes 0 and 1 (V = 1, 2); nx in mode 2
-    int threads;       // threads the slot's step needs (C, C / 2, ceil(C / 2))
-    long long P;       // cells per velocity plane
+    int px;            // row pitch: nx rounded up to a multiple of 4; pad cells hold periodic images
+    int mode;          // cells per thread: 0: one, 1: two x-neighbours, 2: four x-neighbours (row vectors)
+    int ncx;           // px / V
+    int threads;       // threads the slot's step needs (ncx ny nz)
+    long long P;       // stored cells per velocity plane (px ny nz)
     double relax;      // 1 - 1/tau
     double rho0;
     int parity;        // buffer holding the state at the start of the chunk
     int steps_left;    // steps still to run at the start of the chunk
     int unit0;         // first work unit of this slot (table sorted by unit0)
     int units;         // work units of this slot
-    unsigned int mx, sx, my, sy;  // division by ncx (modes 0, 1) or nx (mode 2) and by ny (fastdiv_init)
+    unsigned int mx, sx, my, sy;  // division by ncx and by ny (fastdiv_init)
     float qmul, qinv;             // fixed-point grid step 2^e and 2^-e (LBM_STORE_Q16 only; no reference shift)
     unsigned int *status;         // this request's status word (kStatusRange)
 };
@@ -164,6 +167,10 @@ struct BatchSlot {
 // Header of a slot table: total units, slots, first unit of slot modes 0..2, end unit of
 // slot modes 0..2.
 constexpr int kBatchHeaderInts = 8;
+
+// Row pitch of a pool request: nx rounded up to a multiple of 4, so that every request can run
+// the register pull with up to four cells per thread on aligned row vectors.
+inline int pool_pitch(int nx) { return (nx + 3) / 4 * 4; }
 
 // Division by a runtime constant d (1 <= d < 2^31) as q = (umulhi(n, m) + n) >> s for
 // 0 <= n < 2^31 -- the round-up multiply-and-shift method of Granlund and Montgomery (1994):
@@ -177,11 +184,9 @@ inline void fastdiv_init(unsigned int d, unsigned int *m, unsigned int *s) {
 }
 
 typedef cudaError_t (*step_fn)(const StepArgs &, int block_threads, cudaStream_t);
-// side, fork, join: a second stream and two events; when given, the two slot-mode kernels
-// of cells_per_thread 2 run side by side (fork on the first stream, join back into it).
+// One step of every slot of the pool's slot mode (cells per thread 1, 2 or 4).
 typedef cudaError_t (*batch_fn)(const BatchSlot *slots, const int *header, int step_index, const int *grids,
-                                int block, int cells_per_thread, cudaStream_t, cudaStream_t side,
-                                cudaEvent_t fork, cudaEvent_t join);
+                                int block, int cells_per_thread, cudaStream_t);
 typedef cudaError_t (*init_fn)(const InitArgs &, cudaStream_t);
 typedef cudaError_t (*pull_fn)(const PullArgs &, cudaStream_t);
 typedef cudaError_t (*reduce_fn)(const ReduceArgs &, cudaStream_t);
@@ -195,7 +200,7 @@ struct KernelSet {
     pull_fn pull_f;
     reduce_fn conservation;  // nvals = 4
     reduce_fn mode;          // nvals = 2
-    batch_fn batch;          // persistent multi-lattice step (1 or at most 2 cells per thread)
+    batch_fn batch;          // persistent multi-lattice step (1, 2 or 4 cells per thread)
     int (*batch_occupancy)(int block, int mode);  // blocks per SM of the slot-mode kernel
     step_fn bgk;             // BGK comparison operator, register pull with V = 1
     step_fn theta;           // filtered collision with the energy-flux term (K >= 3), V = 1

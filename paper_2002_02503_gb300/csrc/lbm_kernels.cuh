@@ -80,17 +80,30 @@ __host__ __device__ constexpr int floordiv(int e, int V) { return e >= 0 ? e / V
 // the missing values directly.  Every lane of the warp must call this (the
 // shuffles use the full mask); lanes with active == false compute on a valid
 // clamped position and store nothing.
-template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false>
+//
+// PADDED (the pools' layout): rows are stored with a pitch px >= nx (a multiple of 4), and
+// the pad cells x = nx + k hold periodic images of cells k.  A pad cell pulls exactly the
+// values its original pulls (its sources are images or, past the row, wrap onto the same
+// cells), so it computes and stores the same bits and the images stay exact; chunks run over
+// the whole pitch (ncx = px / V), and a source x outside the stored row moves by one period
+// nx into it.  Without it px = nx.
+template <class LT, int K, class ST, int V, bool BGK = false, bool THETA = false, bool PADDED = false>
 __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restrict__ src,
                                                    typename ST::S *__restrict__ dst, int nx, int ny, int nz, int ncx,
                                                    long long P, int y, int z, int chunk, bool active,
                                                    typename ST::T relax, typename ST::T rho0, typename ST::T kq,
-                                                   const QScale &qs, unsigned int *__restrict__ status) {
+                                                   const QScale &qs, unsigned int *__restrict__ status,
+                                                   int pitch = 0) {
     using S = typename ST::S;
     using T = typename ST::T;
     constexpr int Q = LT::Q, M = LT::MAXC;
     const int lane = threadIdx.x & 31;
     const int x0 = chunk * V;
+    const int px = PADDED ? pitch : nx;  // row pitch in stored elements
+    // x of a source cell brought into the stored row [0, px) by one period nx: every stored
+    // position congruent to it modulo nx holds its value (pads are images), and x lies in
+    // [-M, px - 1 + M] with nx >= M, so one step either way is enough
+    auto wrapx = [&](int v) { return v < 0 ? v + nx : (v >= px ? v - nx : v); };
 
     int ys[2 * M + 1], zs[2 * M + 1];
 #pragma unroll
@@ -107,12 +120,12 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
 
     int xs[2 * M + 1];  // wrapped source x of one cell per thread (V = 1)
 #pragma unroll
-    for (int k = -M; k <= M; ++k) xs[k + M] = wrap1(x0 - k, nx);
+    for (int k = -M; k <= M; ++k) xs[k + M] = wrapx(x0 - k);
 
     // The V values of one stored plane pulled along velocity (cx, cy, cz): out[j] holds the
     // plane's value at x0 + j - cx of row (y - cy, z - cz).  ci: the codec's velocity index.
     auto pull = [&](const S *__restrict__ plane, int cx, int cy, int cz, int ci, T(&out)[V]) {
-        const long long roff = (long long)(zs[cz + M] * ny + ys[cy + M]) * nx;  // row offset in its plane
+        const long long roff = (long long)(zs[cz + M] * ny + ys[cy + M]) * px;  // row offset in its plane
         const S *row = plane + roff;
         if constexpr (V == 1) {
             // one cell per thread: load the x-shifted element directly (the warp's load is still
@@ -139,7 +152,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
                         const int sl = lane + dl;
                         T sh = __shfl_sync(kFull, v[ei], sl < 0 ? 0 : (sl > 31 ? 31 : sl));
                         if (!ok[dl + kMaxDl]) {
-                            const int xw = wrap1(x0 + e, nx);
+                            const int xw = wrapx(x0 + e);
                             sh = guard(roff + xw, 1, P, status) ? decode<ST>(row[xw], qs, ci) : T(0);
                         }
                         out[j] = sh;
@@ -265,7 +278,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         }
     }
 
-    const long long ooff = (long long)(z * ny + y) * nx + x0;  // offset of the thread's cells in a plane
+    const long long ooff = (long long)(z * ny + y) * px + x0;  // offset of the thread's cells in a plane
     S *out = dst + ooff;
     const bool store_ok = active && guard(ooff, V, P, status);
     if constexpr (kRef) {
@@ -375,11 +388,13 @@ cudaError_t launch_step_direct(const StepArgs &a, int block, cudaStream_t stream
 // The forms with a reference velocity take two passes over the cells: phase 0 stores each
 // cell's reference a = u / T0 (rounded) at its own position; phase 1 stores f^eq relative to
 // the reference of the position it is written to.
+// px: the row pitch of the stored field (nx, or the pools' padded pitch, whose pad cells
+// x = nx + k receive the images of cells k).
 template <class LT, int K, class ST>
 __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__restrict__ rho,
                             const double *__restrict__ u, long long ustride, long long c0, long long count, int nx,
                             int ny, int nz, long long P, double rho0, QScale qs,
-                            unsigned int *__restrict__ status, unsigned int *__restrict__ hmax, int phase) {
+                            unsigned int *__restrict__ status, unsigned int *__restrict__ hmax, int phase, int px) {
     using S = typename ST::S;
     using T = typename ST::T;
     unsigned int acc = 0u;
@@ -397,7 +412,7 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
         if constexpr (RefOf<ST>::value) {
             if (phase == 0) {
 #pragma unroll
-                if (guard(cell, 1, P, status)) {
+                if (guard(cell, 1, P, status)) {  // (reference forms run on single lattices: px = nx)
 #pragma unroll
                     for (int a = 0; a < LT::D; ++a)
                         dst[(long long)(LT::Q + a) * P + cell] = encode<ST>(uu[a] * T(1.0 / LT::T0), qs, 0, acc);
@@ -417,7 +432,7 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
             const int xs = wrapn(x - vel<LT>(i, 0), nx);
             const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
             const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
-            const long long at = (long long)(zsrc * ny + ysrc) * nx + xs;
+            const long long at = (long long)(zsrc * ny + ysrc) * px + xs;
             if (!guard(at, 1, P, status)) continue;
             T v = g[i];
             if constexpr (RefOf<ST>::value) {
@@ -430,7 +445,10 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
                     v -= ref_value<LT>(i, a);
                 }
             }
-            dst[(long long)i * P + at] = encode<ST>(v, qs, i, acc);
+            const typename ST::S code = encode<ST>(v, qs, i, acc);
+            dst[(long long)i * P + at] = code;
+            for (int q = xs + nx; q < px; q += nx)  // the pad images of this position (padded rows)
+                if (guard(at - xs + q, 1, P, status)) dst[(long long)i * P + at - xs + q] = code;
         }
     }
     if constexpr (ST::id == LBM_STORE_Q16) {
@@ -449,7 +467,8 @@ cudaError_t launch_init(const InitArgs &a, cudaStream_t stream) {
     if (blocks > 65535) blocks = 65535;
     init_kernel<LT, K, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<typename ST::S *>(a.dst), a.rho, a.u,
                                                                   a.ustride, a.c0, a.count, a.nx, a.ny, a.nz, a.P,
-                                                                  a.rho0, a.qs, a.status, a.hmax, a.phase);
+                                                                  a.rho0, a.qs, a.status, a.hmax, a.phase,
+                                                                  a.px > 0 ? a.px : a.nx);
     return cudaGetLastError();
 }
 
@@ -458,7 +477,7 @@ cudaError_t launch_init(const InitArgs &a, cudaStream_t stream) {
 template <class LT, class ST>
 __device__ __forceinline__ void pull_cell(const typename ST::S *__restrict__ src, long long cell, int nx, int ny,
                                           int nz, long long P, const QScale &qs, double (&gt)[LT::Q],
-                                          unsigned int *status) {
+                                          unsigned int *status, int px) {
     const int x = int(cell % nx);
     const int y = int((cell / nx) % ny);
     const int z = int(cell / ((long long)nx * ny));
@@ -467,7 +486,7 @@ __device__ __forceinline__ void pull_cell(const typename ST::S *__restrict__ src
         const int xs = wrapn(x - vel<LT>(i, 0), nx);
         const int ysrc = wrapn(y - vel<LT>(i, 1), ny);
         const int zsrc = wrapn(z - vel<LT>(i, 2), nz);
-        const long long at = (long long)(zsrc * ny + ysrc) * nx + xs;
+        const long long at = (long long)(zsrc * ny + ysrc) * px + xs;
         if (!guard(at, 1, P, status)) {
             gt[i] = 0.0;
             continue;
@@ -490,11 +509,11 @@ template <class LT, class ST>
 __global__ void moments_kernel(const typename ST::S *__restrict__ src, double *__restrict__ rho,
                                double *__restrict__ u, double *__restrict__ f, long long ustride, long long fstride,
                                long long c0, long long count, int nx, int ny, int nz, long long P, double rho0,
-                               QScale qs, unsigned int *__restrict__ status) {
+                               QScale qs, unsigned int *__restrict__ status, int px) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
          k += (long long)gridDim.x * blockDim.x) {
         double gt[LT::Q];
-        pull_cell<LT, ST>(src, c0 + k, nx, ny, nz, P, qs, gt, status);
+        pull_cell<LT, ST>(src, c0 + k, nx, ny, nz, P, qs, gt, status, px);
         if (f) {
 #pragma unroll
             for (int i = 0; i < LT::Q; ++i) f[i * fstride + k] = gt[i] + weight<LT>(i) * rho0;
@@ -524,7 +543,8 @@ cudaError_t launch_moments(const PullArgs &a, cudaStream_t stream) {
     if (blocks > 65535) blocks = 65535;
     moments_kernel<LT, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const typename ST::S *>(a.src), a.rho,
                                                                   a.u, nullptr, a.ustride, a.fstride, a.c0, a.count,
-                                                                  a.nx, a.ny, a.nz, a.P, a.rho0, a.qs, a.status);
+                                                                  a.nx, a.ny, a.nz, a.P, a.rho0, a.qs, a.status,
+                                                                  a.px > 0 ? a.px : a.nx);
     return cudaGetLastError();
 }
 
@@ -535,7 +555,8 @@ cudaError_t launch_pull_f(const PullArgs &a, cudaStream_t stream) {
     if (blocks > 65535) blocks = 65535;
     moments_kernel<LT, ST><<<(unsigned)blocks, 256, 0, stream>>>(static_cast<const typename ST::S *>(a.src), nullptr,
                                                                   nullptr, a.f, a.ustride, a.fstride, a.c0, a.count,
-                                                                  a.nx, a.ny, a.nz, a.P, a.rho0, a.qs, a.status);
+                                                                  a.nx, a.ny, a.nz, a.P, a.rho0, a.qs, a.status,
+                                                                  a.px > 0 ? a.px : a.nx);
     return cudaGetLastError();
 }
 
@@ -652,7 +673,7 @@ __global__ void __launch_bounds__(kReduceThreads) mode_kernel(const typename ST:
     const long long b1 = b0 + per < P ? b0 + per : P;
     for (long long cell = b0 + threadIdx.x; cell < b1; cell += blockDim.x) {
         double gt[LT::Q];
-        pull_cell<LT, ST>(src, cell, nx, ny, nz, P, qs, gt, status);
+        pull_cell<LT, ST>(src, cell, nx, ny, nz, P, qs, gt, status, nx);
         double dr = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int i = 0; i < LT::Q; ++i) {

@@ -180,26 +180,27 @@ def test_pool_other_classes_match_single_lattice(lattice, K, storage, sides):
 
 
 def test_cells_per_thread_of_the_batched_step():
-    """Two cells per thread (x-neighbours for even nx, flat-index neighbours for odd nx) against one
-    cell per thread: the same fields within the FP32 tolerance, and a request's result does not
-    depend on the residents."""
-    reqs = [(24, 0.7, 0.05, 30), (25, 0.6, 0.04, 30), (40, 0.55, 0.06, 17)]
+    """Two and four x-neighbours per thread (every nx: the pool pads rows to a multiple of 4 with
+    periodic images) against one cell per thread: the same fields within the FP32 tolerance, and
+    a request's result does not depend on the residents."""
+    reqs = [(24, 0.7, 0.05, 30), (25, 0.6, 0.04, 30), (40, 0.55, 0.06, 17), (7, 0.65, 0.03, 21)]
     one = _run_pool(reqs, kernel=(1, 256))
-    two = _run_pool(reqs, kernel=(2, 128))
-    for k, (side, tau, u0, steps) in enumerate(reqs):
-        assert rel_f(two[k][0], one[k][0]) < TOL_F32
-        assert rel_u(two[k][1], one[k][1]) < TOL_F32
-        r, u = _single(side, tau, u0, steps)
-        assert rel_u(two[k][1], u) < TOL_F32
-    for k in (0, 1):  # an even and an odd nx, alone against the mix
-        alone = _run_pool([reqs[k]], kernel=(2, 128))[0]
-        np.testing.assert_array_equal(alone[1], two[k][1])
+    for cpt in (2, 4):
+        many = _run_pool(reqs, kernel=(cpt, 128))
+        for k, (side, tau, u0, steps) in enumerate(reqs):
+            assert rel_f(many[k][0], one[k][0]) < TOL_F32
+            assert rel_u(many[k][1], one[k][1]) < TOL_F32
+            r, u = _single(side, tau, u0, steps)
+            assert rel_u(many[k][1], u) < TOL_F32
+        for k in (0, 1, 3):  # nx = 24, 25 and 7 (pads of 0, 3 and 1 cells), alone against the mix
+            alone = _run_pool([reqs[k]], kernel=(cpt, 128))[0]
+            np.testing.assert_array_equal(alone[1], many[k][1])
     pool = lbm.Pool("D3Q19", 3, "f32", 1 << 24, 4)
-    for bad in [(3, 0), (0, 96)]:
+    assert lbm.lbm_pool_get_kernel(pool.handle) == (4, 128)
+    for bad in [(3, 0), (0, 96), (8, 128)]:
         with pytest.raises(lbm.LbmError) as e:
             lbm.lbm_pool_set_kernel(pool.handle, *bad)
         assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
-    assert lbm.lbm_pool_get_kernel(pool.handle) == (2, 256)
     pool.close()
 
 
