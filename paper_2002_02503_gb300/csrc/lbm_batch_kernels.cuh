@@ -183,11 +183,15 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchSlot *__rest
     batch_step_body<LT, K, ST, MODE>(slots, header, step_index);
 }
 
-// Register cap of a mode's kernel (0 = none; a no-op cap would still change the allocation):
-// the four-cell mode takes the single-lattice four-cell step's cap.
+// Register cap of a mode's kernel (0 = none; a no-op cap would still change the allocation).
+// Measured on 40 resident D3Q19 lattices, K = 3, four cells per thread: FP16 and BF16 at 96
+// registers instead of 126 (five 128-thread CTAs per SM instead of four) gain 1.3% and 2.2%;
+// the fixed-point form loses 2.3% there, and 80 registers lose for all three.  Otherwise the
+// four-cell mode takes the single-lattice four-cell step's cap.
 template <class LT, int K, class ST, int MODE>
 constexpr int batch_cap() {
-    if constexpr (MODE == 2) return step_direct_cap<LT, K, ST, 4, false, false>();
+    if constexpr (MODE == 2 && LT::Q == 19 && (ST::id == LBM_STORE_F16 || ST::id == LBM_STORE_BF16)) return 96;
+    else if constexpr (MODE == 2) return step_direct_cap<LT, K, ST, 4, false, false>();
     else return 0;
 }
 
