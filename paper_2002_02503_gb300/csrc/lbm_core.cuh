@@ -355,36 +355,6 @@ __device__ __forceinline__ void accumulate_scaled(T &acc, int c, T v) {
     else if (c != 0) acc += T(c) * v;
 }
 
-// Accumulate drho = sum w h, j = sum w c h, sum w c c h from scaled values h in
-// pair order (each term is one fused multiply-add with a compile-time constant).
-template <class LT, typename T>
-__device__ __forceinline__ void accumulate_moments(const T (&g)[LT::Q], T &drho, T (&j)[3], T (&m2)[3][3]) {
-    drho = T(LT::w0) * g[0];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        j[a] = neg_zero<T>();
-#pragma unroll
-        for (int b = 0; b < 3; ++b) m2[a][b] = neg_zero<T>();
-    }
-#pragma unroll
-    for (int p = 0; p < LT::NP; ++p) {
-        const T w = T(LT::w(p));
-        const T sp = g[2 * p + 1] + g[2 * p + 2];
-        const T dp = g[2 * p + 1] - g[2 * p + 2];
-        drho += w * sp;
-#pragma unroll
-        for (int a = 0; a < LT::D; ++a) {
-            const int ca = LT::c(p, a);
-            if (ca != 0) j[a] += T(ca * LT::w(p)) * dp;
-#pragma unroll
-            for (int b = a; b < LT::D; ++b) {
-                const int cab = ca * LT::c(p, b);
-                if (cab != 0) m2[a][b] += T(cab * LT::w(p)) * sp;
-            }
-        }
-    }
-}
-
 // ------------------------------------------------------------------ collision
 // Scalar Hermite values h_2..h_K at (s, v2): h_{n+1} = s h_n - n v2 h_{n-1}.
 // Only the orders that exist for this K are formed.
@@ -406,6 +376,169 @@ struct ScalarHermite {
         if constexpr (K >= 5) return s + h3 * T(1.0 / 6.0) + h5 * T(1.0 / 120.0);
         else if constexpr (K >= 3) return s + h3 * T(1.0 / 6.0);
         else return s;
+    }
+};
+
+// The filtered collision in two parts.  Its output depends on the distributions only through
+// drho = sum w h, j = sum w c h and sum w c c h (the moments), so a step may fold each value
+// into MomentSums as it is pulled and drop it, and FilteredOutput forms each post-collision
+// value from the moments just before it is stored.  The operations are those of collide()
+// below (without the energy-flux term), in the same order.
+template <class LT, typename T>
+struct MomentSums {
+    T drho, j[3], m2[3][3];
+    __device__ __forceinline__ void start(T g0) {
+        drho = T(LT::w0) * g0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            j[a] = neg_zero<T>();
+#pragma unroll
+            for (int b = 0; b < 3; ++b) m2[a][b] = neg_zero<T>();
+        }
+    }
+    // the values of velocity pair p: gp of +c_p, gm of -c_p
+    __device__ __forceinline__ void add_pair(int p, T gp, T gm) {
+        const T w = T(LT::w(p));
+        const T sp = gp + gm;
+        const T dp = gp - gm;
+        drho += w * sp;
+#pragma unroll
+        for (int a = 0; a < LT::D; ++a) {
+            const int ca = LT::c(p, a);
+            if (ca != 0) j[a] += T(ca * LT::w(p)) * dp;
+#pragma unroll
+            for (int b = a; b < LT::D; ++b) {
+                const int cab = ca * LT::c(p, b);
+                if (cab != 0) m2[a][b] += T(cab * LT::w(p)) * sp;
+            }
+        }
+    }
+};
+
+// Accumulate drho = sum w h, j = sum w c h, sum w c c h from scaled values h in
+// pair order (each term is one fused multiply-add with a compile-time constant).
+template <class LT, typename T>
+__device__ __forceinline__ void accumulate_moments(const T (&g)[LT::Q], T &drho, T (&j)[3], T (&m2)[3][3]) {
+    MomentSums<LT, T> ms;
+    ms.start(g[0]);
+#pragma unroll
+    for (int p = 0; p < LT::NP; ++p) ms.add_pair(p, g[2 * p + 1], g[2 * p + 2]);
+    drho = ms.drho;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        j[a] = ms.j[a];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) m2[a][b] = ms.m2[a][b];
+    }
+}
+
+// Post-collision values (Eq. lbe-reg, scaled and shifted) from the moments: rest() for the rest
+// velocity, pair(p) for the pair (+c_p, -c_p).  See collide() for the notation.
+template <class LT, int K, typename T>
+struct FilteredOutput {
+    T drho, rho, us[3], P[3][3], v2, trP, Pu[3], R, kappa;
+    FilteredOutput() = default;
+    __device__ __forceinline__ FilteredOutput(const MomentSums<LT, T> &m, T relax, T rho0, T *us_out = nullptr) {
+        init(m, relax, rho0, us_out);
+    }
+    // us_out, when given, receives u / T0
+    __device__ __forceinline__ void init(const MomentSums<LT, T> &m, T relax, T rho0, T *us_out = nullptr) {
+        constexpr int D = LT::D;
+        const T iT0 = T(1.0 / LT::T0);
+        const T T0 = T(LT::T0);
+        drho = m.drho;
+        rho = rho0 + drho;
+        const T irho = T(1) / rho;
+        T u[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) us[a] = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            u[a] = m.j[a] * irho;
+            us[a] = u[a] * iT0;
+            if (us_out) us_out[a] = us[a];
+        }
+        // Pi^neq = sum c c g~ - T0 drho I - j u  (Eq. coeff-2; equal to Eq. Pi_def)
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) {
+                T v = m.m2[a][b] - m.j[a] * u[b];
+                if (a == b) v -= T0 * drho;
+                P[a][b] = v;
+                P[b][a] = v;
+            }
+        v2 = neg_zero<T>();
+        trP = neg_zero<T>();
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            v2 += u[a] * us[a];  // u.u / T0
+            trP += P[a][a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Pu[a] = neg_zero<T>();  // Pi u / T0
+        R = neg_zero<T>();                                   // u.Pi.u / T0
+        if constexpr (K >= 3) {
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) Pu[a] += P[a][b] * us[b];
+        }
+        if constexpr (K >= 4) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) R += u[a] * Pu[a];
+        }
+        kappa = relax * T(1.0 / (2.0 * LT::T0));  // (1 - 1/tau) / (2 T0)
+    }
+    // rest velocity: s = 0, A = -tr Pi, B = 0; h2 = -v2, h4 = 3 v2^2
+    __device__ __forceinline__ T rest() const {
+        T feq = drho;
+        T fh = -trP;
+        if constexpr (K >= 4) {
+            feq += rho * (v2 * v2 * T(3.0 / 24.0) - v2 * T(0.5));
+            fh = -trP * (T(1) - v2 * T(0.5)) + R;
+        } else {
+            feq -= rho * v2 * T(0.5);
+        }
+        return feq + kappa * fh;
+    }
+    __device__ __forceinline__ void pair(int p, T &gp, T &gm) const {
+        constexpr int D = LT::D;
+        const T iT0 = T(1.0 / LT::T0);
+        T s = neg_zero<T>(), cPc = neg_zero<T>(), B = neg_zero<T>();
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int ca = LT::c(p, a);
+            if (ca == 0) continue;
+            accumulate_scaled(s, ca, us[a]);
+            if constexpr (K >= 3) accumulate_scaled(B, ca, Pu[a]);
+            accumulate_scaled(cPc, ca * ca, P[a][a]);
+#pragma unroll
+            for (int b = a + 1; b < D; ++b) accumulate_scaled(cPc, 2 * ca * LT::c(p, b), P[a][b]);
+        }
+        const T A = cPc * iT0 - trP;
+        const ScalarHermite<K, T> H(s, v2);
+        const T feq_e = drho + rho * H.feq_even();
+        const T feq_o = rho * H.feq_odd(s);
+        T fh_e, fh_o;  // bracket of Eq. hermite-coll, even / odd parts
+        if constexpr (K == 2) {
+            fh_e = A;
+        } else if constexpr (K == 3) {
+            fh_e = A;
+            fh_o = A * s - T(2) * B;
+        } else if constexpr (K == 4) {
+            fh_e = A * (T(1) + H.h2 * T(0.5)) - T(2) * B * s + R;
+            fh_o = A * s - T(2) * B;
+        } else {
+            const T e2 = T(1) + H.h2 * T(0.5);
+            fh_e = A * e2 - T(2) * B * s + R;
+            fh_o = A * (s + H.h3 * T(1.0 / 6.0)) - T(2) * B * e2 + R * s;
+        }
+        const T e = feq_e + kappa * fh_e;
+        T o = feq_o;
+        if constexpr (K >= 3) o += kappa * fh_o;
+        gp = e + o;
+        gm = e - o;
     }
 };
 

@@ -10,6 +10,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lbm_core.cuh"
 #include "lbm_internal.h"
 #include "lbm_staged.cuh"
@@ -162,14 +164,10 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         }
     };
 
-    T f[Q][V];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) pull(src + (long long)i * P, vel<LT>(i, 0), vel<LT>(i, 1), vel<LT>(i, 2), i, f[i]);
-    if constexpr (RefOf<ST>::value) {
-        // add back r_i of the cell each value came from (its reference planes, pulled along
-        // the same velocity); two cells per instruction where V allows
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
+    // reference-velocity forms: add back r_i of the cell each value of velocity i came from (its
+    // reference planes, pulled along the same velocity); two cells per instruction where V allows
+    auto add_reference = [&](int i, T(&v)[V]) {
+        if constexpr (RefOf<ST>::value) {
             T a[3][V];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -186,24 +184,138 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
                     F2 a2[3];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) a2[d] = F2(make_float2(a[d][j], a[d][j + 1]));
-                    const F2 h = F2(make_float2(f[i][j], f[i][j + 1])) + ref_value<LT>(i, a2);
-                    f[i][j] = h.v.x;
-                    f[i][j + 1] = h.v.y;
+                    const F2 h = F2(make_float2(v[j], v[j + 1])) + ref_value<LT>(i, a2);
+                    v[j] = h.v.x;
+                    v[j + 1] = h.v.y;
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < V; ++j) {
                     const T a1[3] = {a[0][j], a[1][j], a[2][j]};
-                    f[i][j] += ref_value<LT>(i, a1);
+                    v[j] += ref_value<LT>(i, a1);
                 }
             }
         }
-    }
+    };
 
     constexpr bool kRef = RefOf<ST>::value;
-    unsigned int acc = 0u;
-    S refraw[3][V];  // the rounded reference a = u / T0 of each cell (reference forms only)
     constexpr bool kPaired = V % 2 == 0 && sizeof(T) == 4;
+    unsigned int acc = 0u;
+
+    // The filtered collision needs the pulled values only through their moments: on the large
+    // velocity sets (Q >= 27) each value is folded into MomentSums as it arrives and dropped, and
+    // each post-collision value is formed from the moments just before it is stored -- no Q x V
+    // array of values is held, which frees the registers four cells per thread need there
+    // (D3Q39 K = 4, FP16, two cells per thread: 126 -> 74 registers).  On the smaller sets the
+    // held values cost fewer registers than the per-cell output constants, and holding them
+    // measured faster (D3Q19 K = 3 FP16 -9%, fixed point -11% when streamed).
+    constexpr bool kStream = !BGK && !THETA && LT::Q >= 27;
+    if constexpr (kStream) {
+        // FP32 arithmetic with V >= 2 runs two cells per pass on the paired FP32 instructions.
+        const long long ooff = (long long)(z * ny + y) * px + x0;  // offset of the thread's cells in a plane
+        S *out = dst + ooff;
+        const bool store_ok = active && guard(ooff, V, P, status);
+        using A = typename std::conditional<kPaired, F2, T>::type;
+        constexpr int NA = kPaired ? V / 2 : V;
+        auto pack = [&](const T(&v)[V], int n) -> A {
+            if constexpr (kPaired) return F2(make_float2(v[2 * n], v[2 * n + 1]));
+            else return v[n];
+        };
+        auto unpack = [&](A x, T(&v)[V], int n) {
+            if constexpr (kPaired) {
+                v[2 * n] = x.v.x;
+                v[2 * n + 1] = x.v.y;
+            } else {
+                v[n] = x;
+            }
+        };
+        auto store_plane = [&](int i, const T(&v)[V]) {
+            S raw[V];
+            encode_vec<ST, V>(v, raw, qs, i, acc);
+            if (store_ok) store_vec<S, V>(out + (long long)i * P, raw);
+        };
+        MomentSums<LT, A> ms[NA];
+        {
+            T v0[V];
+            pull(src, 0, 0, 0, 0, v0);
+#pragma unroll
+            for (int n = 0; n < NA; ++n) ms[n].start(pack(v0, n));
+        }
+#pragma unroll
+        for (int p = 0; p < LT::NP; ++p) {
+            const int ip = 2 * p + 1, im = 2 * p + 2;
+            T vp[V], vm[V];
+            pull(src + (long long)ip * P, vel<LT>(ip, 0), vel<LT>(ip, 1), vel<LT>(ip, 2), ip, vp);
+            pull(src + (long long)im * P, vel<LT>(im, 0), vel<LT>(im, 1), vel<LT>(im, 2), im, vm);
+            add_reference(ip, vp);
+            add_reference(im, vm);
+#pragma unroll
+            for (int n = 0; n < NA; ++n) ms[n].add_pair(p, pack(vp, n), pack(vm, n));
+        }
+        FilteredOutput<LT, K, A> fo[NA];
+        A us_n[NA][3];
+#pragma unroll
+        for (int n = 0; n < NA; ++n) fo[n].init(ms[n], A(relax), A(rho0), kRef ? us_n[n] : nullptr);
+        A ar[NA][3];  // the rounded reference a = u / T0 (reference forms)
+        if constexpr (kRef) {
+            S refraw[3][V];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d < LT::D) {
+                    T v[V], back[V];
+#pragma unroll
+                    for (int n = 0; n < NA; ++n) unpack(us_n[n][d], v, n);
+                    encode_vec<ST, V>(v, refraw[d], qs, 0, acc);
+                    decode_vec<ST, V>(refraw[d], back, qs, 0);
+#pragma unroll
+                    for (int n = 0; n < NA; ++n) ar[n][d] = pack(back, n);
+                    if (store_ok) store_vec<S, V>(out + (long long)(Q + d) * P, refraw[d]);
+                } else {
+#pragma unroll
+                    for (int n = 0; n < NA; ++n) ar[n][d] = A(0.0);
+                }
+            }
+        }
+        {
+            T v[V];
+#pragma unroll
+            for (int n = 0; n < NA; ++n) unpack(fo[n].rest(), v, n);
+            store_plane(0, v);
+        }
+#pragma unroll
+        for (int p = 0; p < LT::NP; ++p) {
+            T vp[V], vm[V];
+#pragma unroll
+            for (int n = 0; n < NA; ++n) {
+                A gp, gm;
+                fo[n].pair(p, gp, gm);
+                if constexpr (kRef) {
+                    A rp, rm;
+                    ref_pair<LT>(p, ar[n], rp, rm);
+                    gp -= rp;
+                    gm -= rm;
+                }
+                unpack(gp, vp, n);
+                unpack(gm, vm, n);
+            }
+            store_plane(2 * p + 1, vp);
+            store_plane(2 * p + 2, vm);
+        }
+        if constexpr (ST::id == LBM_STORE_Q16) {
+            // one flag per warp that met a value outside the fixed-point range
+            if (__any_sync(kFull, range_exceeded(acc)) && lane == 0 && status) atomicOr(status, kStatusRange);
+        }
+    } else {
+    // held values (smaller velocity sets, BGK and the energy-flux term, which need the values
+    // themselves): pull all of them, collide, store
+    T f[Q][V];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        pull(src + (long long)i * P, vel<LT>(i, 0), vel<LT>(i, 1), vel<LT>(i, 2), i, f[i]);
+        if (i > 0) add_reference(i, f[i]);
+    }
+
+    S refraw[3][V];  // the rounded reference a = u / T0 of each cell (reference forms only)
     if constexpr (kPaired) {
 #pragma unroll
         for (int j = 0; j < V; j += 2) {
@@ -299,6 +411,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         // one flag per warp that met a value outside the fixed-point range
         if (__any_sync(kFull, range_exceeded(acc)) && lane == 0 && status) atomicOr(status, kStatusRange);
     }
+    }
 }
 
 template <class LT, int K, class ST, int V, bool BGK, bool THETA>
@@ -330,7 +443,6 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
 // takes one more CTA per SM without spills, chosen by measurement):
 //  - fixed point, four cells per thread, D3Q19, K = 2: ~108 registers, four 128-thread CTAs
 //    per SM; at 96 five fit and the step runs 8% faster;
-//  - fixed point, two cells per thread, D3Q39, K = 4: 138 registers, three CTAs; at 128 four;
 //  - FP32 energy-flux step, D3Q39, K = 4: 128 registers, four CTAs; at 96 five despite a
 //    56-byte spill, 1.6% faster (at 104, with four CTAs still, 2% slower);
 //  - reference-velocity storage, four cells per thread, D3Q19: 130 registers, three CTAs; at
@@ -343,7 +455,6 @@ constexpr int step_direct_cap() {
     else if constexpr (RefOf<ST>::value && LT::Q == 19 && V == 4 && !BGK && !THETA) return 128;
     else if constexpr (ST::id != LBM_STORE_Q16 || BGK || THETA) return 0;
     else if constexpr (LT::Q == 19 && K == 2 && V == 4) return 96;
-    else if constexpr (LT::Q == 39 && K == 4 && V == 2 && !ShiftedOf<ST>::value) return 128;
     else return 0;
 }
 
@@ -411,7 +522,6 @@ __global__ void init_kernel(typename ST::S *__restrict__ dst, const double *__re
         for (int a = 0; a < LT::D; ++a) uu[a] = T(u[a * ustride + k]);
         if constexpr (RefOf<ST>::value) {
             if (phase == 0) {
-#pragma unroll
                 if (guard(cell, 1, P, status)) {  // (reference forms run on single lattices: px = nx)
 #pragma unroll
                     for (int a = 0; a < LT::D; ++a)
