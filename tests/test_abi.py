@@ -187,3 +187,17 @@ def test_bounds_walk_consistent_and_inconsistent_plane_sizes(L):
             assert bad > 0, (name, dims, V)
     assert lbm.lib().lbm_bounds_walk(lbm.LATTICES["D3Q19"], 3, (ctypes.c_int64 * 3)(8, 8, 8), 512, None) == -1
     assert lbm.lbm_bounds_checked() in (False, True)
+
+
+def test_pool_request_bytes_use_the_padded_pitch(L):
+    """A pool stores each request with its rows padded to a multiple of 4 cells (pad cells hold
+    periodic images): two buffers of Q planes of px*ny*nz values, each 256-byte aligned, and a
+    256-byte status word."""
+    def align(v):
+        return (v + 255) // 256 * 256
+
+    for nx, ny, nz in [(33, 20, 7), (32, 32, 32), (1, 5, 6), (127, 3, 4)]:
+        px = (nx + 3) // 4 * 4
+        want = 2 * align(19 * px * ny * nz * 2) + 256
+        assert lbm.lbm_pool_request_bytes("D3Q19", (nx, ny, nz), "f16") == want, (nx, ny, nz)
+    assert lbm.lbm_pool_request_bytes("D3Q19", (33, 20, 7), "f32") == 2 * align(19 * 36 * 20 * 7 * 4) + 256
