@@ -379,6 +379,155 @@ struct ScalarHermite {
     }
 };
 
+// c * v as the first term of a sum (no addition; no multiply for c = +-1), else added to acc.
+// `has` is known at compile time once the velocity loops are unrolled.
+template <typename T>
+__device__ __forceinline__ void add_term(T &acc, bool &has, int c, T v) {
+    if (c == 0) return;
+    if (has) {
+        accumulate_scaled(acc, c, v);
+    } else {
+        acc = c == 1 ? v : (c == -1 ? -v : T(T(double(c)) * v));
+        has = true;
+    }
+}
+
+// The post-collision values of a velocity pair (+c_p, -c_p), Eq. lbe-reg in scaled shifted
+// form, written as polynomials in s = c_p.u / T0 and q = s^2 whose coefficients depend on the
+// cell only, so they are formed once per cell and each pair costs a few multiply-adds.  With
+//   kappa = (1 - 1/tau) / (2 T0),  kt = kappa tr Pi,  a1 = 1 - v2/2  (v2 = u.u / T0),
+//   Z  = c.(kappa Pi / T0).c = kappa A + kt,   B' = c.(-2 kappa Pi u / T0) = -2 kappa B,
+// and the Hermite values of collide() in s and q,
+//   h2 = q - v2,  h3 = s (q - 3 v2),  h4 = q^2 - 6 v2 q + 3 v2^2,  h5 = s (q^2 - 10 v2 q + 15 v2^2),
+// the even part e and odd part o of drho + rho (E_K - 1) + kappa [bracket] collect to
+//   K = 2:  e = E0 + Z + (rho/2) q,                                    o = rho s
+//   K = 3:  e as K = 2,                                                o = s (O0 + Z + (rho/6) q) + B'
+//   K = 4:  e = E0 + a1 Z + q (E1 + Z/2 + (rho/24) q) + B' s,          o as K = 3
+//   K = 5:  e as K = 4,  o = s (O0 + a1 Z + q (O1 + Z/6 + (rho/120) q)) + B' (a1 + q/2)
+// with the per-cell constants
+//   K = 2, 3:  E0 = drho - (rho/2) v2 - kt,                    O0 = rho a1 - kt
+//   K = 4, 5:  E0 = drho + rho (v2^2/8 - v2/2) + kappa R - kt a1,   E1 = rho (1/2 - v2/4) - kt/2
+//   K = 4:     O0 = rho a1 - kt
+//   K = 5:     O0 = rho (1 - v2/2 + v2^2/8) - kt a1 + kappa R,      O1 = rho (1/6 - v2/12) - kt/6.
+// At s = 0 (the rest velocity, where A = -tr Pi and B = 0) the value is E0 for every K.
+template <class LT, int K, typename T>
+struct PairPoly {
+    T us[3], Pk[3][3], Bk[3];
+    T E0, E1, O0, O1, a1, rE, rO;
+    __device__ __forceinline__ void init(T drho, T rho, const T (&us_)[3], const T (&P)[3][3], T v2, T trP,
+                                         const T (&Pu)[3], T R, T kappa) {
+        constexpr int D = LT::D;
+        const T kP = kappa * T(1.0 / LT::T0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) us[a] = us_[a];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) Pk[a][b] = kP * P[a][b];
+        if constexpr (K >= 3) {
+            const T m2k = kappa * T(-2.0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) Bk[a] = m2k * Pu[a];
+        }
+        const T kt = kappa * trP;
+        a1 = T(1) - v2 * T(0.5);
+        if constexpr (K <= 3) {
+            const T rh = rho * T(0.5);
+            E0 = drho - rh * v2;
+            E0 = E0 - kt;
+            rE = rh;
+            if constexpr (K == 2) {
+                rO = rho;
+            } else {
+                O0 = rho * a1 - kt;
+                rO = rho * T(1.0 / 6.0);
+            }
+        } else {
+            const T c2 = v2 * T(0.125) - T(0.5);  // v2/8 - 1/2
+            const T t = c2 * v2;
+            E0 = drho + rho * t;
+            E0 = E0 + kappa * R;
+            E0 = E0 - kt * a1;
+            const T c1 = T(0.5) - v2 * T(0.25);
+            E1 = rho * c1 - kt * T(0.5);
+            rE = rho * T(1.0 / 24.0);
+            if constexpr (K == 4) {
+                O0 = rho * a1 - kt;
+                rO = rho * T(1.0 / 6.0);
+            } else {
+                const T c0 = c2 * v2 + T(1);  // 1 - v2/2 + v2^2/8
+                O0 = rho * c0;
+                O0 = O0 - kt * a1;
+                O0 = O0 + kappa * R;
+                const T c3 = T(1.0 / 6.0) - v2 * T(1.0 / 12.0);
+                O1 = rho * c3 - kt * T(1.0 / 6.0);
+                rO = rho * T(1.0 / 120.0);
+            }
+        }
+    }
+    __device__ __forceinline__ T rest() const { return E0; }
+    // s = c_p.u / T0
+    __device__ __forceinline__ T dot(int p) const {
+        T s = neg_zero<T>();
+        bool has = false;
+#pragma unroll
+        for (int a = 0; a < LT::D; ++a) add_term(s, has, LT::c(p, a), us[a]);
+        return s;
+    }
+    // even and odd parts of the pair's values: g(+c_p) = e + o, g(-c_p) = e - o
+    __device__ __forceinline__ void eo(int p, T s, T &e, T &o) const {
+        constexpr int D = LT::D;
+        T Z = neg_zero<T>(), B = neg_zero<T>();
+        bool hz = false, hb = false;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int ca = LT::c(p, a);
+            if (ca == 0) continue;
+            if constexpr (K >= 3) add_term(B, hb, ca, Bk[a]);
+            add_term(Z, hz, ca * ca, Pk[a][a]);
+#pragma unroll
+            for (int b = a + 1; b < D; ++b) add_term(Z, hz, 2 * ca * LT::c(p, b), Pk[a][b]);
+        }
+        const T q = s * s;
+        if constexpr (K <= 3) {
+            const T ez = E0 + Z;
+            e = ez + rE * q;
+            if constexpr (K == 2) {
+                o = rO * s;
+            } else {
+                const T oz = O0 + Z;
+                const T y = oz + rO * q;
+                o = s * y + B;
+            }
+        } else {
+            const T t1 = E0 + a1 * Z;
+            const T t2 = E1 + Z * T(0.5);
+            const T t3 = t2 + rE * q;
+            const T t4 = t1 + q * t3;
+            e = t4 + B * s;
+            if constexpr (K == 4) {
+                const T oz = O0 + Z;
+                const T y = oz + rO * q;
+                o = s * y + B;
+            } else {
+                const T t5 = O0 + a1 * Z;
+                const T t6 = O1 + Z * T(1.0 / 6.0);
+                const T t7 = t6 + rO * q;
+                const T t8 = t5 + q * t7;
+                const T w = a1 + q * T(0.5);
+                const T bw = B * w;
+                o = s * t8 + bw;
+            }
+        }
+    }
+    __device__ __forceinline__ void pair(int p, T &gp, T &gm) const {
+        T e, o;
+        eo(p, dot(p), e, o);
+        gp = e + o;
+        gm = e - o;
+    }
+};
+
 // The filtered collision in two parts.  Its output depends on the distributions only through
 // drho = sum w h, j = sum w c h and sum w c c h (the moments), so a step may fold each value
 // into MomentSums as it is pulled and drop it, and FilteredOutput forms each post-collision
@@ -436,7 +585,7 @@ __device__ __forceinline__ void accumulate_moments(const T (&g)[LT::Q], T &drho,
 // velocity, pair(p) for the pair (+c_p, -c_p).  See collide() for the notation.
 template <class LT, int K, typename T>
 struct FilteredOutput {
-    T drho, rho, us[3], P[3][3], v2, trP, Pu[3], R, kappa;
+    PairPoly<LT, K, T> poly;
     FilteredOutput() = default;
     __device__ __forceinline__ FilteredOutput(const MomentSums<LT, T> &m, T relax, T rho0, T *us_out = nullptr) {
         init(m, relax, rho0, us_out);
@@ -446,10 +595,10 @@ struct FilteredOutput {
         constexpr int D = LT::D;
         const T iT0 = T(1.0 / LT::T0);
         const T T0 = T(LT::T0);
-        drho = m.drho;
-        rho = rho0 + drho;
+        const T drho = m.drho;
+        const T rho = rho0 + drho;
         const T irho = T(1) / rho;
-        T u[3];
+        T u[3], us[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) us[a] = T(0);
 #pragma unroll
@@ -459,6 +608,7 @@ struct FilteredOutput {
             if (us_out) us_out[a] = us[a];
         }
         // Pi^neq = sum c c g~ - T0 drho I - j u  (Eq. coeff-2; equal to Eq. Pi_def)
+        T P[3][3];
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -468,16 +618,14 @@ struct FilteredOutput {
                 P[a][b] = v;
                 P[b][a] = v;
             }
-        v2 = neg_zero<T>();
-        trP = neg_zero<T>();
+        T v2 = neg_zero<T>(), trP = neg_zero<T>();
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             v2 += u[a] * us[a];  // u.u / T0
             trP += P[a][a];
         }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) Pu[a] = neg_zero<T>();  // Pi u / T0
-        R = neg_zero<T>();                                   // u.Pi.u / T0
+        T Pu[3] = {neg_zero<T>(), neg_zero<T>(), neg_zero<T>()};  // Pi u / T0
+        T R = neg_zero<T>();                                      // u.Pi.u / T0
         if constexpr (K >= 3) {
 #pragma unroll
             for (int a = 0; a < D; ++a)
@@ -488,58 +636,11 @@ struct FilteredOutput {
 #pragma unroll
             for (int a = 0; a < D; ++a) R += u[a] * Pu[a];
         }
-        kappa = relax * T(1.0 / (2.0 * LT::T0));  // (1 - 1/tau) / (2 T0)
+        const T kappa = relax * T(1.0 / (2.0 * LT::T0));  // (1 - 1/tau) / (2 T0)
+        poly.init(drho, rho, us, P, v2, trP, Pu, R, kappa);
     }
-    // rest velocity: s = 0, A = -tr Pi, B = 0; h2 = -v2, h4 = 3 v2^2
-    __device__ __forceinline__ T rest() const {
-        T feq = drho;
-        T fh = -trP;
-        if constexpr (K >= 4) {
-            feq += rho * (v2 * v2 * T(3.0 / 24.0) - v2 * T(0.5));
-            fh = -trP * (T(1) - v2 * T(0.5)) + R;
-        } else {
-            feq -= rho * v2 * T(0.5);
-        }
-        return feq + kappa * fh;
-    }
-    __device__ __forceinline__ void pair(int p, T &gp, T &gm) const {
-        constexpr int D = LT::D;
-        const T iT0 = T(1.0 / LT::T0);
-        T s = neg_zero<T>(), cPc = neg_zero<T>(), B = neg_zero<T>();
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const int ca = LT::c(p, a);
-            if (ca == 0) continue;
-            accumulate_scaled(s, ca, us[a]);
-            if constexpr (K >= 3) accumulate_scaled(B, ca, Pu[a]);
-            accumulate_scaled(cPc, ca * ca, P[a][a]);
-#pragma unroll
-            for (int b = a + 1; b < D; ++b) accumulate_scaled(cPc, 2 * ca * LT::c(p, b), P[a][b]);
-        }
-        const T A = cPc * iT0 - trP;
-        const ScalarHermite<K, T> H(s, v2);
-        const T feq_e = drho + rho * H.feq_even();
-        const T feq_o = rho * H.feq_odd(s);
-        T fh_e, fh_o;  // bracket of Eq. hermite-coll, even / odd parts
-        if constexpr (K == 2) {
-            fh_e = A;
-        } else if constexpr (K == 3) {
-            fh_e = A;
-            fh_o = A * s - T(2) * B;
-        } else if constexpr (K == 4) {
-            fh_e = A * (T(1) + H.h2 * T(0.5)) - T(2) * B * s + R;
-            fh_o = A * s - T(2) * B;
-        } else {
-            const T e2 = T(1) + H.h2 * T(0.5);
-            fh_e = A * e2 - T(2) * B * s + R;
-            fh_o = A * (s + H.h3 * T(1.0 / 6.0)) - T(2) * B * e2 + R * s;
-        }
-        const T e = feq_e + kappa * fh_e;
-        T o = feq_o;
-        if constexpr (K >= 3) o += kappa * fh_o;
-        gp = e + o;
-        gm = e - o;
-    }
+    __device__ __forceinline__ T rest() const { return poly.rest(); }
+    __device__ __forceinline__ void pair(int p, T &gp, T &gm) const { poly.pair(p, gp, gm); }
 };
 
 // g: scaled shifted pre-collision values h = (f - w rho0)/w in pair order;
@@ -547,7 +648,8 @@ struct FilteredOutput {
 // relax = 1 - 1/tau.  Divided by w_i, the two parts read
 //   (f^eq - w rho0)/w = drho + rho (E_K - 1)
 //   fhat / w          = 1/(2 T0) [E_{K-2} A - 2 E_{K-3} B + E_{K-4} R]
-// with the even/odd parts of E_n written out for K = 2..5 (E_n = 0 for n < 0).
+// with the even/odd parts of E_n written out for K = 2..5 (E_n = 0 for n < 0); PairPoly
+// forms them for each velocity pair as polynomials in s = c.u / T0 with per-cell coefficients.
 // Energy-flux part (Eq. pq, theta != 0): the series of Eq. filter-Q truncated at the same
 // K reduces, with Qt the relative-frame flux of Eq. Q_def and q_a = Qt_abb, to
 //   fhat^q / w = 1/(6 T0^3) sum_{m=0}^{K-3} sum_k a_k h_{m-k}/(m-k)!
@@ -603,8 +705,10 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0, T kq = T
         for (int a = 0; a < D; ++a) R += u[a] * Pu[a];
     }
     const T kappa = relax * T(1.0 / (2.0 * LT::T0));  // (1 - 1/tau) / (2 T0)
+    PairPoly<LT, K, T> poly;
+    poly.init(drho, rho, us, P, v2, trP, Pu, R, kappa);
 
-    // energy flux: Qt (symmetric, stored for a <= b <= c), q, Qt u, Qt u u
+    // energy flux: Qt (symmetric, stored for a <= b <= c), q, Qt u (symmetric), Qt u u
     T Qt[3][3][3], q[3], Qu[3][3], Quu[3];
     T uq = T(0);
     if constexpr (THETA) {
@@ -614,13 +718,32 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0, T kq = T
             for (int b = 0; b < 3; ++b)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) Qt[a][b][c] = neg_zero<T>();
+        // 2 rho feq_odd(s) = s y(q): y = 2 rho (1 - v2/2 + q/6) for K = 3, 4 and
+        // 2 rho (1 - v2/2 + v2^2/8 + q (1/6 - v2/12) + q^2/120) for K = 5 (q = s^2)
+        const T r2 = rho * T(2);
+        T f0, f1, f2;
+        if constexpr (K <= 4) {
+            f0 = r2 * poly.a1;
+            f1 = rho * T(1.0 / 3.0);
+        } else {
+            const T c0 = v2 * (v2 * T(0.125) - T(0.5)) + T(1);
+            f0 = r2 * c0;
+            const T c1 = T(1.0 / 6.0) - v2 * T(1.0 / 12.0);
+            f1 = r2 * c1;
+            f2 = rho * T(1.0 / 60.0);
+        }
 #pragma unroll
         for (int p = 0; p < LT::NP; ++p) {
-            T s = neg_zero<T>();
-#pragma unroll
-            for (int a = 0; a < D; ++a) accumulate_scaled(s, LT::c(p, a), us[a]);
-            const ScalarHermite<K, T> H(s, v2);
-            const T d = (g[2 * p + 1] - g[2 * p + 2]) - T(2) * rho * H.feq_odd(s);  // odd part of h - h^eq
+            const T s = poly.dot(p);
+            const T qq = s * s;
+            T y;
+            if constexpr (K <= 4) {
+                y = f0 + f1 * qq;
+            } else {
+                const T y1 = f1 + f2 * qq;
+                y = f0 + qq * y1;
+            }
+            const T d = (g[2 * p + 1] - g[2 * p + 2]) - s * y;  // odd part of h - h^eq
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -650,11 +773,14 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0, T kq = T
             q[a] = neg_zero<T>();
             Quu[a] = neg_zero<T>();
 #pragma unroll
-            for (int b = 0; b < D; ++b) {
-                q[a] += Qt[a][b][b];
-                Qu[a][b] = neg_zero<T>();
+            for (int b = 0; b < D; ++b) q[a] += Qt[a][b][b];
 #pragma unroll
-                for (int c = 0; c < D; ++c) Qu[a][b] += Qt[a][b][c] * u[c];
+            for (int b = a; b < D; ++b) {
+                T v = neg_zero<T>();
+#pragma unroll
+                for (int c = 0; c < D; ++c) v += Qt[a][b][c] * u[c];
+                Qu[a][b] = v;
+                Qu[b][a] = v;
             }
         }
 #pragma unroll
@@ -665,71 +791,35 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0, T kq = T
         }
     }
 
-    // rest velocity: s = 0, A = -tr Pi, B = 0; h2 = -v2, h4 = 3 v2^2
-    {
-        T feq = drho;
-        T fh = -trP;
-        if constexpr (K >= 4) {
-            feq += rho * (v2 * v2 * T(3.0 / 24.0) - v2 * T(0.5));
-            fh = -trP * (T(1) - v2 * T(0.5)) + R;
-        } else {
-            feq -= rho * v2 * T(0.5);
-        }
-        g[0] = feq + kappa * fh;
-        // energy flux at c = 0: a_0 = a_2 = 0, a_1 = 3 T0 u.q enters from K = 4 on
-        if constexpr (THETA && K >= 4) g[0] += kq * T(3.0 * LT::T0) * uq;
-    }
+    g[0] = poly.rest();
+    // energy flux at c = 0: a_0 = a_2 = 0, a_1 = 3 T0 u.q enters from K = 4 on
+    if constexpr (THETA && K >= 4) g[0] += kq * T(3.0 * LT::T0) * uq;
 #pragma unroll
     for (int p = 0; p < LT::NP; ++p) {
-        T s = neg_zero<T>(), cPc = neg_zero<T>(), B = neg_zero<T>();
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const int ca = LT::c(p, a);
-            if (ca == 0) continue;
-            accumulate_scaled(s, ca, us[a]);
-            if constexpr (K >= 3) accumulate_scaled(B, ca, Pu[a]);
-            accumulate_scaled(cPc, ca * ca, P[a][a]);
-#pragma unroll
-            for (int b = a + 1; b < D; ++b) accumulate_scaled(cPc, 2 * ca * LT::c(p, b), P[a][b]);
-        }
-        const T A = cPc * iT0 - trP;
-        const ScalarHermite<K, T> H(s, v2);
-        const T feq_e = drho + rho * H.feq_even();
-        const T feq_o = rho * H.feq_odd(s);
-        T fh_e, fh_o;  // bracket of Eq. hermite-coll, even / odd parts
-        if constexpr (K == 2) {
-            fh_e = A;
-        } else if constexpr (K == 3) {
-            fh_e = A;
-            fh_o = A * s - T(2) * B;
-        } else if constexpr (K == 4) {
-            fh_e = A * (T(1) + H.h2 * T(0.5)) - T(2) * B * s + R;
-            fh_o = A * s - T(2) * B;
-        } else {
-            const T e2 = T(1) + H.h2 * T(0.5);
-            fh_e = A * e2 - T(2) * B * s + R;
-            fh_o = A * (s + H.h3 * T(1.0 / 6.0)) - T(2) * B * e2 + R * s;
-        }
-        T e = feq_e + kappa * fh_e;
-        T o = feq_o;
-        if constexpr (K >= 3) o += kappa * fh_o;
+        const T s = poly.dot(p);
+        T e, o;
+        poly.eo(p, s, e, o);
         if constexpr (THETA) {
+            // c.Qt.c.c and c.(Qt u).c over the distinct components of the symmetric tensors
+            // (a <= b <= c), each with its number of index orders
             T Qccc = neg_zero<T>(), cq = neg_zero<T>(), cQuc = neg_zero<T>(), cQuu = neg_zero<T>();
+            bool h0 = false, h1 = false, h2 = false, h3 = false;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 const int ca = LT::c(p, a);
                 if (ca == 0) continue;
-                accumulate_scaled(cq, ca, q[a]);
-                accumulate_scaled(cQuu, ca, Quu[a]);
+                add_term(cq, h1, ca, q[a]);
+                add_term(cQuu, h3, ca, Quu[a]);
 #pragma unroll
-                for (int b = 0; b < D; ++b) {
+                for (int b = a; b < D; ++b) {
                     const int cb = LT::c(p, b);
                     if (cb == 0) continue;
-                    accumulate_scaled(cQuc, ca * cb, Qu[a][b]);
+                    add_term(cQuc, h2, (a == b ? 1 : 2) * ca * cb, Qu[a][b]);
 #pragma unroll
-                    for (int c = 0; c < D; ++c) {
+                    for (int c = b; c < D; ++c) {
                         const int cc = LT::c(p, c);
-                        if (cc != 0) accumulate_scaled(Qccc, ca * cb * cc, Qt[a][b][c]);
+                        const int orders = (a == b && b == c) ? 1 : ((a == b || b == c) ? 3 : 6);
+                        if (cc != 0) add_term(Qccc, h0, orders * ca * cb * cc, Qt[a][b][c]);
                     }
                 }
             }
@@ -737,7 +827,10 @@ __device__ __forceinline__ void collide(T (&g)[LT::Q], T relax, T rho0, T kq = T
             const T a1 = T(-3) * (cQuc - T(LT::T0) * uq);
             T q_odd = a0, q_even = T(0);
             if constexpr (K >= 4) q_even = a0 * s + a1;
-            if constexpr (K >= 5) q_odd = a0 * (T(1) + H.h2 * T(0.5)) + a1 * s + T(3) * cQuu;
+            if constexpr (K >= 5) {
+                const T e2 = poly.a1 + T(s * s) * T(0.5);  // 1 + h2/2
+                q_odd = a0 * e2 + a1 * s + T(3) * cQuu;
+            }
             if constexpr (K >= 4) e += kq * q_even;
             o += kq * q_odd;
         }

@@ -123,7 +123,7 @@ def test_pool_autotune_keeps_results():
     us = lbm.lbm_pool_autotune(pool.handle, 2)
     assert us > 0
     chosen = lbm.lbm_pool_get_kernel(pool.handle)
-    assert chosen[0] in (1, 2) and chosen[1] in (128, 256)
+    assert chosen[0] in (1, 2, 4) and chosen[1] in (128, 256)
     base = _run_pool(reqs, kernel=chosen)
     while not all(pool.poll(i)[0] for i in ids):
         pool.advance(7)
