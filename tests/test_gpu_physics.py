@@ -13,8 +13,14 @@
     higher powers of the velocity), including D3Q39's K = 3 -> 4 step (~1e-4, below FP32
     resolution at this length).
 * Precision of the storage forms (Taylor-Green u0 = 0.05, tau = 0.52, 500 steps, 64^3):
-  FP32 within 1e-5 and shifted FP16 within 1e-3 of the FP64 oracle on u; BF16 (8-bit
-  significand) misses 1e-3 and is reported; 16-bit fixed point (range 1/4) within 3e-4.
+  FP32 within 1e-5 of the FP64 oracle on u, 16-bit fixed point (range 1/4) within 3e-4, the
+  reference-velocity forms within 2e-4 (FP16) and 1e-3 (BF16).  Plain shifted FP16 sits near
+  1e-3 and does not meet it reliably: its error is the accumulated half-precision rounding of
+  the stored values, a different realisation for every grouping of the FP32 collision
+  arithmetic (8.9e-4 and 1.15e-3 measured with two groupings; a CPU model of the same step
+  gives 7.6e-4 with exact arithmetic and 1.14e-3 with FP32-sized noise before each rounding).
+  It is recorded as missing the bound, with a regression ceiling; BF16 (8-bit significand)
+  misses 1e-3 and is reported the same way.
 """
 import numpy as np
 import pytest
@@ -111,7 +117,12 @@ def taylor_green_reference():
     return dims, rho, u, r_ref, u_ref
 
 
+_ERRORS = {}
+
+
 def _storage_error(taylor_green_reference, storage):
+    if storage in _ERRORS:
+        return _ERRORS[storage]
     dims, rho, u, r_ref, u_ref = taylor_green_reference
     s = lbm.Solver("D3Q19", dims, 0.52, 2, storage, storage_range=0.25 if storage == "q16" else None)
     s.set_fields(rho, u)
@@ -121,17 +132,30 @@ def _storage_error(taylor_green_reference, storage):
     eu, er = rel_u(uu, u_ref), rel_f(r, r_ref)
     print("D3Q19 64^3 Taylor-Green tau=0.52 K=2, %s storage, 500 steps: rel u error %.3e, rel rho error %.3e" % (
         storage, eu, er))
+    _ERRORS[storage] = eu
     return eu
 
 
-@pytest.mark.parametrize("storage,tol", [("f32", TOL_F32), ("f16", TOL_U16), ("q16", 3e-4), ("f16r", 2e-4),
-                                         ("bf16r", TOL_U16)])
+@pytest.mark.parametrize("storage,tol", [("f32", TOL_F32), ("q16", 3e-4), ("f16r", 2e-4), ("bf16r", TOL_U16)])
 def test_storage_precision_taylor_green_500_steps(taylor_green_reference, storage, tol):
     """Error of each storage form after 500 steps against the FP64 oracle on 64^3 (the 16-bit
     workload, tau = 0.52, at a size the oracle finishes in seconds; the stated sizes are checked
-    in test_gpu_storage_accuracy.py, where FP16 misses the target).  The fixed-point form runs
-    with range 1/4 (|h| reaches about 0.16 in this flow)."""
+    in test_gpu_storage_accuracy.py, where plain FP16 misses the target).  The fixed-point form
+    runs with range 1/4 (|h| reaches about 0.16 in this flow)."""
     assert _storage_error(taylor_green_reference, storage) < tol
+
+
+@pytest.mark.xfail(strict=False, reason="plain FP16 storage does not reliably meet 1e-3 on u at 64^3 "
+                                        "(measured 8.9e-4 and 1.15e-3 with two groupings of the FP32 collision)")
+def test_f16_storage_meets_u_bound_at_64(taylor_green_reference):
+    """The 16-bit target (1e-3 on u) for plain FP16 storage at 64^3: near the bound, on either side
+    of it depending on the rounding realisation, so recorded as not met (not strict)."""
+    assert _storage_error(taylor_green_reference, "f16") < TOL_U16
+
+
+def test_f16_storage_error_regression_at_64(taylor_green_reference):
+    """FP16's error at 64^3 (8.9e-4 and 1.15e-3 measured) must not grow past 1.5e-3."""
+    assert _storage_error(taylor_green_reference, "f16") < 1.5e-3
 
 
 @pytest.mark.xfail(strict=True, reason="BF16 storage misses the 1e-3 bound on u already at 64^3 (measured 4.9e-2)")
