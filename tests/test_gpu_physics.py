@@ -18,7 +18,8 @@
   1e-3 and does not meet it reliably: its error is the accumulated half-precision rounding of
   the stored values, a different realisation for every grouping of the FP32 collision
   arithmetic (8.9e-4 and 1.15e-3 measured with two groupings; a CPU model of the same step
-  gives 7.6e-4 with exact arithmetic and 1.14e-3 with FP32-sized noise before each rounding).
+  gives 7.6e-4 with exact arithmetic and 1.12e-3 to 1.21e-3 in three realisations with
+  FP32-sized noise before each rounding).
   It is recorded as missing the bound, with a regression ceiling; BF16 (8-bit significand)
   misses 1e-3 and is reported the same way.
 """
