@@ -75,13 +75,17 @@ __device__ __forceinline__ int wrapn(int v, int n) {
 __host__ __device__ constexpr int floordiv(int e, int V) { return e >= 0 ? e / V : -((-e + V - 1) / V); }
 
 // ------------------------------------------------------------------ fused step, variant 0
-// One thread owns V consecutive cells of one x-row.  For each velocity it loads
-// the source row's aligned V-vector (same x range), then realigns the x shift
-// with warp shuffles from the neighbouring lanes; lanes whose neighbour does not
-// hold the adjacent chunk of the same row (warp or row edge, periodic wrap) read
-// the missing values directly.  Every lane of the warp must call this (the
-// shuffles use the full mask); lanes with active == false compute on a valid
-// clamped position and store nothing.
+// One thread owns V consecutive cells (a chunk) of one x-row.  For velocity c it needs the
+// source row's values at x0 - c_x ... x0 + V - 1 - c_x.  Two ways to get them:
+//  - whole-chunk loads (unpadded rows of D3Q39 and of the reference-velocity forms): every
+//    chunk holding one of them is loaded as an aligned vector -- its own and up to
+//    ceil(max|c_x| / V) neighbours, which the neighbouring lanes load as well, so they come
+//    from L1 -- with no shuffles and no per-lane fix-ups;
+//  - shuffles (the other sets, and the pools' padded rows): the thread loads its own chunk and
+//    realigns the shift with warp shuffles; lanes whose neighbour does not hold the adjacent
+//    chunk of the same row (warp or row edge, periodic wrap) read the missing values directly.
+// Every lane of the warp must call this (the shuffles use the full mask); lanes with
+// active == false compute on a valid clamped position and store nothing.
 //
 // PADDED (the pools' layout): rows are stored with a pitch px >= nx (a multiple of 4), and
 // the pad cells x = nx + k hold periodic images of cells k.  A pad cell pulls exactly the
@@ -123,6 +127,15 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
     int xs[2 * M + 1];  // wrapped source x of one cell per thread (V = 1)
 #pragma unroll
     for (int k = -M; k <= M; ++k) xs[k + M] = wrapx(x0 - k);
+    // Whole-chunk loads on unpadded rows (which hold a whole number of chunks, so the periodic
+    // wrap moves whole chunks): xc[dl] is the first x of chunk + dl of the same row (nx >= max|c|
+    // keeps |dl| <= ncx).  Measured against the shuffles: D3Q39 K = 4 FP16 +27%, the reference-
+    // velocity forms +8%; on the max|c| = 1 sets with the held values the extra addresses cost
+    // registers (fixed point -10% from a spill, D3Q27 FP16 -3.5%), so those keep the shuffles.
+    constexpr bool kChunkLoads = !PADDED && V > 1 && (M >= 2 || RefOf<ST>::value);
+    int xc[2 * kMaxDl + 1];
+#pragma unroll
+    for (int dl = -kMaxDl; dl <= kMaxDl; ++dl) xc[dl + kMaxDl] = kChunkLoads ? wrap1(chunk + dl, ncx) * V : 0;
 
     // The V values of one stored plane pulled along velocity (cx, cy, cz): out[j] holds the
     // plane's value at x0 + j - cx of row (y - cy, z - cz).  ci: the codec's velocity index.
@@ -133,6 +146,26 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
             // one cell per thread: load the x-shifted element directly (the warp's load is still
             // one contiguous span; the neighbour warps' loads keep the extra sector in cache)
             out[0] = guard(roff + xs[cx + M], 1, P, status) ? decode<ST>(row[xs[cx + M]], qs, ci) : T(0);
+        } else if constexpr (kChunkLoads) {
+            // load each chunk that holds a shifted value whole (an aligned vector load; the
+            // neighbour lanes' chunks come from L1) and take the values from it
+#pragma unroll
+            for (int dl = -kMaxDl; dl <= kMaxDl; ++dl) {
+                bool need = false;
+#pragma unroll
+                for (int j = 0; j < V; ++j) need |= floordiv(j - cx, V) == dl;
+                if (!need) continue;
+                const int xo = xc[dl + kMaxDl];
+                S raw[V] = {};
+                if (guard(roff + xo, V, P, status)) load_vec<S, V>(row + xo, raw);
+                T v[V];
+                decode_vec<ST, V>(raw, v, qs, ci);
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const int e = j - cx;  // source element relative to x0
+                    if (floordiv(e, V) == dl) out[j] = v[e - dl * V];
+                }
+            }
         } else {
             S raw[V] = {};
             if (guard(roff + x0, V, P, status)) load_vec<S, V>(row + x0, raw);
