@@ -276,8 +276,10 @@ int lbm_bounds_checked(void);
 
 /* Host walk of the register-pull step's index arithmetic (no device work, any build): for
  * every thread of one launch with cells_per_thread V (1, 2, 4, 8; V must divide nx) on
- * dims, the offsets its loads and stores compute inside a velocity plane, each checked
- * against a plane of P elements with the same test the bounds-check build's kernels apply.
+ * dims, the offsets its loads and stores compute inside a velocity plane (the x-shift
+ * scheme of the plain storage forms: whole-chunk loads on D3Q39, warp shuffles with direct
+ * loads at warp and row edges on the other lattices), each checked against a plane of P
+ * elements with the same test the bounds-check build's kernels apply.
  * Returns how many accesses fall outside (0 for a consistent P = nx*ny*nz) and sets
  * *accesses (if not NULL) to the number checked; -1 for invalid arguments.  The paper has
  * no counterpart: it is a check of the library's own indexing. */

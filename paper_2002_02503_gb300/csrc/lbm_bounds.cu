@@ -4,7 +4,10 @@
 // The walk restates, for every thread of one launch of the register-pull step (V cells per
 // thread, the grid the launcher uses), the offsets its loads and stores compute inside a
 // velocity plane, and checks each span with span_in -- the test the bounds-check build's
-// kernels apply before every access.  With a consistent plane size (P = nx*ny*nz) nothing
+// kernels apply before every access.  It follows the x-shift scheme of the plain storage
+// forms: whole-chunk loads on D3Q39 (the reference-velocity forms use them on every lattice,
+// with the same offsets in their reference planes), shuffles with direct loads at the warp and
+// row edges on the other lattices.  With a consistent plane size (P = nx*ny*nz) nothing
 // falls outside; with an inconsistent dims/P pair the walk counts the accesses the device
 // guard would skip and record.
 #include <cuda_runtime.h>
@@ -33,6 +36,9 @@ extern "C" int64_t lbm_bounds_walk(lbm_lattice lattice, int V, const int64_t dim
     const int ncx = nx / V;
     const long long total = (long long)ncx * ny;  // threads per z-plane (grid.x * block covers it)
     const int kMaxDl = (maxc + V - 1) / V;
+    // the x-shift scheme of the plain storage forms: whole-chunk loads on the max|c| >= 2 set,
+    // shuffles with direct loads at warp and row edges on the others
+    const bool chunk_loads = V > 1 && maxc >= 2;
     long long bad = 0, n = 0;
     auto check = [&](long long first, int len) {
         ++n;
@@ -51,6 +57,15 @@ extern "C" int64_t lbm_bounds_walk(lbm_lattice lattice, int V, const int64_t dim
                 const long long roff = (long long)(wrap_host(z - cz, nz) * ny + wrap_host(y - cy, ny)) * nx;
                 if (V == 1) {
                     check(roff + wrap_host(x0 - cx, nx), 1);
+                    continue;
+                }
+                if (chunk_loads) {
+                    // every chunk that holds a shifted value, loaded whole (wrapped by whole chunks)
+                    for (int dl = -kMaxDl; dl <= kMaxDl; ++dl) {
+                        bool need = false;
+                        for (int j = 0; j < V; ++j) need = need || floordiv_host(j - cx, V) == dl;
+                        if (need) check(roff + (long long)wrap_host(chunk + dl, ncx) * V, V);
+                    }
                     continue;
                 }
                 check(roff + x0, V);  // the row vector
