@@ -21,6 +21,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CASES = [
     "tests/test_gpu_edges.py::test_degenerate_and_odd_sizes",
     "tests/test_gpu_edges.py::test_zero_steps_is_a_no_op",
+    "tests/test_gpu_edges.py::test_whole_chunk_loads_on_short_rows",
     "tests/test_gpu_parity.py::test_every_kernel_configuration",
     "tests/test_gpu_parity.py::test_staged_variant_matches_oracle",
     "tests/test_gpu_parity.py::test_flat_pair_variant_on_odd_lattices",

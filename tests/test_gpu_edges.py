@@ -3,6 +3,10 @@ lattice of the benchmark family that one GPU holds.
 
 * 1x1x1 (D3Q19) and 3x3x3 (D3Q39, the smallest its velocities allow) periodic lattices and odd
   sizes, against the oracle;
+* the register pull's whole-chunk loads (D3Q39 and the reference-velocity forms) on rows of one
+  to four chunks, where the periodic wrap of the neighbour chunks folds back onto the thread's
+  own chunk or its nearest neighbour, for every cells-per-thread the width admits, against the
+  oracle;
 * n = 0 steps changes nothing;
 * a uniform state (rho = 1, u = U everywhere) is left uniform by the collision and the
   streaming: every cell must hold the same stored values to the last bit, on D3Q19 1024^3 with
@@ -14,7 +18,7 @@ import pytest
 import oracle
 from paper_2002_02503_gb300 import fields, lbm
 
-from _lbmtest import TOL_F32, oracle_reference, rel_f, rel_u
+from _lbmtest import TOL_F32, TOL_ROUND, oracle_reference, rel_f, rel_u, to_lib_order
 
 pytestmark = pytest.mark.gpu
 
@@ -33,6 +37,44 @@ def test_degenerate_and_odd_sizes(name, K, dims):
     s.close()
     assert rel_f(r, r_ref) < TOL_F32
     assert rel_u(uu, u_ref) < TOL_F32
+
+
+@pytest.mark.parametrize("name,K,storage,dims", [("D3Q39", 4, "f32", (4, 5, 3)), ("D3Q39", 4, "f32", (8, 3, 3)),
+                                                 ("D3Q39", 3, "f16", (8, 4, 3)), ("D3Q19", 3, "f16r", (4, 3, 5)),
+                                                 ("D3Q19", 2, "f16r", (2, 3, 3)), ("D3Q27", 3, "bf16r", (8, 3, 2))])
+def test_whole_chunk_loads_on_short_rows(name, K, storage, dims):
+    """Rows of nx / V = 1, 2 or 4 chunks: the neighbour chunks of the x shifts (up to 3 on D3Q39,
+    two chunks away for two cells per thread) wrap onto the row's own chunks.  Each built
+    cells-per-thread against the oracle after 10 steps (white-noise fields) and against one cell
+    per thread (the direct shifted loads)."""
+    D = lbm.lbm_lattice_info(name)["D"]
+    rho, u = fields.random_fields(dims, D, salt=62)
+    f_ref, r_ref, u_ref = oracle_reference(name, K, 0.6, dims, rho, u, 10)
+    tol = TOL_F32 if storage == "f32" else TOL_ROUND[storage.rstrip("r")]
+    results = {}
+    for V in (1, 2, 4, 8):
+        if dims[0] % V:
+            continue
+        s = lbm.Solver(name, dims, 0.6, K, storage)
+        try:
+            lbm.lbm_set_kernel(s.handle, 0, V, 128)
+        except lbm.LbmError:  # not every cells-per-thread is built for every lattice and order
+            s.close()
+            continue
+        s.set_fields(rho, u)
+        s.step(10)
+        r, uu = s.moments()
+        results[V] = s.f()
+        s.close()
+        assert rel_u(uu, u_ref) < tol, (V, rel_u(uu, u_ref))
+        assert rel_f(r, r_ref) < tol, V
+    assert len(results) >= 2
+    if storage == "f32":
+        f_want = to_lib_order(name, f_ref)
+        for V, f in results.items():
+            assert rel_f(f, f_want) < TOL_F32, V
+    for V, f in results.items():
+        np.testing.assert_allclose(f, results[1], rtol=tol, atol=tol * np.abs(results[1]).max())
 
 
 def test_zero_steps_is_a_no_op():

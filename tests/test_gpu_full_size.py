@@ -106,6 +106,16 @@ def test_d3q19_512_taylor_green_storage_forms(storage, tol):
     _check("D3Q19", 2, 0.52, dims, rho, u, storage, tol, storage_range=0.25 if storage == "q16" else None)
 
 
+@pytest.mark.parametrize("name,K,storage,side,tau", [("D3Q39", 4, "f16", 192, 0.6), ("D3Q19", 2, "f16r", 512, 0.52)])
+def test_whole_chunk_load_forms_at_full_size(name, K, storage, side, tau):
+    """The configurations whose x shifts come from whole neighbour-chunk loads, at the sizes their
+    rates are quoted on (D3Q39 K = 4 FP16 192^3; FP16 with a reference velocity, D3Q19 512^3),
+    in the autotuned launch: f after three steps at the sampled cells and the periodic faces."""
+    dims = (side,) * 3
+    rho, u = fields.taylor_green_3d(dims, 0.05, lbm.lbm_lattice_info(name)["T0"])
+    _check(name, K, tau, dims, rho, u, storage, TOL_U16)
+
+
 @pytest.mark.parametrize("K", [2, 3])
 def test_d3q19_128_taylor_green_100_steps_full_field(K):
     """The headline workload (D3Q19 FP32 Taylor-Green, u0 = 0.05, tau = 0.55) on 128^3, in the
