@@ -476,8 +476,9 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename ST::S *
 // takes one more CTA per SM without spills, chosen by measurement):
 //  - fixed point, four cells per thread, D3Q19, K = 2: ~108 registers, four 128-thread CTAs
 //    per SM; at 96 five fit and the step runs 8% faster;
-//  - FP32 energy-flux step, D3Q39, K = 4: 128 registers, four CTAs; at 96 five despite a
-//    56-byte spill, 1.6% faster (at 104, with four CTAs still, 2% slower);
+//  - FP32 energy-flux step, D3Q39, K = 4: 128 registers, four CTAs; at 96 five, 1.6% faster
+//    even with the 56-byte spill it had then (at 104, with four CTAs still, 2% slower); since the
+//    energy-flux contractions run over the distinct tensor components it fits 96 without one;
 //  - reference-velocity storage, four cells per thread, D3Q19: 130 registers, three CTAs; at
 //    128 four.
 // A cap is not applied elsewhere: even a no-op cap changes the register allocation.  The
