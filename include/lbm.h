@@ -302,8 +302,9 @@ typedef struct lbm_pool lbm_pool;
 
 /* Device bytes one request of these dims occupies in a pool's arena: its two
  * distribution buffers (Q planes of px*ny*nz values, px = nx rounded up to a multiple of
- * 4) and a 256-byte status word.  0 for invalid arguments and for
- * the storage forms pools do not run (the reference-velocity forms). */
+ * 4) and a 256-byte status word.  0 for invalid arguments, for dims whose padded plane
+ * px*ny*nz exceeds 2^31-1 cells (lbm_pool_submit rejects those with LBM_ERR_INVALID_ARG),
+ * and for the storage forms pools do not run (the reference-velocity forms). */
 size_t lbm_pool_request_bytes(lbm_lattice lattice, const int64_t dims[3], lbm_storage storage);
 
 /* arena: caller-owned device memory (256-byte aligned) that the pool carves

@@ -287,7 +287,9 @@ size_t lbm_pool_request_bytes(lbm_lattice lat, const int64_t dims[3], lbm_storag
     if (!lattice_query(lat, &D, &Q, &maxc, &kmax) || storage_bytes(st) == 0) return 0;
     if (has_reference_planes(st)) return 0;  // pools do not run the reference-velocity forms
     if (!dims_check(lat, dims).empty()) return 0;
-    return request_bytes(Q, storage_bytes(st), (long long)pool_pitch(int(dims[0])) * dims[1] * dims[2]);
+    const long long Cp = (long long)pool_pitch(int(dims[0])) * dims[1] * dims[2];
+    if (Cp > 2147483647LL) return 0;  // the padded plane must stay within int offsets
+    return request_bytes(Q, storage_bytes(st), Cp);
 }
 
 lbm_status lbm_pool_create(lbm_lattice lat, int K, lbm_storage st, void *arena, size_t arena_bytes, int max_slots,
@@ -373,6 +375,8 @@ lbm_status lbm_pool_submit(lbm_pool *p, const int64_t dims[3], double tau, doubl
     r.px = pool_pitch(r.nx);
     r.C = (long long)dims[0] * dims[1] * dims[2];
     r.Cp = (long long)r.px * dims[1] * dims[2];
+    if (r.Cp > 2147483647LL)  // thread and in-plane offsets of the batch kernels are ints
+        return set_error(LBM_ERR_INVALID_ARG, "rows padded to a multiple of 4 make more than 2^31-1 cells per plane");
     r.relax = 1.0 - 1.0 / tau;
     r.rho0 = rho0;
     r.steps_total = steps;

@@ -201,3 +201,6 @@ def test_pool_request_bytes_use_the_padded_pitch(L):
         want = 2 * align(19 * px * ny * nz * 2) + 256
         assert lbm.lbm_pool_request_bytes("D3Q19", (nx, ny, nz), "f16") == want, (nx, ny, nz)
     assert lbm.lbm_pool_request_bytes("D3Q19", (33, 20, 7), "f32") == 2 * align(19 * 36 * 20 * 7 * 4) + 256
+    # a plane within 2^31 - 1 cells whose padded rows would pass it: not admitted
+    assert lbm.lbm_pool_request_bytes("D3Q19", (2 ** 24 - 1, 128, 1), "f16") == 0
+    assert lbm.lbm_pool_request_bytes("D3Q19", (2 ** 24, 127, 1), "f16") == 2 * align(19 * 2 ** 24 * 127 * 2) + 256
