@@ -137,15 +137,23 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
 #pragma unroll
     for (int dl = -kMaxDl; dl <= kMaxDl; ++dl) xc[dl + kMaxDl] = kChunkLoads ? wrap1(chunk + dl, ncx) * V : 0;
 
+    // Offsets within a plane (< P <= 2^31 - 1, checked on the host) as 32-bit ints on D3Q19 with
+    // the plain storage forms, 64-bit elsewhere -- the addressing form that measured faster per
+    // lattice (ints: D3Q19 K = 3 FP16 four cells +9%, the fixed-point and pool steps +1%; D3Q27
+    // K = 3 FP16 -15%, D3Q39 K = 4 FP16 -6%, FP16 with a reference velocity -3%), as ptxas
+    // schedules and allocates the address arithmetic differently.
+    constexpr bool kIntOffsets = LT::Q == 19 && !RefOf<ST>::value;
+    using Off = typename std::conditional<kIntOffsets, int, long long>::type;
+
     // The V values of one stored plane pulled along velocity (cx, cy, cz): out[j] holds the
     // plane's value at x0 + j - cx of row (y - cy, z - cz).  ci: the codec's velocity index.
     auto pull = [&](const S *__restrict__ plane, int cx, int cy, int cz, int ci, T(&out)[V]) {
-        const long long roff = (long long)(zs[cz + M] * ny + ys[cy + M]) * px;  // row offset in its plane
-        const S *row = plane + roff;
+        const Off roff = Off(zs[cz + M] * ny + ys[cy + M]) * Off(px);  // row offset in its plane
+        const S *row = plane + roff;  // (the 64-bit form addresses element x as row + x)
         if constexpr (V == 1) {
             // one cell per thread: load the x-shifted element directly (the warp's load is still
             // one contiguous span; the neighbour warps' loads keep the extra sector in cache)
-            out[0] = guard(roff + xs[cx + M], 1, P, status) ? decode<ST>(row[xs[cx + M]], qs, ci) : T(0);
+            out[0] = guard(roff + xs[cx + M], 1, P, status) ? decode<ST>(kIntOffsets ? plane[roff + xs[cx + M]] : row[xs[cx + M]], qs, ci) : T(0);
         } else if constexpr (kChunkLoads) {
             // load each chunk that holds a shifted value whole (an aligned vector load; the
             // neighbour lanes' chunks come from L1) and take the values from it
@@ -157,7 +165,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
                 if (!need) continue;
                 const int xo = xc[dl + kMaxDl];
                 S raw[V] = {};
-                if (guard(roff + xo, V, P, status)) load_vec<S, V>(row + xo, raw);
+                if (guard(roff + xo, V, P, status)) load_vec<S, V>(kIntOffsets ? plane + (roff + xo) : row + xo, raw);
                 T v[V];
                 decode_vec<ST, V>(raw, v, qs, ci);
 #pragma unroll
@@ -168,7 +176,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
             }
         } else {
             S raw[V] = {};
-            if (guard(roff + x0, V, P, status)) load_vec<S, V>(row + x0, raw);
+            if (guard(roff + x0, V, P, status)) load_vec<S, V>(kIntOffsets ? plane + (roff + x0) : row + x0, raw);
             T v[V];
             decode_vec<ST, V>(raw, v, qs, ci);
             if (cx == 0) {
@@ -188,7 +196,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
                         T sh = __shfl_sync(kFull, v[ei], sl < 0 ? 0 : (sl > 31 ? 31 : sl));
                         if (!ok[dl + kMaxDl]) {
                             const int xw = wrapx(x0 + e);
-                            sh = guard(roff + xw, 1, P, status) ? decode<ST>(row[xw], qs, ci) : T(0);
+                            sh = guard(roff + xw, 1, P, status) ? decode<ST>(kIntOffsets ? plane[roff + xw] : row[xw], qs, ci) : T(0);
                         }
                         out[j] = sh;
                     }
@@ -245,7 +253,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
     constexpr bool kStream = !BGK && !THETA && LT::Q >= 27;
     if constexpr (kStream) {
         // FP32 arithmetic with V >= 2 runs two cells per pass on the paired FP32 instructions.
-        const long long ooff = (long long)(z * ny + y) * px + x0;  // offset of the thread's cells in a plane
+        const Off ooff = Off(z * ny + y) * Off(px) + x0;  // offset of the thread's cells in a plane
         S *out = dst + ooff;
         const bool store_ok = active && guard(ooff, V, P, status);
         using A = typename std::conditional<kPaired, F2, T>::type;
@@ -423,7 +431,7 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
         }
     }
 
-    const long long ooff = (long long)(z * ny + y) * px + x0;  // offset of the thread's cells in a plane
+    const Off ooff = Off(z * ny + y) * Off(px) + x0;  // offset of the thread's cells in a plane
     S *out = dst + ooff;
     const bool store_ok = active && guard(ooff, V, P, status);
     if constexpr (kRef) {
