@@ -180,7 +180,7 @@ def batched_rate(n=40, steps=200, storage="f32", K=3, chunk=50, salt=5, autotune
             lbm.lbm_pool_set_kernel(pool.handle, *kernel)
         pool.advance(chunk)
         if autotune and kernel is None:
-            lbm.lbm_pool_autotune(pool.handle, 5)
+            lbm.lbm_pool_autotune(pool.handle, 20)
         pool.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(pool.compute)
