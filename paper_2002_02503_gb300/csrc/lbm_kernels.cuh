@@ -137,12 +137,13 @@ __device__ __forceinline__ void pull_collide_store(const typename ST::S *__restr
 #pragma unroll
     for (int dl = -kMaxDl; dl <= kMaxDl; ++dl) xc[dl + kMaxDl] = kChunkLoads ? wrap1(chunk + dl, ncx) * V : 0;
 
-    // Offsets within a plane (< P <= 2^31 - 1, checked on the host) as 32-bit ints on D3Q19 with
-    // the plain storage forms, 64-bit elsewhere -- the addressing form that measured faster per
-    // lattice (ints: D3Q19 K = 3 FP16 four cells +9%, the fixed-point and pool steps +1%; D3Q27
-    // K = 3 FP16 -15%, D3Q39 K = 4 FP16 -6%, FP16 with a reference velocity -3%), as ptxas
-    // schedules and allocates the address arithmetic differently.
-    constexpr bool kIntOffsets = LT::Q == 19 && !RefOf<ST>::value;
+    // Offsets within a plane (< P <= 2^31 - 1, checked on the host) as 32-bit ints on unpadded
+    // D3Q19 rows with the plain storage forms, 64-bit elsewhere -- the addressing form that
+    // measured faster per case (ints: D3Q19 K = 3 FP16 four cells +9%, fixed point +1%; D3Q27
+    // K = 3 FP16 -15%, D3Q39 K = 4 FP16 -6%, FP16 with a reference velocity -3%, the FP32 pool
+    // -10%, the FP16 pool +0.7%), as ptxas schedules and allocates the address arithmetic
+    // differently.
+    constexpr bool kIntOffsets = !PADDED && LT::Q == 19 && !RefOf<ST>::value;
     using Off = typename std::conditional<kIntOffsets, int, long long>::type;
 
     // The V values of one stored plane pulled along velocity (cx, cy, cz): out[j] holds the
