@@ -172,7 +172,8 @@ def test_bounds_walk_consistent_and_inconsistent_plane_sizes(L):
     (P = nx*ny*nz); with a dims/P pair that disagrees (one element short, or the nz of a bigger
     lattice) the walk counts the accesses the bounds-check build's kernels would skip."""
     cases = [("D3Q19", (1, 1, 1)), ("D3Q19", (5, 7, 9)), ("D3Q39", (3, 3, 3)), ("D3Q39", (12, 5, 3)),
-             ("D2Q9", (3, 11, 1)), ("D3Q27", (8, 3, 1)), ("D3Q15", (16, 1, 5)), ("D3Q19", (72, 9, 4))]
+             ("D2Q9", (3, 11, 1)), ("D3Q27", (8, 3, 1)), ("D3Q15", (16, 1, 5)), ("D3Q19", (72, 9, 4)),
+             ("D3Q39", (4, 5, 3)), ("D3Q39", (8, 3, 3))]  # rows of one to four chunks (whole-chunk loads)
     for name, dims in cases:
         C = int(np.prod(dims))
         for V in (1, 2, 4, 8):
